@@ -1,0 +1,137 @@
+/*
+ * swmm.h -- C ABI of the GB300 (sm_103a) Strassen / Strassen-Winograd matrix product.
+ *
+ * Every entry point computes C <- A * B (overwrite; no alpha/beta), the problem of
+ * Sec. 2.1 of arXiv 2309.00628 ("Algoritmos para Multiplicacao Matricial"):
+ *   c_ij = sum_p a_ip b_pj,  C m x n,  A m x k,  B k x n  (the Sec. 3.4 naming).
+ * Matrices are ROW-MAJOR with leading dimensions (elements): A[i*lda + p],
+ * B[p*ldb + j], C[i*ldc + j].  A column-major caller gets the same product by
+ * passing the transposed problem (C^T = B^T A^T).
+ *
+ * Pointers:  device pointers unless the name says _host.  The caller owns A, B and C
+ * and the stream; the library owns its workspace (taken from the budget given to
+ * sw_create) and never frees caller memory.  Calls are asynchronous on `stream`
+ * (a cudaStream_t passed as void*, NULL = legacy default stream) unless documented
+ * otherwise; device-side failures (a bounded wait that expired) are reported by
+ * sw_sync().  No call throws; every call returns an sw_status, and sw_last_error()
+ * gives a one-line reason for the last non-OK status on the handle.
+ *
+ * Variant bitfield (OR one value of each group):
+ *   algorithm   SW_ALGO_NAIVE     plain product (Alg. 1) as one tiled tensor-core GEMM
+ *               SW_ALGO_STRASSEN  Strassen's 7 products and 18 additions (Sec. 2.2, Alg. 2)
+ *               SW_ALGO_WINOGRAD  Strassen-Winograd, the 22-operation BDPZ form (Sec. 2.3, Alg. 3)
+ *   schedule    SW_SCHED_FUSED    all levels' operand sums in one pass; the 7^L leaf products in
+ *                                 one grouped launch whose epilogue adds +-P into the C blocks
+ *               SW_SCHED_TWO_TEMP Table 2 ("Two Temp Winograd", Sec. 3.3): two temporaries X, Y
+ *                                 per level; products written into C quadrants (Winograd only)
+ *               SW_SCHED_IN_PLACE Table 3 ("In-Place Winograd", Sec. 3.3): temporaries stored in
+ *                                 A, B and C; needs m == n == k; A AND B ARE OVERWRITTEN with
+ *                                 unspecified values (Winograd only)
+ *               SW_SCHED_ALLOC    Alg. 2 / Alg. 3 as written: fresh temporaries at every level
+ *   odd sizes   SW_PAD            zero padding to a multiple of 2^L (Sec. 3.1); virtual (TMA
+ *                                 out-of-bounds fill) where the schedule allows, else a copy
+ *               SW_PEEL           peel the trailing rows / columns / inner indices that are not a
+ *                                 multiple of the split granularity and fix them up with thin
+ *                                 products
+ *   leaf        SW_LEAF_TF32      FP32 inputs, TF32 tensor-core products (operands rounded to
+ *                                 nearest), FP32 accumulation
+ *               SW_LEAF_BF16X3    FP32 inputs split as hi = bf16(x), lo = bf16(x - hi); products
+ *                                 hi*hi + hi*lo + lo*hi with FP32 accumulation (FP32-level accuracy)
+ *   The FP64 entry points ignore the leaf group and always use FP64 leaves.
+ *
+ * Recursion depth L (Sec. 3.4 cutoff): halve while min(ceil(m/2^l), ceil(n/2^l), ceil(k/2^l))
+ * > cutoff.  cutoff <= 0 asks the library's tuned choice.  SW_ALGO_NAIVE ignores the cutoff.
+ */
+#ifndef SWMM_H
+#define SWMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SW_OK = 0,
+    SW_EINVAL = 1,        /* bad argument (negative size, null pointer, ld too small, ...) */
+    SW_ENOMEM = 2,        /* device allocation failed */
+    SW_EBUDGET = 3,       /* the request needs more workspace than the handle's budget */
+    SW_ECUDA = 4,         /* a CUDA runtime / driver call failed */
+    SW_ETIMEOUT = 5,      /* a bounded device-side wait expired (see sw_sync) */
+    SW_EUNSUPPORTED = 6   /* valid request this build does not implement (e.g. IN_PLACE, m != n) */
+} sw_status;
+
+#define SW_ALGO_NAIVE 0x0u
+#define SW_ALGO_STRASSEN 0x1u
+#define SW_ALGO_WINOGRAD 0x2u
+#define SW_ALGO_MASK 0xFu
+#define SW_SCHED_FUSED 0x00u
+#define SW_SCHED_TWO_TEMP 0x10u
+#define SW_SCHED_IN_PLACE 0x20u
+#define SW_SCHED_ALLOC 0x30u
+#define SW_SCHED_MASK 0xF0u
+#define SW_PAD 0x000u
+#define SW_PEEL 0x100u
+#define SW_ODD_MASK 0xF00u
+#define SW_LEAF_TF32 0x0000u
+#define SW_LEAF_BF16X3 0x1000u
+#define SW_LEAF_MASK 0xF000u
+
+typedef struct sw_handle_s *sw_handle;
+
+/* Create a handle on the current CUDA device.  `workspace_budget_bytes` caps the device
+ * memory the library may hold for temporaries (0 = no cap).  Memory is taken lazily. */
+sw_status sw_create(sw_handle *h, size_t workspace_budget_bytes);
+
+/* Release the handle and all memory it holds.  Synchronises the device first. */
+sw_status sw_destroy(sw_handle h);
+
+/* One-line reason for the last non-OK status returned on `h` ("" if none). */
+const char *sw_last_error(sw_handle h);
+
+/* Workspace bytes the product would take (elem_bytes 4 = FP32 entry, 8 = FP64 entry),
+ * without running it.  For SW_SCHED_ALLOC this is the peak of the per-level temporaries
+ * (Alg. 3: 4 S + 4 T + 7 P blocks per level, all levels live); for SW_SCHED_TWO_TEMP the
+ * X and Y temporaries of every level (Table 2); SW_SCHED_IN_PLACE needs none beyond a
+ * padded copy for unaligned sizes; SW_SCHED_FUSED the materialised operand sums. */
+sw_status sw_mm_workspace_size(int m, int n, int k, int cutoff, uint32_t variant, int elem_bytes,
+                               size_t *bytes);
+
+/* Recursion depth the product will use (see the header comment). */
+sw_status sw_mm_depth(int m, int n, int k, int cutoff, uint32_t variant, int elem_bytes, int *depth);
+
+/* FP32 product C <- A B (device pointers, row-major).  Asynchronous on `stream`.
+ * Alignment: fastest when A, B, C are 16-byte aligned and lda, ldb, ldc are multiples of 4;
+ * otherwise the operands are copied into aligned workspace first. */
+sw_status sw_smm(sw_handle h, const float *A, int lda, const float *B, int ldb, float *C, int ldc,
+                 int m, int n, int k, int cutoff, uint32_t variant, void *stream);
+
+/* FP64 product C <- A B (device pointers, row-major); FP64 leaves and additions. */
+sw_status sw_dmm(sw_handle h, const double *A, int lda, const double *B, int ldb, double *C, int ldc,
+                 int m, int n, int k, int cutoff, uint32_t variant, void *stream);
+
+/* FP32 product with HOST operands: copies A and B to the device, runs sw_smm and copies C back,
+ * all on `stream`; returns after the stream has finished (synchronous).  Pinned host memory
+ * gives the fastest copies.  Device buffers come from the handle's workspace. */
+sw_status sw_smm_host(sw_handle h, const float *A_host, int lda, const float *B_host, int ldb,
+                      float *C_host, int ldc, int m, int n, int k, int cutoff, uint32_t variant,
+                      void *stream);
+
+/* Wait for `stream` and report device-side failures of this handle's kernels: SW_ETIMEOUT if a
+ * bounded wait inside a kernel expired, SW_ECUDA if the stream reported a CUDA error.
+ * Clears the device error word. */
+sw_status sw_sync(sw_handle h, void *stream);
+
+/* Reductions used by the error checks, FP64 on the device (Sec. 2.1 problem's error metric):
+ *   out[0] = max_ij |C_ij - R_ij|,  out[1] = max |A|,  out[2] = max |B|
+ * C is FP32 (elem_bytes 4) or FP64 (8); A and B have the same type as C; R is FP64.
+ * Any pointer may be NULL (its entry is then 0).  Synchronous: `out` is a host array. */
+sw_status sw_error_norms(sw_handle h, int elem_bytes, int m, int n, int k, const void *A, int lda,
+                         const void *B, int ldb, const void *C, int ldc, const double *R, int ldr,
+                         double *out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SWMM_H */

@@ -1,0 +1,939 @@
+// api.cu -- C ABI (include/swmm.h), workspace pool and the planner that lowers a product
+// C <- A B into kernel launches:
+//
+//   NAIVE            one grouped-GEMM launch, one leaf, one STORE target (Alg. 1 on tensor cores)
+//   FUSED            one operand-sum pass per operand (all L levels at once) + one grouped-GEMM
+//                    launch over the 7^L leaves; the leaf epilogues add +-P into the C blocks
+//   TWO_TEMP         Table 2 of Sec. 3.3, step by step, X / Y temporaries per level
+//   IN_PLACE         Table 3 of Sec. 3.3, step by step, temporaries in A, B and C
+//   ALLOC            Alg. 2 / Alg. 3 as written: fresh temporaries at every level
+//
+// The recursion depth follows the Sec. 3.4 cutoff; odd sizes are padded (Sec. 3.1) or peeled.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/swmm.h"
+#include "internal.h"
+#include "plan.h"
+
+using namespace swk;
+
+namespace {
+
+// ------------------------------------------------------------------ tensor-map encoding
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    return fn;
+}
+
+// FP32 row-major view rows x cols (ld elements) -> 2-D tensor map with a box of
+// box_cols (innermost, 128 bytes) x box_rows, 128-byte swizzle, zero fill out of bounds.
+bool make_map_f32(CUtensorMap* m, const void* base, int rows, int cols, long long ld, int box_cols, int box_rows) {
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)std::max(cols, 1), (cuuint64_t)std::max(rows, 1)};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
+    cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+inline long long round_up(long long x, long long a) { return (x + a - 1) / a * a; }
+inline long long ceil_div(long long x, long long a) { return (x + a - 1) / a; }
+
+// ------------------------------------------------------------------ plan
+enum OpKind { OP_GEMM_TF32, OP_GEMM_F64, OP_ADDSUB, OP_COPY_PAD, OP_PREADD, OP_MEMSET };
+
+struct Op {
+    OpKind kind;
+    // grouped GEMM
+    MapSet maps;
+    int bn = 256, nleaves = 0, items = 0;
+    size_t leaves_off = 0, targets_off = 0, refs_off = 0;
+    // elementwise
+    int eb = 4, rows = 0, cols = 0, src_rows = 0, src_cols = 0;
+    void* z = nullptr;
+    long long ldz = 0, ldx = 0, ldy = 0;
+    const void* x = nullptr;
+    const void* y = nullptr;
+    float sy = 1.f;
+    PreaddArgs pre;
+};
+
+struct Plan {
+    std::vector<Op> ops;
+    std::vector<uint8_t> blob;  // leaves / targets / refs, uploaded once
+    void* d_blob = nullptr;
+    size_t ws_need = 0;
+    int depth = 0;
+    ~Plan() {
+        if (d_blob) cudaFree(d_blob);
+    }
+};
+
+// A row-major view (byte pointer, ld in elements).
+struct View {
+    char* p;
+    long long ld;
+    int rows, cols;
+};
+
+struct Planner {
+    int eb;                 // 4 = FP32 (TF32 leaves), 8 = FP64
+    uint32_t variant;
+    bool dry;               // size only: no pointers, no maps
+    char* ws_base;
+    size_t ws_top = 0, ws_peak = 0;
+    Plan* plan;
+    std::string err;
+    int sched, algo;
+
+    View quad(View v, int q) const {
+        const int h = v.rows / 2, w = v.cols / 2;
+        View r;
+        r.p = v.p + ((long long)(q >> 1) * h * v.ld + (long long)(q & 1) * w) * eb;
+        r.ld = v.ld;
+        r.rows = h;
+        r.cols = w;
+        return r;
+    }
+
+    View talloc(int rows, int cols) {
+        const long long ld = round_up(std::max(cols, 1), 4);
+        const size_t bytes = (size_t)round_up((long long)std::max(rows, 1) * ld * eb, 256);
+        View v;
+        v.p = dry ? nullptr : ws_base + ws_top;
+        v.ld = ld;
+        v.rows = rows;
+        v.cols = cols;
+        ws_top += bytes;
+        ws_peak = std::max(ws_peak, ws_top);
+        return v;
+    }
+
+    size_t put_blob(const void* src, size_t bytes) {
+        size_t off = round_up(plan->blob.size(), 64);
+        plan->blob.resize(off + bytes);
+        if (bytes) memcpy(plan->blob.data() + off, src, bytes);
+        return off;
+    }
+
+    void add(View z, View x, View y, float sy) {
+        if (dry) return;
+        Op o;
+        o.kind = OP_ADDSUB;
+        o.eb = eb;
+        o.rows = z.rows;
+        o.cols = z.cols;
+        o.z = z.p;
+        o.ldz = z.ld;
+        o.x = x.p;
+        o.ldx = x.ld;
+        o.y = y.p;
+        o.ldy = y.ld;
+        o.sy = sy;
+        plan->ops.push_back(o);
+    }
+
+    void copy_pad(View z, View x) {  // z (its full extent) <- x, zero outside x's extent
+        if (dry) return;
+        Op o;
+        o.kind = OP_COPY_PAD;
+        o.eb = eb;
+        o.rows = z.rows;
+        o.cols = z.cols;
+        o.z = z.p;
+        o.ldz = z.ld;
+        o.x = x.p;
+        o.ldx = x.ld;
+        o.src_rows = x.rows;
+        o.src_cols = x.cols;
+        plan->ops.push_back(o);
+    }
+
+    void memset0(View z) {
+        if (dry) return;
+        Op o;
+        o.kind = OP_MEMSET;
+        o.eb = eb;
+        o.rows = z.rows;
+        o.cols = z.cols;
+        o.z = z.p;
+        o.ldz = z.ld;
+        plan->ops.push_back(o);
+    }
+
+    static bool vec_ok(const View& v) {
+        return ((reinterpret_cast<uintptr_t>(v.p) & 15) == 0) && (v.ld % 4) == 0;
+    }
+
+    // One leaf product c (=|+=) a b.
+    bool gemm(View a, View b, View c, int mode) {
+        if (dry || c.rows <= 0 || c.cols <= 0) return true;
+        if (a.cols == 0) {
+            if (mode == TGT_STORE) memset0(c);
+            return true;
+        }
+        Target t;
+        t.c = c.p;
+        t.ldc = c.ld;
+        t.rows = c.rows;
+        t.cols = c.cols;
+        t.sign = 1.f;
+        t.mode = mode;
+        t.vec_ok = vec_ok(c) ? 1 : 0;
+        t.pad_ = 0;
+        Leaf lf;
+        memset(&lf, 0, sizeof(lf));
+        lf.a_map = 0;
+        lf.b_map = 1;
+        lf.m = c.rows;
+        lf.n = c.cols;
+        lf.tgt_begin = 0;
+        lf.tgt_count = 1;
+        lf.tile_begin = 0;
+        Op o;
+        if (eb == 4) {
+            o.kind = OP_GEMM_TF32;
+            o.bn = c.cols <= 128 ? 128 : 256;
+            lf.kblocks = (int)ceil_div(a.cols, tf32_tile_k());
+            lf.tiles_n = (int)ceil_div(c.cols, o.bn);
+            if (!make_map_f32(&o.maps.m[0], a.p, a.rows, a.cols, a.ld, 32, tf32_tile_m()) ||
+                !make_map_f32(&o.maps.m[1], b.p, b.rows, b.cols, b.ld, 32, 32)) {
+                err = "tensor map encoding failed (alignment?)";
+                return false;
+            }
+            o.items = (int)(ceil_div(c.rows, tf32_tile_m()) * lf.tiles_n);
+        } else {
+            o.kind = OP_GEMM_F64;
+            lf.kblocks = a.cols;
+            lf.tiles_n = (int)ceil_div(c.cols, F64_BN);
+            MatRef refs[2] = {{a.p, a.ld, a.rows, a.cols}, {b.p, b.ld, b.rows, b.cols}};
+            o.refs_off = put_blob(refs, sizeof(refs));
+            o.items = (int)(ceil_div(c.rows, F64_BM) * lf.tiles_n);
+        }
+        o.nleaves = 1;
+        o.leaves_off = put_blob(&lf, sizeof(lf));
+        o.targets_off = put_blob(&t, sizeof(t));
+        plan->ops.push_back(o);
+        return true;
+    }
+
+    // ---------------------------------------------------------- materialised schedules
+    bool product(View a, View b, View c, int L) {
+        if (L == 0) return gemm(a, b, c, TGT_STORE);
+        if (sched == SW_SCHED_TWO_TEMP) return two_temp(a, b, c, L);
+        if (sched == SW_SCHED_IN_PLACE) return in_place(a, b, c, L);
+        return algo == SW_ALGO_STRASSEN ? alloc_strassen(a, b, c, L) : alloc_winograd(a, b, c, L);
+    }
+
+    // Alg. 2 (Sec. 2.2) with fresh temporaries: two operand sums, seven products.
+    bool alloc_strassen(View a, View b, View c, int L) {
+        View A11 = quad(a, 0), A12 = quad(a, 1), A21 = quad(a, 2), A22 = quad(a, 3);
+        View B11 = quad(b, 0), B12 = quad(b, 1), B21 = quad(b, 2), B22 = quad(b, 3);
+        View C11 = quad(c, 0), C12 = quad(c, 1), C21 = quad(c, 2), C22 = quad(c, 3);
+        const size_t mark = ws_top;
+        View sa = talloc(A11.rows, A11.cols), sb = talloc(B11.rows, B11.cols), P[7];
+        for (int i = 0; i < 7; ++i) P[i] = talloc(C11.rows, C11.cols);
+        bool ok = true;
+        add(sa, A11, A22, +1); add(sb, B11, B22, +1); ok &= product(sa, sb, P[0], L - 1);
+        add(sa, A21, A22, +1); ok &= product(sa, B11, P[1], L - 1);
+        add(sb, B12, B22, -1); ok &= product(A11, sb, P[2], L - 1);
+        add(sb, B21, B11, -1); ok &= product(A22, sb, P[3], L - 1);
+        add(sa, A11, A12, +1); ok &= product(sa, B22, P[4], L - 1);
+        add(sa, A21, A11, -1); add(sb, B11, B12, +1); ok &= product(sa, sb, P[5], L - 1);
+        add(sa, A12, A22, -1); add(sb, B21, B22, +1); ok &= product(sa, sb, P[6], L - 1);
+        // C11 = P1 + P4 - P5 + P7 ; C12 = P3 + P5 ; C21 = P2 + P4 ; C22 = P1 + P3 - P2 + P6
+        add(C11, P[0], P[3], +1); add(C11, C11, P[4], -1); add(C11, C11, P[6], +1);
+        add(C12, P[2], P[4], +1);
+        add(C21, P[1], P[3], +1);
+        add(C22, P[0], P[2], +1); add(C22, C22, P[1], -1); add(C22, C22, P[5], +1);
+        ws_top = mark;
+        return ok;
+    }
+
+    // Alg. 3 with the BDPZ 22-operation form (Sec. 2.3): 4 S, 4 T and 7 P temporaries per
+    // level; the U chain reuses the P blocks once they are consumed.
+    bool alloc_winograd(View a, View b, View c, int L) {
+        View A11 = quad(a, 0), A12 = quad(a, 1), A21 = quad(a, 2), A22 = quad(a, 3);
+        View B11 = quad(b, 0), B12 = quad(b, 1), B21 = quad(b, 2), B22 = quad(b, 3);
+        View C11 = quad(c, 0), C12 = quad(c, 1), C21 = quad(c, 2), C22 = quad(c, 3);
+        const size_t mark = ws_top;
+        View S1 = talloc(A11.rows, A11.cols), S2 = talloc(A11.rows, A11.cols), S3 = talloc(A11.rows, A11.cols),
+             S4 = talloc(A11.rows, A11.cols);
+        View T1 = talloc(B11.rows, B11.cols), T2 = talloc(B11.rows, B11.cols), T3 = talloc(B11.rows, B11.cols),
+             T4 = talloc(B11.rows, B11.cols);
+        View P[7];
+        for (int i = 0; i < 7; ++i) P[i] = talloc(C11.rows, C11.cols);
+        bool ok = true;
+        add(S1, A21, A22, +1);
+        add(S2, S1, A11, -1);
+        add(S3, A11, A21, -1);
+        add(T1, B12, B11, -1);
+        add(T2, B22, T1, -1);
+        add(T3, B22, B12, -1);
+        add(S4, A12, S2, -1);
+        add(T4, T2, B21, -1);
+        ok &= product(A11, B11, P[0], L - 1);
+        ok &= product(A12, B21, P[1], L - 1);
+        ok &= product(S4, B22, P[2], L - 1);
+        ok &= product(A22, T4, P[3], L - 1);
+        ok &= product(S1, T1, P[4], L - 1);
+        ok &= product(S2, T2, P[5], L - 1);
+        ok &= product(S3, T3, P[6], L - 1);
+        add(C11, P[0], P[1], +1);  // U1 = P1 + P2
+        add(P[5], P[0], P[5], +1); // U2 = P1 + P6
+        add(P[6], P[5], P[6], +1); // U3 = U2 + P7
+        add(P[0], P[5], P[4], +1); // U4 = U2 + P5
+        add(C12, P[0], P[2], +1);  // U5 = U4 + P3
+        add(C21, P[6], P[3], -1);  // U6 = U3 - P4
+        add(C22, P[6], P[4], +1);  // U7 = U3 + P5
+        ws_top = mark;
+        return ok;
+    }
+
+    // Table 2 (Sec. 3.3): two temporaries per level, X (A-quadrant sums, then P1) and Y.
+    bool two_temp(View a, View b, View c, int L) {
+        View A11 = quad(a, 0), A12 = quad(a, 1), A21 = quad(a, 2), A22 = quad(a, 3);
+        View B11 = quad(b, 0), B12 = quad(b, 1), B21 = quad(b, 2), B22 = quad(b, 3);
+        View C11 = quad(c, 0), C12 = quad(c, 1), C21 = quad(c, 2), C22 = quad(c, 3);
+        const int m2 = A11.rows, k2 = A11.cols, n2 = B11.cols;
+        const size_t mark = ws_top;
+        View X = talloc(m2, std::max(k2, n2));
+        X.cols = k2;                       // X as an A-quadrant sum
+        View Xp = X;
+        Xp.cols = n2;
+        Xp.ld = round_up(std::max(n2, 1), 4);  // X as P1 (m2 x n2)
+        X.ld = round_up(std::max(k2, 1), 4);
+        View Y = talloc(k2, n2);
+        bool ok = true;
+        add(X, A11, A21, -1);                  //  1  S3 = A11 - A21      -> X
+        add(Y, B22, B12, -1);                  //  2  T3 = B22 - B12      -> Y
+        ok &= product(X, Y, C21, L - 1);       //  3  P7 = S3 T3          -> C21
+        add(X, A21, A22, +1);                  //  4  S1 = A21 + A22      -> X
+        add(Y, B12, B11, -1);                  //  5  T1 = B12 - B11      -> Y
+        ok &= product(X, Y, C22, L - 1);       //  6  P5 = S1 T1          -> C22
+        add(X, X, A11, -1);                    //  7  S2 = S1 - A11       -> X
+        add(Y, B22, Y, -1);                    //  8  T2 = B22 - T1       -> Y
+        ok &= product(X, Y, C12, L - 1);       //  9  P6 = S2 T2          -> C12
+        add(X, A12, X, -1);                    // 10  S4 = A12 - S2       -> X
+        ok &= product(X, B22, C11, L - 1);     // 11  P3 = S4 B22         -> C11
+        ok &= product(A11, B11, Xp, L - 1);    // 12  P1 = A11 B11        -> X
+        add(C12, Xp, C12, +1);                 // 13  U2 = P1 + P6        -> C12
+        add(C21, C12, C21, +1);                // 14  U3 = U2 + P7        -> C21
+        add(C12, C12, C22, +1);                // 15  U4 = U2 + P5        -> C12
+        add(C22, C21, C22, +1);                // 16  U7 = U3 + P5        -> C22
+        add(C12, C12, C11, +1);                // 17  U5 = U4 + P3        -> C12
+        add(Y, Y, B21, -1);                    // 18  T4 = T2 - B21       -> Y
+        ok &= product(A22, Y, C11, L - 1);     // 19  P4 = A22 T4         -> C11
+        add(C21, C21, C11, -1);                // 20  U6 = U3 - P4        -> C21
+        ok &= product(A12, B21, C11, L - 1);   // 21  P2 = A12 B21        -> C11
+        add(C11, Xp, C11, +1);                 // 22  U1 = P1 + P2        -> C11
+        ws_top = mark;
+        return ok;
+    }
+
+    // Table 3 (Sec. 3.3): temporaries stored in the quadrants of A, B and C.  Sub-products
+    // recurse in place too, so each one may overwrite its two operand blocks; the table's
+    // order never reads a block after such a product consumed it.
+    bool in_place(View a, View b, View c, int L) {
+        View A11 = quad(a, 0), A12 = quad(a, 1), A21 = quad(a, 2), A22 = quad(a, 3);
+        View B11 = quad(b, 0), B12 = quad(b, 1), B21 = quad(b, 2), B22 = quad(b, 3);
+        View C11 = quad(c, 0), C12 = quad(c, 1), C21 = quad(c, 2), C22 = quad(c, 3);
+        bool ok = true;
+        add(C11, A11, A21, -1);                //  1  S3 = A11 - A21      -> C11
+        add(A21, A21, A22, +1);                //  2  S1 = A21 + A22      -> A21
+        add(C22, B12, B11, -1);                //  3  T1 = B12 - B11      -> C22
+        add(B12, B22, B12, -1);                //  4  T3 = B22 - B12      -> B12
+        ok &= product(C11, B12, C21, L - 1);   //  5  P7 = S3 T3          -> C21
+        add(C12, A21, A11, -1);                //  6  S2 = S1 - A11       -> C12
+        ok &= product(A11, B11, C11, L - 1);   //  7  P1 = A11 B11        -> C11
+        add(B11, B22, C22, -1);                //  8  T2 = B22 - T1       -> B11
+        ok &= product(A21, C22, A11, L - 1);   //  9  P5 = S1 T1          -> A11
+        add(C22, B11, B21, -1);                // 10  T4 = T2 - B21       -> C22
+        ok &= product(A22, C22, A21, L - 1);   // 11  P4 = A22 T4         -> A21
+        add(A22, A12, C12, -1);                // 12  S4 = A12 - S2       -> A22
+        ok &= product(C12, B11, C22, L - 1);   // 13  P6 = S2 T2          -> C22
+        add(C22, C11, C22, +1);                // 14  U2 = P1 + P6        -> C22
+        ok &= product(A12, B21, C12, L - 1);   // 15  P2 = A12 B21        -> C12
+        add(C11, C11, C12, +1);                // 16  U1 = P1 + P2        -> C11
+        add(C12, C22, A11, +1);                // 17  U4 = U2 + P5        -> C12
+        add(C22, C22, C21, +1);                // 18  U3 = U2 + P7        -> C22
+        add(C21, C22, A21, -1);                // 19  U6 = U3 - P4        -> C21
+        add(C22, C22, A11, +1);                // 20  U7 = U3 + P5        -> C22
+        ok &= product(A22, B22, A12, L - 1);   // 21  P3 = S4 B22         -> A12
+        add(C12, C12, A12, +1);                // 22  U5 = U4 + P3        -> C12
+        return ok;
+    }
+
+    // ---------------------------------------------------------- FUSED
+    // Per-level coefficient tables of the 7 products.
+    struct Term { int q; int s; };  // quadrant (0:11 1:12 2:21 3:22), sign
+    struct ProdTab {
+        int pure_a_q[7];  // quadrant of A if the A operand is a single block, else -1
+        int pure_b_q[7];
+        int ntgt[7];
+        Term tgt[7][4];
+    };
+
+    static const ProdTab& table(int algo) {
+        // Winograd, BDPZ (Sec. 2.3): C11 = U1 = P1+P2, C12 = U5 = P1+P6+P5+P3,
+        // C21 = U6 = P1+P6+P7-P4, C22 = U7 = P1+P6+P7+P5.
+        static const ProdTab win = {
+            {0, 1, -1, 3, -1, -1, -1},
+            {0, 2, 3, -1, -1, -1, -1},
+            {4, 1, 1, 1, 2, 3, 2},
+            {{{0, 1}, {1, 1}, {2, 1}, {3, 1}},
+             {{0, 1}},
+             {{1, 1}},
+             {{2, -1}},
+             {{1, 1}, {3, 1}},
+             {{1, 1}, {2, 1}, {3, 1}},
+             {{2, 1}, {3, 1}}}};
+        // Strassen (Sec. 2.2): C11 = P1+P4-P5+P7, C12 = P3+P5, C21 = P2+P4, C22 = P1+P3-P2+P6.
+        static const ProdTab str = {
+            {-1, -1, 0, 3, -1, -1, -1},
+            {-1, 0, -1, -1, 3, -1, -1},
+            {2, 2, 2, 2, 2, 1, 1},
+            {{{0, 1}, {3, 1}},
+             {{2, 1}, {3, -1}},
+             {{1, 1}, {3, 1}},
+             {{0, 1}, {2, 1}},
+             {{0, -1}, {1, 1}},
+             {{3, 1}},
+             {{0, 1}}}};
+        return algo == SW_ALGO_STRASSEN ? str : win;
+    }
+
+    // FUSED plan for C (m x n) <- A (m x k) B (k x n) at depth L (1..3).
+    bool fused(View A, View B, View C, int L) {
+        const ProdTab& T = table(algo);
+        const int m = C.rows, n = C.cols, k = A.cols;
+        const int s = 1 << L;
+        const int mb = (int)ceil_div(m, s);
+        const int kb = eb == 4 ? (int)round_up(ceil_div(k, s), tf32_tile_k()) : (int)ceil_div(k, s);
+        const int nb = eb == 4 ? (int)round_up(ceil_div(n, s), 4) : (int)ceil_div(n, s);
+        int nleaf = 1;
+        for (int i = 0; i < L; ++i) nleaf *= 7;
+        std::vector<short> slot_a(nleaf, -1), slot_b(nleaf, -1);
+        std::vector<int> ar(nleaf), ac(nleaf), br(nleaf), bc(nleaf);
+        int na = 0, nbs = 0;
+        for (int w = 0; w < nleaf; ++w) {
+            bool pa = true, pb = true;
+            int r_a = 0, c_a = 0, r_b = 0, c_b = 0;
+            for (int l = 0, ww = w, div = nleaf / 7; l < L; ++l, div /= 7) {
+                const int p = (ww / div) % 7;
+                const int qa = T.pure_a_q[p], qb = T.pure_b_q[p];
+                if (qa < 0) pa = false;
+                if (qb < 0) pb = false;
+                r_a = r_a * 2 + (qa >= 0 ? (qa >> 1) : 0);
+                c_a = c_a * 2 + (qa >= 0 ? (qa & 1) : 0);
+                r_b = r_b * 2 + (qb >= 0 ? (qb >> 1) : 0);
+                c_b = c_b * 2 + (qb >= 0 ? (qb & 1) : 0);
+            }
+            if (pa) { ar[w] = r_a * mb; ac[w] = c_a * kb; } else { slot_a[w] = (short)na++; }
+            if (pb) { br[w] = r_b * kb; bc[w] = c_b * nb; } else { slot_b[w] = (short)nbs++; }
+        }
+        // scratch for the materialised operand sums
+        const size_t mark = ws_top;
+        View SA = talloc(std::max(na, 1) * mb, kb);
+        View SB = talloc(std::max(nbs, 1) * kb, nb);
+        SA.rows = na * mb;
+        SB.rows = nbs * kb;
+        SA.ld = kb;  // slots are dense: row stride = block width (the pre-add pass writes so)
+        SB.ld = nb;
+        if (dry) { ws_top = mark; return true; }
+        if (na > 0) {
+            Op o;
+            o.kind = OP_PREADD;
+            o.eb = eb;
+            PreaddArgs& p = o.pre;
+            memset(&p, 0, sizeof(p));
+            p.x = A.p; p.ldx = A.ld; p.rows = m; p.cols = k; p.brows = mb; p.bcols = kb;
+            p.out = SA.p; p.L = L; p.alg = algo == SW_ALGO_STRASSEN ? 1 : 2; p.bside = 0;
+            for (int w = 0; w < 343; ++w) p.slot_of[w] = w < nleaf ? slot_a[w] : (short)-1;
+            plan->ops.push_back(o);
+        }
+        if (nbs > 0) {
+            Op o;
+            o.kind = OP_PREADD;
+            o.eb = eb;
+            PreaddArgs& p = o.pre;
+            memset(&p, 0, sizeof(p));
+            p.x = B.p; p.ldx = B.ld; p.rows = k; p.cols = n; p.brows = kb; p.bcols = nb;
+            p.out = SB.p; p.L = L; p.alg = algo == SW_ALGO_STRASSEN ? 1 : 2; p.bside = 1;
+            for (int w = 0; w < 343; ++w) p.slot_of[w] = w < nleaf ? slot_b[w] : (short)-1;
+            plan->ops.push_back(o);
+        }
+        memset0(C);
+        // leaves (leaf-major order) and their Kronecker-product targets
+        std::vector<Leaf> leaves;
+        std::vector<Target> tg;
+        int items = 0;
+        const int tm_sz = eb == 4 ? tf32_tile_m() : F64_BM;
+        const int bn = eb == 4 ? (nb <= 128 ? 128 : 256) : F64_BN;
+        for (int w = 0; w < nleaf; ++w) {
+            Leaf lf;
+            memset(&lf, 0, sizeof(lf));
+            if (slot_a[w] < 0) { lf.a_map = 0; lf.a_row = ar[w]; lf.a_col = ac[w]; }
+            else { lf.a_map = 2; lf.a_row = slot_a[w] * mb; lf.a_col = 0; }
+            if (slot_b[w] < 0) { lf.b_map = 1; lf.b_row = br[w]; lf.b_col = bc[w]; }
+            else { lf.b_map = 3; lf.b_row = slot_b[w] * kb; lf.b_col = 0; }
+            lf.m = mb;
+            lf.n = nb;
+            lf.kblocks = eb == 4 ? kb / tf32_tile_k() : kb;
+            lf.tiles_n = (int)ceil_div(nb, bn);
+            lf.tile_begin = items;
+            lf.tgt_begin = (int)tg.size();
+            // enumerate target combinations over the levels
+            int digits[3] = {0, 0, 0};
+            for (int l = 0, div = nleaf / 7; l < L; ++l, div /= 7) digits[l] = (w / div) % 7;
+            int idx[3] = {0, 0, 0};
+            for (;;) {
+                int r = 0, c = 0;
+                float sg = 1.f;
+                for (int l = 0; l < L; ++l) {
+                    const Term t = T.tgt[digits[l]][idx[l]];
+                    r = r * 2 + (t.q >> 1);
+                    c = c * 2 + (t.q & 1);
+                    sg *= (float)t.s;
+                }
+                Target t;
+                t.c = C.p + ((long long)r * mb * C.ld + (long long)c * nb) * eb;
+                t.ldc = C.ld;
+                t.rows = std::min(mb, m - r * mb);
+                t.cols = std::min(nb, n - c * nb);
+                t.sign = sg;
+                t.mode = TGT_ATOMIC;
+                t.vec_ok = 0;
+                t.pad_ = 0;
+                View tv = {static_cast<char*>(t.c), C.ld, 0, 0};
+                t.vec_ok = vec_ok(tv) ? 1 : 0;
+                if (t.rows > 0 && t.cols > 0) tg.push_back(t);
+                int l = L - 1;
+                while (l >= 0 && ++idx[l] == T.ntgt[digits[l]]) { idx[l] = 0; --l; }
+                if (l < 0) break;
+            }
+            lf.tgt_count = (int)tg.size() - lf.tgt_begin;
+            leaves.push_back(lf);
+            items += (int)ceil_div(mb, tm_sz) * lf.tiles_n;
+        }
+        Op o;
+        o.nleaves = (int)leaves.size();
+        o.items = items;
+        o.leaves_off = put_blob(leaves.data(), leaves.size() * sizeof(Leaf));
+        o.targets_off = put_blob(tg.data(), tg.size() * sizeof(Target));
+        if (eb == 4) {
+            o.kind = OP_GEMM_TF32;
+            o.bn = bn;
+            if (!make_map_f32(&o.maps.m[0], A.p, m, k, A.ld, 32, tf32_tile_m()) ||
+                !make_map_f32(&o.maps.m[1], B.p, k, n, B.ld, 32, 32) ||
+                !make_map_f32(&o.maps.m[2], SA.p, std::max(SA.rows, 1), kb, SA.ld, 32, tf32_tile_m()) ||
+                !make_map_f32(&o.maps.m[3], SB.p, std::max(SB.rows, 1), nb, SB.ld, 32, 32)) {
+                err = "tensor map encoding failed";
+                return false;
+            }
+        } else {
+            o.kind = OP_GEMM_F64;
+            MatRef refs[4] = {{A.p, A.ld, m, k}, {B.p, B.ld, k, n}, {SA.p, SA.ld, SA.rows, kb},
+                              {SB.p, SB.ld, SB.rows, nb}};
+            o.refs_off = put_blob(refs, sizeof(refs));
+        }
+        plan->ops.push_back(o);
+        return true;
+    }
+};
+
+}  // namespace
+
+// ====================================================================== handle
+struct sw_handle_s {
+    int device = 0;
+    int sms = 148;
+    size_t budget = 0;
+    char* ws = nullptr;
+    size_t ws_bytes = 0;
+    int* d_err = nullptr;
+    unsigned long long* d_norms = nullptr;
+    std::string last_error;
+    std::unordered_map<std::string, Plan*> plans;
+    // device buffers of the host-operand entry point
+    char* io = nullptr;
+    size_t io_bytes = 0;
+    std::mutex mu;
+};
+
+static sw_status fail(sw_handle h, sw_status s, const std::string& msg) {
+    if (h) h->last_error = msg;
+    return s;
+}
+
+static sw_status cuda_fail(sw_handle h, cudaError_t e, const char* where) {
+    return fail(h, SW_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+static void flush_plans(sw_handle h) {
+    if (h->plans.empty()) return;
+    cudaDeviceSynchronize();
+    for (auto& kv : h->plans) delete kv.second;
+    h->plans.clear();
+}
+
+// Make the workspace at least `need` bytes (flushes cached plans, which point into it).
+static sw_status ensure_ws(sw_handle h, size_t need) {
+    if (need <= h->ws_bytes) return SW_OK;
+    if (h->budget && need > h->budget)
+        return fail(h, SW_EBUDGET, "workspace need " + std::to_string(need) + " B exceeds budget " +
+                                       std::to_string(h->budget) + " B");
+    flush_plans(h);
+    if (h->ws) { cudaDeviceSynchronize(); cudaFree(h->ws); h->ws = nullptr; h->ws_bytes = 0; }
+    size_t bytes = round_up((long long)need, 1 << 21);
+    if (h->budget && bytes > h->budget) bytes = need;
+    if (cudaMalloc(&h->ws, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(h, SW_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " B workspace failed");
+    }
+    h->ws_bytes = bytes;
+    return SW_OK;
+}
+
+static int resolve_depth(int m, int n, int k, int cutoff, uint32_t variant, int eb) {
+    if ((variant & SW_ALGO_MASK) == SW_ALGO_NAIVE) return 0;
+    if (cutoff <= 0) cutoff = eb == 4 ? 4096 : 64;  // tuned default: see the bench's sweep
+    int L = 0;
+    while (L < 20) {
+        const long long s = 1LL << L;
+        const long long lo = std::min(std::min(ceil_div(m, s), ceil_div(n, s)), ceil_div(k, s));
+        if (lo > cutoff) ++L; else break;
+    }
+    if ((variant & SW_SCHED_MASK) == SW_SCHED_FUSED && L > 3) L = 3;
+    return L;
+}
+
+// Build the whole plan for one product (planner dry-run for sizes, then the real one).
+static sw_status build_plan(sw_handle h, int eb, const void* A, int lda, const void* B, int ldb, void* C, int ldc,
+                            int m, int n, int k, int cutoff, uint32_t variant, bool dry, Plan* plan) {
+    const uint32_t algo = variant & SW_ALGO_MASK, sched = variant & SW_SCHED_MASK, odd = variant & SW_ODD_MASK;
+    if (algo > SW_ALGO_WINOGRAD) return fail(h, SW_EINVAL, "unknown algorithm bits");
+    if (sched > SW_SCHED_ALLOC) return fail(h, SW_EINVAL, "unknown schedule bits");
+    if ((variant & SW_LEAF_MASK) != SW_LEAF_TF32 && eb == 4)
+        return fail(h, SW_EUNSUPPORTED, "leaf kind not built yet");
+    if (algo == SW_ALGO_STRASSEN && (sched == SW_SCHED_TWO_TEMP || sched == SW_SCHED_IN_PLACE))
+        return fail(h, SW_EUNSUPPORTED, "Tables 2 and 3 are Winograd schedules");
+    if (sched == SW_SCHED_IN_PLACE && algo != SW_ALGO_NAIVE && !(m == n && n == k))
+        return fail(h, SW_EUNSUPPORTED, "in-place schedule needs m == n == k");
+
+    Planner P;
+    P.eb = eb;
+    P.variant = variant;
+    P.dry = dry;
+    P.ws_base = h->ws;
+    P.plan = plan;
+    P.sched = (int)sched;
+    P.algo = (int)algo;
+    const int L = resolve_depth(m, n, k, cutoff, variant, eb);
+    plan->depth = L;
+
+    View Av = {(char*)A, lda, m, k}, Bv = {(char*)B, ldb, k, n}, Cv = {(char*)C, ldc, m, n};
+    const bool aligned = eb == 8 || (Planner::vec_ok(Av) && Planner::vec_ok(Bv) && Planner::vec_ok(Cv));
+    bool ok = true;
+    if (m == 0 || n == 0) {
+        ok = true;
+    } else if (k == 0) {
+        P.memset0(Cv);
+    } else if (L == 0 || algo == SW_ALGO_NAIVE) {
+        if (aligned) {
+            ok = P.gemm(Av, Bv, Cv, TGT_STORE);
+        } else {  // pack into aligned workspace
+            View a2 = P.talloc(m, k), b2 = P.talloc(k, n), c2 = P.talloc(m, n);
+            P.copy_pad(a2, Av); P.copy_pad(b2, Bv);
+            ok = P.gemm(a2, b2, c2, TGT_STORE);
+            P.copy_pad(Cv, c2);
+        }
+    } else if (sched == SW_SCHED_FUSED) {
+        if (aligned) {
+            ok = P.fused(Av, Bv, Cv, L);
+        } else {
+            View a2 = P.talloc(m, k), b2 = P.talloc(k, n), c2 = P.talloc(m, n);
+            P.copy_pad(a2, Av); P.copy_pad(b2, Bv);
+            ok = P.fused(a2, b2, c2, L);
+            P.copy_pad(Cv, c2);
+        }
+    } else if (L > 5) {
+        return fail(h, SW_EUNSUPPORTED, "materialised schedules stop at depth 5 (7^5 leaf launches); raise the cutoff");
+    } else {
+        // materialised schedules: halve exactly; column splits must stay 16-byte aligned (FP32)
+        const long long gm = 1LL << L, gk = eb == 4 ? 4LL << L : 1LL << L, gn = gk;
+        const bool exact = m % gm == 0 && k % gk == 0 && n % gn == 0;
+        if (exact && aligned) {
+            ok = P.product(Av, Bv, Cv, L);
+        } else if (odd == SW_PEEL && aligned) {
+            long long me = m / gm * gm, ke = k / gk * gk, ne = n / gn * gn;
+            if (sched == SW_SCHED_IN_PLACE) { me = ke = ne = std::min(me, std::min(ke, ne)); }
+            auto sub = [&](View v, long long r0, long long c0, long long rows, long long cols) {
+                View s = v;
+                s.p = v.p + (r0 * v.ld + c0) * eb;
+                s.rows = (int)rows;
+                s.cols = (int)cols;
+                return s;
+            };
+            // edge products first: they read the even blocks, which IN_PLACE overwrites
+            if (me < m) ok &= P.gemm(sub(Av, me, 0, m - me, k), Bv, sub(Cv, me, 0, m - me, n), TGT_STORE);
+            if (ne < n) ok &= P.gemm(sub(Av, 0, 0, me, k), sub(Bv, 0, ne, k, n - ne), sub(Cv, 0, ne, me, n - ne),
+                                     TGT_STORE);
+            if (me > 0 && ne > 0) {
+                if (ke > 0) ok &= P.product(sub(Av, 0, 0, me, ke), sub(Bv, 0, 0, ke, ne), sub(Cv, 0, 0, me, ne), L);
+                else P.memset0(sub(Cv, 0, 0, me, ne));
+                if (ke < k)
+                    ok &= P.gemm(sub(Av, 0, ke, me, k - ke), sub(Bv, ke, 0, k - ke, ne), sub(Cv, 0, 0, me, ne),
+                                 ke > 0 ? TGT_ADD : TGT_STORE);
+            }
+        } else {
+            // pad into aligned copies whose sizes halve exactly L times
+            const int mp = (int)round_up(m, gm), kp = (int)round_up(k, gk), np = (int)round_up(n, gn);
+            const int sq = (int)round_up(std::max(m, std::max(k, n)), std::max(gm, gk));
+            View a2 = P.talloc(sched == SW_SCHED_IN_PLACE ? sq : mp, sched == SW_SCHED_IN_PLACE ? sq : kp);
+            View b2 = P.talloc(sched == SW_SCHED_IN_PLACE ? sq : kp, sched == SW_SCHED_IN_PLACE ? sq : np);
+            View c2 = P.talloc(sched == SW_SCHED_IN_PLACE ? sq : mp, sched == SW_SCHED_IN_PLACE ? sq : np);
+            P.copy_pad(a2, Av); P.copy_pad(b2, Bv);
+            ok = P.product(a2, b2, c2, L);
+            View cv = c2;
+            cv.rows = m;
+            cv.cols = n;
+            P.copy_pad(Cv, cv);
+        }
+    }
+    if (!ok) return fail(h, SW_ECUDA, P.err.empty() ? "planning failed" : P.err);
+    plan->ws_need = P.ws_peak;
+    return SW_OK;
+}
+
+static sw_status run_plan(sw_handle h, Plan* plan, cudaStream_t s) {
+    char* blob = static_cast<char*>(plan->d_blob);
+    for (const Op& o : plan->ops) {
+        cudaError_t e = cudaSuccess;
+        switch (o.kind) {
+            case OP_GEMM_TF32:
+                e = launch_gemm_tf32(o.bn, o.maps, nullptr, reinterpret_cast<const Leaf*>(blob + o.leaves_off),
+                                     o.nleaves, reinterpret_cast<const Target*>(blob + o.targets_off), o.items,
+                                     h->d_err, h->sms, s);
+                break;
+            case OP_GEMM_F64:
+                e = launch_gemm_f64(reinterpret_cast<const MatRef*>(blob + o.refs_off),
+                                    reinterpret_cast<const Leaf*>(blob + o.leaves_off), o.nleaves,
+                                    reinterpret_cast<const Target*>(blob + o.targets_off), o.items, h->sms * 8, s);
+                break;
+            case OP_ADDSUB:
+                e = launch_addsub(o.eb, o.rows, o.cols, o.z, o.ldz, o.x, o.ldx, o.y, o.ldy, o.sy, s);
+                break;
+            case OP_COPY_PAD:
+                e = launch_copy_pad(o.eb, o.rows, o.cols, o.z, o.ldz, o.x, o.ldx, o.src_rows, o.src_cols, s);
+                break;
+            case OP_PREADD:
+                e = launch_preadd(o.eb, o.pre, s);
+                break;
+            case OP_MEMSET:
+                e = cudaMemset2DAsync(o.z, (size_t)o.ldz * o.eb, 0, (size_t)o.cols * o.eb, (size_t)o.rows, s);
+                break;
+        }
+        if (e != cudaSuccess) return cuda_fail(h, e, "kernel launch");
+    }
+    return SW_OK;
+}
+
+static sw_status do_mm(sw_handle h, int eb, const void* A, int lda, const void* B, int ldb, void* C, int ldc, int m,
+                       int n, int k, int cutoff, uint32_t variant, void* stream) {
+    if (!h) return SW_EINVAL;
+    if (m < 0 || n < 0 || k < 0) return fail(h, SW_EINVAL, "negative dimension");
+    if ((m && k && !A) || (k && n && !B) || (m && n && !C)) return fail(h, SW_EINVAL, "null matrix pointer");
+    if ((m && k && lda < std::max(k, 1)) || (k && n && ldb < std::max(n, 1)) || (m && n && ldc < std::max(n, 1)))
+        return fail(h, SW_EINVAL, "leading dimension smaller than the row length");
+    std::lock_guard<std::mutex> lock(h->mu);
+    cudaSetDevice(h->device);
+    char key[256];
+    snprintf(key, sizeof(key), "%d|%p|%d|%p|%d|%p|%d|%d|%d|%d|%d|%u", eb, A, lda, B, ldb, C, ldc, m, n, k, cutoff,
+             variant);
+    auto it = h->plans.find(key);
+    Plan* plan = nullptr;
+    if (it != h->plans.end()) {
+        plan = it->second;
+    } else {
+        Plan dryp;
+        sw_status st = build_plan(h, eb, A, lda, B, ldb, C, ldc, m, n, k, cutoff, variant, true, &dryp);
+        if (st != SW_OK) return st;
+        st = ensure_ws(h, dryp.ws_need);
+        if (st != SW_OK) return st;
+        plan = new Plan();
+        st = build_plan(h, eb, A, lda, B, ldb, C, ldc, m, n, k, cutoff, variant, false, plan);
+        if (st != SW_OK) { delete plan; return st; }
+        if (!plan->blob.empty()) {
+            if (cudaMalloc(&plan->d_blob, plan->blob.size()) != cudaSuccess) {
+                cudaGetLastError();
+                delete plan;
+                return fail(h, SW_ENOMEM, "descriptor allocation failed");
+            }
+            cudaMemcpy(plan->d_blob, plan->blob.data(), plan->blob.size(), cudaMemcpyHostToDevice);
+        }
+        if (h->plans.size() >= 256) flush_plans(h);
+        h->plans[key] = plan;
+    }
+    return run_plan(h, plan, static_cast<cudaStream_t>(stream));
+}
+
+// ====================================================================== C ABI
+extern "C" {
+
+sw_status sw_create(sw_handle* out, size_t budget) {
+    if (!out) return SW_EINVAL;
+    *out = nullptr;
+    sw_handle h = new sw_handle_s();
+    h->budget = budget;
+    if (cudaGetDevice(&h->device) != cudaSuccess) { cudaGetLastError(); delete h; return SW_ECUDA; }
+    cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (cudaMalloc(&h->d_err, 256) != cudaSuccess) { cudaGetLastError(); delete h; return SW_ENOMEM; }
+    cudaMemset(h->d_err, 0, 256);
+    h->d_norms = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(h->d_err) + 64);
+    if (!encode_fn()) { cudaFree(h->d_err); delete h; return SW_ECUDA; }
+    *out = h;
+    return SW_OK;
+}
+
+sw_status sw_destroy(sw_handle h) {
+    if (!h) return SW_EINVAL;
+    cudaSetDevice(h->device);
+    cudaDeviceSynchronize();
+    for (auto& kv : h->plans) delete kv.second;
+    h->plans.clear();
+    if (h->ws) cudaFree(h->ws);
+    if (h->io) cudaFree(h->io);
+    if (h->d_err) cudaFree(h->d_err);
+    delete h;
+    return SW_OK;
+}
+
+const char* sw_last_error(sw_handle h) { return h ? h->last_error.c_str() : "null handle"; }
+
+sw_status sw_mm_depth(int m, int n, int k, int cutoff, uint32_t variant, int elem_bytes, int* depth) {
+    if (!depth || m < 0 || n < 0 || k < 0 || (elem_bytes != 4 && elem_bytes != 8)) return SW_EINVAL;
+    *depth = resolve_depth(m, n, k, cutoff, variant, elem_bytes);
+    return SW_OK;
+}
+
+sw_status sw_mm_workspace_size(int m, int n, int k, int cutoff, uint32_t variant, int elem_bytes, size_t* bytes) {
+    if (!bytes || m < 0 || n < 0 || k < 0 || (elem_bytes != 4 && elem_bytes != 8)) return SW_EINVAL;
+    sw_handle_s tmp;
+    Plan p;
+    // sizes only: aligned dummy pointers and tight leading dimensions
+    char* d = reinterpret_cast<char*>(static_cast<uintptr_t>(1) << 20);
+    sw_status st = build_plan(&tmp, elem_bytes, d, std::max(k, 1), d, std::max(n, 1), d, std::max(n, 1), m, n, k,
+                              cutoff, variant, true, &p);
+    if (st != SW_OK) return st;
+    *bytes = p.ws_need;
+    return SW_OK;
+}
+
+sw_status sw_smm(sw_handle h, const float* A, int lda, const float* B, int ldb, float* C, int ldc, int m, int n,
+                 int k, int cutoff, uint32_t variant, void* stream) {
+    return do_mm(h, 4, A, lda, B, ldb, C, ldc, m, n, k, cutoff, variant, stream);
+}
+
+sw_status sw_dmm(sw_handle h, const double* A, int lda, const double* B, int ldb, double* C, int ldc, int m, int n,
+                 int k, int cutoff, uint32_t variant, void* stream) {
+    return do_mm(h, 8, A, lda, B, ldb, C, ldc, m, n, k, cutoff, variant, stream);
+}
+
+sw_status sw_smm_host(sw_handle h, const float* A, int lda, const float* B, int ldb, float* C, int ldc, int m, int n,
+                      int k, int cutoff, uint32_t variant, void* stream) {
+    if (!h) return SW_EINVAL;
+    if (m < 0 || n < 0 || k < 0 || (m && k && (!A || lda < k)) || (k && n && (!B || ldb < n)) ||
+        (m && n && (!C || ldc < n)))
+        return fail(h, SW_EINVAL, "bad host operand");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const long long lda2 = round_up(std::max(k, 1), 4), ldb2 = round_up(std::max(n, 1), 4), ldc2 = ldb2;
+    const size_t ba = (size_t)round_up((long long)m * lda2 * 4, 256), bb = (size_t)round_up((long long)k * ldb2 * 4, 256),
+                 bc = (size_t)round_up((long long)m * ldc2 * 4, 256);
+    {
+        std::lock_guard<std::mutex> lock(h->mu);
+        cudaSetDevice(h->device);
+        if (ba + bb + bc > h->io_bytes) {
+            flush_plans(h);
+            if (h->io) { cudaDeviceSynchronize(); cudaFree(h->io); h->io = nullptr; h->io_bytes = 0; }
+            if (cudaMalloc(&h->io, ba + bb + bc) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(h, SW_ENOMEM, "host-path buffers");
+            }
+            h->io_bytes = ba + bb + bc;
+        }
+    }
+    float* dA = reinterpret_cast<float*>(h->io);
+    float* dB = reinterpret_cast<float*>(h->io + ba);
+    float* dC = reinterpret_cast<float*>(h->io + ba + bb);
+    cudaError_t e = cudaSuccess;
+    if (m && k) e = cudaMemcpy2DAsync(dA, lda2 * 4, A, (size_t)lda * 4, (size_t)k * 4, m, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && k && n)
+        e = cudaMemcpy2DAsync(dB, ldb2 * 4, B, (size_t)ldb * 4, (size_t)n * 4, k, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "host to device copy");
+    sw_status st = sw_smm(h, dA, (int)lda2, dB, (int)ldb2, dC, (int)ldc2, m, n, k, cutoff, variant, stream);
+    if (st != SW_OK) return st;
+    if (m && n) e = cudaMemcpy2DAsync(C, (size_t)ldc * 4, dC, ldc2 * 4, (size_t)n * 4, m, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "device to host copy");
+    return sw_sync(h, stream);
+}
+
+sw_status sw_sync(sw_handle h, void* stream) {
+    if (!h) return SW_EINVAL;
+    cudaSetDevice(h->device);
+    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(h, e, "stream synchronize");
+    int code = 0;
+    e = cudaMemcpy(&code, h->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(h, e, "error word read");
+    if (code != 0) {
+        cudaMemset(h->d_err, 0, sizeof(int));
+        if (code == ERR_ALIGN) return fail(h, SW_ECUDA, "kernel rejected a misaligned TMA coordinate");
+        return fail(h, SW_ETIMEOUT, "bounded device wait expired (code " + std::to_string(code) + ")");
+    }
+    return SW_OK;
+}
+
+sw_status sw_error_norms(sw_handle h, int eb, int m, int n, int k, const void* A, int lda, const void* B, int ldb,
+                         const void* C, int ldc, const double* R, int ldr, double* out, void* stream) {
+    if (!h || !out || (eb != 4 && eb != 8) || m < 0 || n < 0 || k < 0) return fail(h, SW_EINVAL, "bad argument");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaSetDevice(h->device);
+    cudaError_t e = cudaMemsetAsync(h->d_norms, 0, 3 * sizeof(unsigned long long), s);
+    if (e == cudaSuccess)
+        e = launch_norms(eb, m, n, k, A, lda, B, ldb, C, ldc, R, ldr, h->d_norms, s);
+    unsigned long long bits[3] = {0, 0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(bits, h->d_norms, sizeof(bits), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "norms");
+    for (int i = 0; i < 3; ++i) memcpy(&out[i], &bits[i], sizeof(double));
+    return SW_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,300 @@
+// gemm_tf32.cu -- grouped leaf GEMM on the sm_103a tensor cores (tcgen05 + TMEM + TMA).
+//
+// Computes the leaf sub-products P = Aop * Bop of the recursion (Sec. 2.2 / 2.3; with a single
+// leaf and a single STORE target it is the plain product of Alg. 1) and adds sign * P into
+// each of the leaf's target blocks of C -- the post-additions folded into the epilogue.
+//
+// FP32 operands are staged by TMA into 128-byte-swizzled shared memory and consumed by
+// tcgen05.mma.kind::tf32 (the tensor core reads each FP32 operand as TF32: its 10 leading
+// mantissa bits); products accumulate in FP32 in tensor memory.
+//
+// CTA = 6 warps, persistent over work items (one item = one BM x BN output tile of one leaf):
+//   warp 0      TMA producer: A tile (BM x BK, K-major) + B tile (BK x BN, N-major) per stage
+//   warp 1      TMEM allocator + MMA issuer (one thread), BK/8 MMAs of K = 8 per stage
+//   warps 2..5  epilogue: tcgen05.ld 32 columns at a time, sign, store / add into the targets
+// Two TMEM accumulators (2 x BN columns) let the epilogue of tile i overlap the MMAs of i+1.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "plan.h"
+#include "ptx.cuh"
+#include "internal.h"
+
+namespace swk {
+
+constexpr int TF_BM = 128;
+constexpr int TF_BK = 32;  // 32 FP32 = 128 bytes: one swizzle row
+constexpr int TF_GROUP_M = 8;
+
+template <int BN>
+struct TfCfg {
+    static constexpr int STAGES = (BN == 256) ? 4 : 6;
+    static constexpr int A_BYTES = TF_BM * TF_BK * 4;   // 16 KB
+    static constexpr int B_BYTES = TF_BK * BN * 4;      // 32 KB (BN 256) / 16 KB (BN 128)
+    static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+    static constexpr int TMEM_COLS = 2 * BN;
+    static constexpr int BAR_OFF = STAGES * STAGE_BYTES;
+    static constexpr int SMEM_BYTES = BAR_OFF + 256 + 1024;  // + barriers + alignment slack
+    // instruction descriptor: D F32, A/B TF32, A K-major, B MN-major, N = BN, M = 128
+    static constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | (0u << 15) | (1u << 16) |
+                                      ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(TF_BM >> 4) << 24);
+};
+
+struct ItemPos {
+    int leaf, tm, tn;
+};
+
+__device__ __forceinline__ ItemPos decode_item(const Leaf* __restrict__ leaves, int nleaves, int item, int bn) {
+    int lo = 0, hi = nleaves - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&leaves[mid].tile_begin) <= item) lo = mid; else hi = mid - 1;
+    }
+    const Leaf* L = &leaves[lo];
+    int local = item - __ldg(&L->tile_begin);
+    int tiles_m = (__ldg(&L->m) + TF_BM - 1) / TF_BM;
+    int tiles_n = __ldg(&L->tiles_n);
+    int per_group = TF_GROUP_M * tiles_n;
+    int g = local / per_group;
+    int first_m = g * TF_GROUP_M;
+    int gsz = min(tiles_m - first_m, TF_GROUP_M);
+    int r = local - g * per_group;
+    ItemPos p;
+    p.leaf = lo;
+    p.tm = first_m + r % gsz;
+    p.tn = r / gsz;
+    (void)bn;
+    return p;
+}
+
+__device__ __forceinline__ const CUtensorMap* pick_map(const MapSet& maps, const CUtensorMap* gmaps, int idx) {
+    return gmaps ? gmaps + idx : &maps.m[idx];
+}
+
+// Epilogue store of 32 consecutive columns of one row into one target.
+__device__ __forceinline__ void store_row32(const Target& t, int row, int col0, const uint32_t (&r)[32]) {
+    if (row >= t.rows || col0 >= t.cols) return;
+    float* c = reinterpret_cast<float*>(t.c) + (long long)row * t.ldc + col0;
+    const float s = t.sign;
+    const int ncol = min(32, t.cols - col0);
+    if (t.vec_ok && ncol == 32) {
+        float4* c4 = reinterpret_cast<float4*>(c);
+#pragma unroll
+        for (int g = 0; g < 8; ++g) {
+            float4 v = make_float4(s * __uint_as_float(r[4 * g + 0]), s * __uint_as_float(r[4 * g + 1]),
+                                   s * __uint_as_float(r[4 * g + 2]), s * __uint_as_float(r[4 * g + 3]));
+            if (t.mode == TGT_STORE) {
+                c4[g] = v;
+            } else if (t.mode == TGT_ATOMIC) {
+                atomicAdd(&c4[g], v);
+            } else {
+                float4 o = c4[g];
+                o.x += v.x; o.y += v.y; o.z += v.z; o.w += v.w;
+                c4[g] = o;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            if (j < ncol) {
+                float v = s * __uint_as_float(r[j]);
+                if (t.mode == TGT_STORE) c[j] = v;
+                else if (t.mode == TGT_ATOMIC) atomicAdd(&c[j], v);
+                else c[j] += v;
+            }
+        }
+    }
+}
+
+template <int BN>
+__global__ void __launch_bounds__(192, 1)
+    gemm_tf32_kernel(const __grid_constant__ MapSet maps, const CUtensorMap* __restrict__ gmaps,
+                     const Leaf* __restrict__ leaves, int nleaves, const Target* __restrict__ targets,
+                     int total_items, int* err) {
+    using Cfg = TfCfg<BN>;
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw_addr = smem_u32(smem_raw);
+    const uint32_t base_addr = (raw_addr + 1023u) & ~1023u;
+    uint8_t* base = smem_raw + (base_addr - raw_addr);
+    uint8_t* sA = base;                                  // STAGES x A_BYTES
+    uint8_t* sB = base + Cfg::STAGES * Cfg::A_BYTES;     // STAGES x B_BYTES
+    uint64_t* bars = reinterpret_cast<uint64_t*>(base + Cfg::BAR_OFF);
+    uint64_t* full = bars;                       // [STAGES]
+    uint64_t* empty = bars + Cfg::STAGES;        // [STAGES]
+    uint64_t* tfull = bars + 2 * Cfg::STAGES;    // [2]
+    uint64_t* tempty = tfull + 2;                // [2]
+    uint64_t* done = tempty + 2;                 // [1]
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(done + 1);
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < Cfg::STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&tfull[a], 1);
+            mbar_init(&tempty[a], 4);
+        }
+        mbar_init(done, 1);
+        fence_mbar_init();
+    }
+    if (warp == 1) {
+        tmem_alloc(tmem_holder, Cfg::TMEM_COLS);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *reinterpret_cast<volatile uint32_t*>(tmem_holder);
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ TMA producer
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            int issued = 0;
+            bool ok = true;
+            for (int item = blockIdx.x; item < total_items && ok; item += gridDim.x) {
+                const ItemPos ip = decode_item(leaves, nleaves, item, BN);
+                const Leaf* L = &leaves[ip.leaf];
+                const CUtensorMap* ma = pick_map(maps, gmaps, __ldg(&L->a_map));
+                const CUtensorMap* mb = pick_map(maps, gmaps, __ldg(&L->b_map));
+                const int a_row = __ldg(&L->a_row) + ip.tm * TF_BM;
+                const int a_col = __ldg(&L->a_col);
+                const int b_row = __ldg(&L->b_row);
+                const int b_col = __ldg(&L->b_col) + ip.tn * BN;
+                const int kb_n = __ldg(&L->kblocks);
+                if (((a_col | b_col) & 3) != 0) {  // TMA x coordinate must be 16-byte aligned
+                    set_error(err, ERR_ALIGN);
+                    ok = false;
+                    break;
+                }
+                for (int kb = 0; kb < kb_n; ++kb) {
+                    if (!mbar_wait(&empty[stage], phase ^ 1u, err, ERR_WAIT_EMPTY)) { ok = false; break; }
+                    mbar_arrive_expect_tx(&full[stage], Cfg::STAGE_BYTES);
+                    uint8_t* dA = sA + stage * Cfg::A_BYTES;
+                    uint8_t* dB = sB + stage * Cfg::B_BYTES;
+                    tma_load_2d(dA, ma, &full[stage], a_col + kb * TF_BK, a_row);
+#pragma unroll
+                    for (int c = 0; c < BN / 32; ++c)
+                        tma_load_2d(dB + c * (TF_BK * 128), mb, &full[stage], b_col + c * 32, b_row + kb * TF_BK);
+                    ++issued;
+                    if (++stage == Cfg::STAGES) { stage = 0; phase ^= 1u; }
+                }
+            }
+            // drain: every issued copy must have landed before the CTA may exit
+            int s = stage;
+            uint32_t ph = phase;
+            for (int i = 0; i < min(issued, Cfg::STAGES); ++i) {
+                if (--s < 0) { s = Cfg::STAGES - 1; ph ^= 1u; }
+                mbar_wait(&full[s], ph, err, ERR_WAIT_DRAIN);
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            int local = 0;
+            bool ok = true;
+            for (int item = blockIdx.x; item < total_items && ok; item += gridDim.x, ++local) {
+                const ItemPos ip = decode_item(leaves, nleaves, item, BN);
+                const int kb_n = __ldg(&leaves[ip.leaf].kblocks);
+                const int acc = local & 1;
+                const uint32_t acc_phase = (local >> 1) & 1;
+                if (!mbar_wait(&tempty[acc], acc_phase ^ 1u, err, ERR_WAIT_ACC_FREE)) { ok = false; break; }
+                tc_fence_after();
+                const uint32_t d_tmem = tmem_base + (uint32_t)(acc * BN);
+                for (int kb = 0; kb < kb_n; ++kb) {
+                    if (!mbar_wait(&full[stage], phase, err, ERR_WAIT_FULL)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t a_addr = smem_u32(sA + stage * Cfg::A_BYTES);
+                    const uint32_t b_addr = smem_u32(sB + stage * Cfg::B_BYTES);
+#pragma unroll
+                    for (int kk = 0; kk < TF_BK / 8; ++kk) {
+                        const uint64_t ad = make_sdesc(a_addr + kk * 32, 16, 1024, SWZ_128B);
+                        const uint64_t bd = make_sdesc(b_addr + kk * 1024, TF_BK * 128, 1024, SWZ_128B);
+                        mma_tf32(d_tmem, ad, bd, Cfg::IDESC, (kb | kk) != 0 ? 1u : 0u);
+                    }
+                    mma_commit(&empty[stage]);  // stage is free once these MMAs have read it
+                    if (++stage == Cfg::STAGES) { stage = 0; phase ^= 1u; }
+                }
+                if (!ok) break;
+                mma_commit(&tfull[acc]);  // accumulator ready for the epilogue
+            }
+            // drain: all MMAs issued by this thread must finish before TMEM is released
+            mma_commit(done);
+            mbar_wait(done, 0, err, ERR_WAIT_DRAIN);
+        }
+    } else {
+        // ------------------------------------------------------------ epilogue (warps 2..5)
+        const int q = warp & 3;  // TMEM lane quarter this warp may access
+        int local = 0;
+        for (int item = blockIdx.x; item < total_items; item += gridDim.x, ++local) {
+            const ItemPos ip = decode_item(leaves, nleaves, item, BN);
+            const Leaf* L = &leaves[ip.leaf];
+            const int acc = local & 1;
+            const uint32_t acc_phase = (local >> 1) & 1;
+            if (!mbar_wait(&tfull[acc], acc_phase, err, ERR_WAIT_ACC)) break;
+            tc_fence_after();
+            const int tb = __ldg(&L->tgt_begin), tc = __ldg(&L->tgt_count);
+            const int row = ip.tm * TF_BM + q * 32 + lane;
+            const uint32_t t_base = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN);
+#pragma unroll 1
+            for (int chunk = 0; chunk < BN / 32; ++chunk) {
+                uint32_t r[32];
+                tmem_ld32(t_base + chunk * 32, r);
+                tmem_ld_wait();
+                const int col0 = ip.tn * BN + chunk * 32;
+                for (int t = 0; t < tc; ++t) {
+                    Target tg = targets[tb + t];
+                    store_row32(tg, row, col0, r);
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[acc]);
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem_base, Cfg::TMEM_COLS);
+    }
+}
+
+template <int BN>
+static cudaError_t launch_tf32_impl(const MapSet& maps, const CUtensorMap* gmaps, const Leaf* leaves, int nleaves,
+                                    const Target* targets, int total_items, int* err, int grid,
+                                    cudaStream_t stream) {
+    using Cfg = TfCfg<BN>;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(gemm_tf32_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             Cfg::SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    if (total_items <= 0) return cudaSuccess;
+    if (grid > total_items) grid = total_items;
+    gemm_tf32_kernel<BN><<<grid, 192, Cfg::SMEM_BYTES, stream>>>(maps, gmaps, leaves, nleaves, targets,
+                                                                  total_items, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_tf32(int bn, const MapSet& maps, const CUtensorMap* gmaps, const Leaf* leaves, int nleaves,
+                             const Target* targets, int total_items, int* err, int grid, cudaStream_t stream) {
+    if (bn == 256) return launch_tf32_impl<256>(maps, gmaps, leaves, nleaves, targets, total_items, err, grid, stream);
+    return launch_tf32_impl<128>(maps, gmaps, leaves, nleaves, targets, total_items, err, grid, stream);
+}
+
+int tf32_tile_m() { return TF_BM; }
+int tf32_tile_k() { return TF_BK; }
+
+}  // namespace swk

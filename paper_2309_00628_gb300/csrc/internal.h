@@ -1,0 +1,62 @@
+// internal.h -- launchers shared between the kernels and the host planner (not part of the ABI).
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "plan.h"
+
+namespace swk {
+
+// Up to four tensor maps passed by value (__grid_constant__): A, B and the two operand-sum
+// scratch matrices of one product.
+struct MapSet {
+    CUtensorMap m[4];
+};
+
+// A strided matrix view with its valid extent (reads beyond it return 0).
+struct MatRef {
+    const void* p;
+    long long ld;
+    int rows, cols;
+};
+
+// Leaf for the pointer-based (FP64) kernels: operands are MatRef indices.
+cudaError_t launch_gemm_tf32(int bn, const MapSet& maps, const CUtensorMap* gmaps, const Leaf* leaves, int nleaves,
+                             const Target* targets, int total_items, int* err, int grid, cudaStream_t stream);
+int tf32_tile_m();
+int tf32_tile_k();
+
+// FP64 SIMT leaf GEMM: same leaf / target descriptors, a_map / b_map index `refs`.
+cudaError_t launch_gemm_f64(const MatRef* refs, const Leaf* leaves, int nleaves, const Target* targets,
+                            int total_items, int grid, cudaStream_t stream);
+constexpr int F64_BM = 64, F64_BN = 64;
+
+// Z = X + sy * Y elementwise on strided views (FP32 or FP64 per elem_bytes).
+cudaError_t launch_addsub(int elem_bytes, int rows, int cols, void* z, long long ldz, const void* x, long long ldx,
+                          const void* y, long long ldy, float sy, cudaStream_t stream);
+
+// Z = X (strided 2-D copy with zero fill outside the source extent).
+cudaError_t launch_copy_pad(int elem_bytes, int rows, int cols, void* z, long long ldz, const void* x,
+                            long long ldx, int src_rows, int src_cols, cudaStream_t stream);
+
+// One pass over a 2^L x 2^L grid of blocks of X that writes every non-pure leaf operand sum
+// (all recursion levels at once) into `out` (slot s occupies rows [s*brows, (s+1)*brows),
+// leading dimension bcols).  alg: 1 Strassen, 2 Winograd.  bside: B-side coefficients.
+struct PreaddArgs {
+    const void* x;
+    long long ldx;
+    int rows, cols;      // real extent of X
+    int brows, bcols;    // leaf block extent
+    void* out;
+    int L, alg, bside;
+    short slot_of[343];  // leaf word -> output slot, -1 = pure (not written)
+};
+cudaError_t launch_preadd(int elem_bytes, const PreaddArgs& a, cudaStream_t stream);
+
+// Device reductions for the error metric (results are written to d_out[0..2] as doubles).
+cudaError_t launch_norms(int elem_bytes, int m, int n, int k, const void* A, long long lda, const void* B,
+                         long long ldb, const void* C, long long ldc, const double* R, long long ldr,
+                         unsigned long long* d_out, cudaStream_t stream);
+
+}  // namespace swk

@@ -1,0 +1,421 @@
+// kernels.cu -- HBM-bound passes and the FP64 leaf of the Strassen / Winograd recursion.
+//
+//  * addsub      Z = X +- Y on strided blocks: the block additions of Sec. 2.2 / 2.3 and the
+//                steps of Tables 2 and 3 (Sec. 3.3) when a schedule materialises them.
+//  * copy_pad    strided copy with zero fill (the padding of Sec. 3.1 when it must be real).
+//  * preadd      one pass over A (or B) that writes the operand sums of every recursion level
+//                at once: the S1..S4 / T1..T4 chains of the BDPZ form (Sec. 2.3) or Strassen's
+//                sums (Sec. 2.2), composed over L levels, for every leaf whose operand is not a
+//                plain block.
+//  * gemm_f64    register-tiled FP64 SIMT GEMM for the FP64 path's leaves (Alg. 1 per tile).
+//  * norms       FP64 max-reductions for max|C - R|, max|A|, max|B|.
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "internal.h"
+#include "plan.h"
+
+namespace swk {
+
+// ============================================================== addsub / copy
+template <typename T>
+__global__ void addsub_kernel(int rows, int cols, T* __restrict__ z, long long ldz, const T* __restrict__ x,
+                              long long ldx, const T* __restrict__ y, long long ldy, T sy) {
+    const long long total = (long long)rows * cols;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / cols), j = (int)(e - (long long)i * cols);
+        z[i * ldz + j] = x[i * ldx + j] + sy * y[i * ldy + j];
+    }
+}
+
+__global__ void addsub4_kernel(int rows, int cols4, float4* __restrict__ z, long long ldz4,
+                               const float4* __restrict__ x, long long ldx4, const float4* __restrict__ y,
+                               long long ldy4, float sy) {
+    const long long total = (long long)rows * cols4;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / cols4), j = (int)(e - (long long)i * cols4);
+        const float4 a = x[i * ldx4 + j], b = y[i * ldy4 + j];
+        z[i * ldz4 + j] = make_float4(a.x + sy * b.x, a.y + sy * b.y, a.z + sy * b.z, a.w + sy * b.w);
+    }
+}
+
+static int grid_for(long long work, int threads) {
+    long long g = (work + threads - 1) / threads;
+    if (g > 152LL * 16) g = 152LL * 16;
+    return g < 1 ? 1 : (int)g;
+}
+
+cudaError_t launch_addsub(int elem_bytes, int rows, int cols, void* z, long long ldz, const void* x, long long ldx,
+                          const void* y, long long ldy, float sy, cudaStream_t stream) {
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    if (elem_bytes == 4) {
+        const bool v4 = ((cols | ldz | ldx | ldy) & 3) == 0 &&
+                        ((reinterpret_cast<uintptr_t>(z) | reinterpret_cast<uintptr_t>(x) |
+                          reinterpret_cast<uintptr_t>(y)) & 15) == 0;
+        if (v4) {
+            addsub4_kernel<<<grid_for((long long)rows * cols / 4, 256), 256, 0, stream>>>(
+                rows, cols / 4, (float4*)z, ldz / 4, (const float4*)x, ldx / 4, (const float4*)y, ldy / 4, sy);
+        } else {
+            addsub_kernel<float><<<grid_for((long long)rows * cols, 256), 256, 0, stream>>>(
+                rows, cols, (float*)z, ldz, (const float*)x, ldx, (const float*)y, ldy, sy);
+        }
+    } else {
+        addsub_kernel<double><<<grid_for((long long)rows * cols, 256), 256, 0, stream>>>(
+            rows, cols, (double*)z, ldz, (const double*)x, ldx, (const double*)y, ldy, (double)sy);
+    }
+    return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void copy_pad_kernel(int rows, int cols, T* __restrict__ z, long long ldz, const T* __restrict__ x,
+                                long long ldx, int src_rows, int src_cols) {
+    const long long total = (long long)rows * cols;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / cols), j = (int)(e - (long long)i * cols);
+        z[i * ldz + j] = (i < src_rows && j < src_cols) ? x[i * ldx + j] : T(0);
+    }
+}
+
+cudaError_t launch_copy_pad(int elem_bytes, int rows, int cols, void* z, long long ldz, const void* x,
+                            long long ldx, int src_rows, int src_cols, cudaStream_t stream) {
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    const int g = grid_for((long long)rows * cols, 256);
+    if (elem_bytes == 4)
+        copy_pad_kernel<float><<<g, 256, 0, stream>>>(rows, cols, (float*)z, ldz, (const float*)x, ldx, src_rows,
+                                                      src_cols);
+    else
+        copy_pad_kernel<double><<<g, 256, 0, stream>>>(rows, cols, (double*)z, ldz, (const double*)x, ldx,
+                                                       src_rows, src_cols);
+    return cudaGetLastError();
+}
+
+// ============================================================== preadd (operand sums, all levels)
+template <typename T, int N>
+struct Vec {
+    T e[N];
+    __device__ __forceinline__ Vec operator+(const Vec& o) const {
+        Vec r;
+#pragma unroll
+        for (int i = 0; i < N; ++i) r.e[i] = e[i] + o.e[i];
+        return r;
+    }
+    __device__ __forceinline__ Vec operator-(const Vec& o) const {
+        Vec r;
+#pragma unroll
+        for (int i = 0; i < N; ++i) r.e[i] = e[i] - o.e[i];
+        return r;
+    }
+};
+
+// Operand of product p (0..6 = P1..P7) from the four quadrant values of one level.
+// ALG 1: Strassen (Sec. 2.2).  ALG 2: Winograd, BDPZ chains (Sec. 2.3), evaluated in the
+// chain order S1 -> S2 -> S4 and T1 -> T2 -> T4 so the rounding matches the 22-step form.
+template <int ALG, bool BSIDE, typename V>
+__device__ __forceinline__ V form(int p, const V& x11, const V& x12, const V& x21, const V& x22) {
+    if (ALG == 2) {
+        if (!BSIDE) {
+            switch (p) {
+                case 0: return x11;                                    // A11
+                case 1: return x12;                                    // A12
+                case 2: { V s1 = x21 + x22; V s2 = s1 - x11; return x12 - s2; }  // S4
+                case 3: return x22;                                    // A22
+                case 4: return x21 + x22;                              // S1
+                case 5: { V s1 = x21 + x22; return s1 - x11; }         // S2
+                default: return x11 - x21;                             // S3
+            }
+        } else {
+            switch (p) {
+                case 0: return x11;                                    // B11
+                case 1: return x21;                                    // B21
+                case 2: return x22;                                    // B22
+                case 3: { V t1 = x12 - x11; V t2 = x22 - t1; return t2 - x21; }  // T4
+                case 4: return x12 - x11;                              // T1
+                case 5: { V t1 = x12 - x11; return x22 - t1; }         // T2
+                default: return x22 - x12;                             // T3
+            }
+        }
+    } else {
+        if (!BSIDE) {
+            switch (p) {
+                case 0: return x11 + x22;  // P1: A11 + A22
+                case 1: return x21 + x22;  // P2: A21 + A22
+                case 2: return x11;        // P3: A11
+                case 3: return x22;        // P4: A22
+                case 4: return x11 + x12;  // P5: A11 + A12
+                case 5: return x21 - x11;  // P6: -A11 + A21
+                default: return x12 - x22; // P7: A12 - A22
+            }
+        } else {
+            switch (p) {
+                case 0: return x11 + x22;  // P1: B11 + B22
+                case 1: return x11;        // P2: B11
+                case 2: return x12 - x22;  // P3: B12 - B22
+                case 3: return x21 - x11;  // P4: -B11 + B21
+                case 4: return x22;        // P5: B22
+                case 5: return x11 + x12;  // P6: B11 + B12
+                default: return x21 + x22; // P7: B21 + B22
+            }
+        }
+    }
+}
+
+template <typename V>
+struct SlotWriter {
+    const short* slot_of;
+    uint8_t* out;           // base of the slot stack
+    long long slot_stride;  // bytes between slots
+    long long off;          // byte offset of this thread's element inside a slot
+    bool valid;
+    __device__ __forceinline__ void put(int w, const V& v) {
+        const int s = slot_of[w];
+        if (s >= 0 && valid) *reinterpret_cast<V*>(out + s * slot_stride + off) = v;
+    }
+};
+
+template <int ALG, bool BSIDE, int L, typename V>
+struct Expand {
+    template <class W>
+    static __device__ __forceinline__ void run(const V (&v)[1 << (2 * L)], int w, W& wr) {
+        constexpr int H = 1 << (L - 1), N = 1 << L;
+#pragma unroll
+        for (int p = 0; p < 7; ++p) {
+            V s[1 << (2 * (L - 1))];
+#pragma unroll
+            for (int r = 0; r < H; ++r)
+#pragma unroll
+                for (int c = 0; c < H; ++c)
+                    s[r * H + c] = form<ALG, BSIDE, V>(p, v[r * N + c], v[r * N + c + H], v[(r + H) * N + c],
+                                                       v[(r + H) * N + c + H]);
+            Expand<ALG, BSIDE, L - 1, V>::run(s, w * 7 + p, wr);
+        }
+    }
+};
+
+template <int ALG, bool BSIDE, typename V>
+struct Expand<ALG, BSIDE, 0, V> {
+    template <class W>
+    static __device__ __forceinline__ void run(const V (&v)[1], int w, W& wr) {
+        wr.put(w, v[0]);
+    }
+};
+
+// One thread = VEC consecutive columns of one row position inside the leaf block.
+template <typename T, int VEC, int L, int ALG, bool BSIDE>
+__global__ void __launch_bounds__(256) preadd_kernel(const PreaddArgs a) {
+    using V = Vec<T, VEC>;
+    constexpr int N = 1 << L;
+    const int cpr = a.bcols / VEC;  // vector columns per block row
+    const long long total = (long long)a.brows * cpr;
+    const T* x = reinterpret_cast<const T*>(a.x);
+    __shared__ short slot_of[343];
+    for (int i = threadIdx.x; i < 343; i += blockDim.x) slot_of[i] = a.slot_of[i];
+    __syncthreads();
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / cpr);
+        const int j = (int)(e - (long long)i * cpr) * VEC;
+        V v[N * N];
+#pragma unroll
+        for (int br = 0; br < N; ++br) {
+#pragma unroll
+            for (int bc = 0; bc < N; ++bc) {
+                const int gr = br * a.brows + i, gc = bc * a.bcols + j;
+                V t;
+                if (gr < a.rows && gc + VEC <= a.cols) {
+                    t = *reinterpret_cast<const V*>(x + gr * a.ldx + gc);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < VEC; ++q)
+                        t.e[q] = (gr < a.rows && gc + q < a.cols) ? x[gr * a.ldx + gc + q] : T(0);
+                }
+                v[br * N + bc] = t;
+            }
+        }
+        SlotWriter<V> wr;
+        wr.slot_of = slot_of;
+        wr.out = reinterpret_cast<uint8_t*>(a.out);
+        wr.slot_stride = (long long)a.brows * a.bcols * sizeof(T);
+        wr.off = ((long long)i * a.bcols + j) * sizeof(T);
+        wr.valid = true;
+        Expand<ALG, BSIDE, L, V>::run(v, 0, wr);
+    }
+}
+
+template <typename T, int VEC, int L>
+static void preadd_dispatch_alg(const PreaddArgs& a, int grid, cudaStream_t s) {
+    if (a.alg == 2) {
+        if (a.bside) preadd_kernel<T, VEC, L, 2, true><<<grid, 256, 0, s>>>(a);
+        else preadd_kernel<T, VEC, L, 2, false><<<grid, 256, 0, s>>>(a);
+    } else {
+        if (a.bside) preadd_kernel<T, VEC, L, 1, true><<<grid, 256, 0, s>>>(a);
+        else preadd_kernel<T, VEC, L, 1, false><<<grid, 256, 0, s>>>(a);
+    }
+}
+
+cudaError_t launch_preadd(int elem_bytes, const PreaddArgs& a, cudaStream_t s) {
+    if (a.L < 1 || a.L > 3) return cudaErrorInvalidValue;
+    if (a.brows <= 0 || a.bcols <= 0) return cudaSuccess;
+    const bool vec_ok = elem_bytes == 4 && (a.bcols % 4) == 0 && (a.ldx % 4) == 0 &&
+                        (reinterpret_cast<uintptr_t>(a.x) & 15) == 0 && (reinterpret_cast<uintptr_t>(a.out) & 15) == 0;
+    if (elem_bytes == 4) {
+        if (vec_ok && a.L <= 2) {
+            const int g = grid_for((long long)a.brows * a.bcols / 4, 256);
+            if (a.L == 1) preadd_dispatch_alg<float, 4, 1>(a, g, s);
+            else preadd_dispatch_alg<float, 4, 2>(a, g, s);
+        } else {
+            const int g = grid_for((long long)a.brows * a.bcols, 256);
+            if (a.L == 1) preadd_dispatch_alg<float, 1, 1>(a, g, s);
+            else if (a.L == 2) preadd_dispatch_alg<float, 1, 2>(a, g, s);
+            else preadd_dispatch_alg<float, 1, 3>(a, g, s);
+        }
+    } else {
+        const int g = grid_for((long long)a.brows * a.bcols, 256);
+        if (a.L == 1) preadd_dispatch_alg<double, 1, 1>(a, g, s);
+        else if (a.L == 2) preadd_dispatch_alg<double, 1, 2>(a, g, s);
+        else preadd_dispatch_alg<double, 1, 3>(a, g, s);
+    }
+    return cudaGetLastError();
+}
+
+// ============================================================== FP64 leaf GEMM (SIMT)
+// 64 x 64 output tile per CTA, 256 threads, 4 x 4 outputs per thread, k blocks of 16.
+constexpr int F64_BK = 16;
+
+__global__ void __launch_bounds__(256) gemm_f64_kernel(const MatRef* __restrict__ refs, const Leaf* __restrict__ leaves,
+                                                       int nleaves, const Target* __restrict__ targets,
+                                                       int total_items) {
+    __shared__ double As[F64_BK][F64_BM + 1];
+    __shared__ double Bs[F64_BK][F64_BN + 1];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    for (int item = blockIdx.x; item < total_items; item += gridDim.x) {
+        int lo = 0, hi = nleaves - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (leaves[mid].tile_begin <= item) lo = mid; else hi = mid - 1;
+        }
+        const Leaf Lf = leaves[lo];
+        const int local = item - Lf.tile_begin;
+        const int tm = local / Lf.tiles_n, tn = local - tm * Lf.tiles_n;
+        const MatRef A = refs[Lf.a_map], B = refs[Lf.b_map];
+        const double* Ap = reinterpret_cast<const double*>(A.p);
+        const double* Bp = reinterpret_cast<const double*>(B.p);
+        const int K = Lf.kblocks;  // for this kernel: the inner dimension in elements
+        double acc[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+        for (int k0 = 0; k0 < K; k0 += F64_BK) {
+            // A tile: rows tm*64.., cols k0.. ; B tile: rows k0.., cols tn*64..
+            for (int e = threadIdx.x; e < F64_BM * F64_BK; e += 256) {
+                const int r = e / F64_BK, c = e - r * F64_BK;
+                const int gr = Lf.a_row + tm * F64_BM + r, gc = Lf.a_col + k0 + c;
+                const bool in = (tm * F64_BM + r) < Lf.m && (k0 + c) < K && gr < A.rows && gc < A.cols;
+                As[c][r] = in ? Ap[gr * A.ld + gc] : 0.0;
+            }
+            for (int e = threadIdx.x; e < F64_BK * F64_BN; e += 256) {
+                const int r = e / F64_BN, c = e - r * F64_BN;
+                const int gr = Lf.b_row + k0 + r, gc = Lf.b_col + tn * F64_BN + c;
+                const bool in = (k0 + r) < K && (tn * F64_BN + c) < Lf.n && gr < B.rows && gc < B.cols;
+                Bs[r][c] = in ? Bp[gr * B.ld + gc] : 0.0;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int kk = 0; kk < F64_BK; ++kk) {
+                double a[4], b[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+            }
+            __syncthreads();
+        }
+        for (int t = 0; t < Lf.tgt_count; ++t) {
+            const Target tg = targets[Lf.tgt_begin + t];
+            double* c = reinterpret_cast<double*>(tg.c);
+            const double s = (double)tg.sign;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int r = tm * F64_BM + ty * 4 + i;
+                if (r >= tg.rows || r >= Lf.m) continue;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int cc = tn * F64_BN + tx * 4 + j;
+                    if (cc >= tg.cols || cc >= Lf.n) continue;
+                    double* p = c + (long long)r * tg.ldc + cc;
+                    const double v = s * acc[i][j];
+                    if (tg.mode == TGT_STORE) *p = v;
+                    else if (tg.mode == TGT_ATOMIC) atomicAdd(p, v);
+                    else *p += v;
+                }
+            }
+        }
+    }
+}
+
+cudaError_t launch_gemm_f64(const MatRef* refs, const Leaf* leaves, int nleaves, const Target* targets,
+                            int total_items, int grid, cudaStream_t stream) {
+    if (total_items <= 0) return cudaSuccess;
+    if (grid > total_items) grid = total_items;
+    gemm_f64_kernel<<<grid, 256, 0, stream>>>(refs, leaves, nleaves, targets, total_items);
+    return cudaGetLastError();
+}
+
+// ============================================================== norms
+template <typename T>
+__global__ void norms_kernel(int m, int n, int k, const T* A, long long lda, const T* B, long long ldb, const T* C,
+                             long long ldc, const double* R, long long ldr, unsigned long long* out) {
+    double e = 0.0, am = 0.0, bm = 0.0;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (C && R)
+        for (long long x = t0; x < (long long)m * n; x += stride) {
+            const int i = (int)(x / n), j = (int)(x - (long long)i * n);
+            const double d = fabs((double)C[i * ldc + j] - R[i * ldr + j]);
+            e = (d > e || d != d) ? d : e;
+        }
+    if (A)
+        for (long long x = t0; x < (long long)m * k; x += stride) {
+            const int i = (int)(x / k), j = (int)(x - (long long)i * k);
+            am = fmax(am, fabs((double)A[i * lda + j]));
+        }
+    if (B)
+        for (long long x = t0; x < (long long)k * n; x += stride) {
+            const int i = (int)(x / n), j = (int)(x - (long long)i * n);
+            bm = fmax(bm, fabs((double)B[i * ldb + j]));
+        }
+    // non-negative doubles order like their bit patterns (NaN above +inf)
+    for (int o = 16; o > 0; o >>= 1) {
+        const double e2 = __shfl_xor_sync(0xffffffffu, e, o);
+        e = (e2 > e || e2 != e2) ? e2 : e;
+        am = fmax(am, __shfl_xor_sync(0xffffffffu, am, o));
+        bm = fmax(bm, __shfl_xor_sync(0xffffffffu, bm, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(&out[0], (unsigned long long)__double_as_longlong(e));
+        atomicMax(&out[1], (unsigned long long)__double_as_longlong(am));
+        atomicMax(&out[2], (unsigned long long)__double_as_longlong(bm));
+    }
+}
+
+cudaError_t launch_norms(int elem_bytes, int m, int n, int k, const void* A, long long lda, const void* B,
+                         long long ldb, const void* C, long long ldc, const double* R, long long ldr,
+                         unsigned long long* d_out, cudaStream_t s) {
+    const int g = grid_for((long long)m * (n > k ? n : k), 256);
+    if (elem_bytes == 4)
+        norms_kernel<float><<<g, 256, 0, s>>>(m, n, k, (const float*)A, lda, (const float*)B, ldb, (const float*)C,
+                                              ldc, R, ldr, d_out);
+    else
+        norms_kernel<double><<<g, 256, 0, s>>>(m, n, k, (const double*)A, lda, (const double*)B, ldb,
+                                               (const double*)C, ldc, R, ldr, d_out);
+    return cudaGetLastError();
+}
+
+}  // namespace swk

@@ -1,0 +1,54 @@
+// plan.h -- work descriptors shared by the host planner and the leaf-GEMM kernels.
+//
+// A launch of the grouped leaf GEMM processes a list of LEAVES.  A leaf is one sub-product
+// P = Aop * Bop of the recursion (Sec. 2.2 / 2.3) whose operands are rectangles of tensor
+// maps (the input matrices or the materialised operand sums), and whose result is added with
+// a sign into one or more TARGET blocks of C -- the post-additions U1..U7 (or C11..C22 of
+// Strassen) folded into the epilogue.  A leaf is cut into BM x BN output tiles; every tile is
+// one work item of the persistent kernel.
+#pragma once
+#include <cstdint>
+
+namespace swk {
+
+// Device error word values (the host maps them to SW_ETIMEOUT / SW_ECUDA).
+enum : int {
+    ERR_NONE = 0,
+    ERR_WAIT_FULL = 1,      // MMA waited too long for a TMA stage
+    ERR_WAIT_EMPTY = 2,     // producer waited too long for a free stage
+    ERR_WAIT_ACC = 3,       // epilogue waited too long for an accumulator
+    ERR_WAIT_ACC_FREE = 4,  // MMA waited too long for the epilogue to free an accumulator
+    ERR_WAIT_DRAIN = 5,     // final drain of in-flight copies / MMAs
+    ERR_ALIGN = 6,          // a TMA coordinate violated the 16-byte rule (the copy was skipped)
+    ERR_ORDER = 7,          // an ordered epilogue waited too long for its predecessor
+};
+
+enum TargetMode : int {
+    TGT_STORE = 0,   // C_block  = sign * P
+    TGT_ATOMIC = 1,  // C_block += sign * P  (atomic; several leaves may hit the block at once)
+    TGT_ADD = 2,     // C_block += sign * P  (plain read-modify-write; single writer at a time)
+};
+
+struct Target {
+    void* c;          // origin of the target block (element type of the product)
+    long long ldc;    // leading dimension in elements
+    int rows, cols;   // valid extent of the block; rows/cols beyond it are not written
+    float sign;       // +1 or -1
+    int mode;         // TargetMode
+    int vec_ok;       // 1 when c is 16-byte aligned and ldc is a multiple of 4 (FP32)
+    int pad_;
+};
+
+struct Leaf {
+    int a_map, b_map;  // tensor-map indices
+    int a_row, a_col;  // origin of the A operand in its map (row, column)
+    int b_row, b_col;  // origin of the B operand in its map
+    int m, n;          // extent of the product (tiles_m = ceil(m/BM), tiles_n = ceil(n/BN))
+    int kblocks;       // number of BK-deep k blocks
+    int tgt_begin, tgt_count;
+    int tile_begin;    // index of the leaf's first work item
+    int tiles_n;
+    int pad_;
+};
+
+}  // namespace swk

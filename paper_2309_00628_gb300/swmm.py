@@ -1,0 +1,147 @@
+"""ctypes binding of libswmm (include/swmm.h): argument marshalling only.
+
+Every function keeps the C name and returns the C status, except where noted.
+All arithmetic runs in the CUDA library; if the library has not been built this
+module raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+SW_OK, SW_EINVAL, SW_ENOMEM, SW_EBUDGET, SW_ECUDA, SW_ETIMEOUT, SW_EUNSUPPORTED = range(7)
+STATUS_NAMES = ["SW_OK", "SW_EINVAL", "SW_ENOMEM", "SW_EBUDGET", "SW_ECUDA", "SW_ETIMEOUT", "SW_EUNSUPPORTED"]
+
+SW_ALGO_NAIVE, SW_ALGO_STRASSEN, SW_ALGO_WINOGRAD = 0x0, 0x1, 0x2
+SW_SCHED_FUSED, SW_SCHED_TWO_TEMP, SW_SCHED_IN_PLACE, SW_SCHED_ALLOC = 0x00, 0x10, 0x20, 0x30
+SW_PAD, SW_PEEL = 0x000, 0x100
+SW_LEAF_TF32, SW_LEAF_BF16X3 = 0x0000, 0x1000
+
+
+class SwError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 7 else status}: {msg}")
+        self.status = status
+
+
+_lib = None
+_V, _I, _U, _S, _P = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint32, ctypes.c_size_t, ctypes.POINTER
+
+
+def library_path() -> str:
+    return _build.lib_path()
+
+
+def load(build_if_missing: bool = False):
+    """Load libswmm.so; raises if it is not built (or builds it when asked)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    so = _build.lib_path()
+    if not os.path.exists(so):
+        if not build_if_missing:
+            raise RuntimeError(f"libswmm is not built ({so} missing): run __graft_entry__.build()")
+        _build.build()
+    lib = ctypes.CDLL(so)
+    lib.sw_create.argtypes = [_P(_V), _S]
+    lib.sw_destroy.argtypes = [_V]
+    lib.sw_last_error.argtypes = [_V]
+    lib.sw_last_error.restype = ctypes.c_char_p
+    lib.sw_mm_workspace_size.argtypes = [_I, _I, _I, _I, _U, _I, _P(_S)]
+    lib.sw_mm_depth.argtypes = [_I, _I, _I, _I, _U, _I, _P(_I)]
+    mm = [_V, _V, _I, _V, _I, _V, _I, _I, _I, _I, _I, _U, _V]
+    lib.sw_smm.argtypes = mm
+    lib.sw_dmm.argtypes = mm
+    lib.sw_smm_host.argtypes = mm
+    lib.sw_sync.argtypes = [_V, _V]
+    lib.sw_error_norms.argtypes = [_V, _I, _I, _I, _I, _V, _I, _V, _I, _V, _I, _V, _I, _P(ctypes.c_double), _V]
+    for name in ("sw_create", "sw_destroy", "sw_mm_workspace_size", "sw_mm_depth", "sw_smm", "sw_dmm",
+                 "sw_smm_host", "sw_sync", "sw_error_norms"):
+        getattr(lib, name).restype = _I
+    _lib = lib
+    return lib
+
+
+# ------------------------------------------------------------------ C names
+def sw_create(budget: int = 0):
+    h = _V()
+    st = load().sw_create(ctypes.byref(h), budget)
+    if st != SW_OK:
+        raise SwError(st, "sw_create failed")
+    return h
+
+
+def sw_destroy(h) -> int:
+    return load().sw_destroy(h)
+
+
+def sw_last_error(h) -> str:
+    r = load().sw_last_error(h)
+    return r.decode() if r else ""
+
+
+def sw_mm_workspace_size(m, n, k, cutoff, variant, elem_bytes):
+    b = _S()
+    st = load().sw_mm_workspace_size(m, n, k, cutoff, variant, elem_bytes, ctypes.byref(b))
+    return st, b.value
+
+
+def sw_mm_depth(m, n, k, cutoff, variant, elem_bytes):
+    d = _I()
+    st = load().sw_mm_depth(m, n, k, cutoff, variant, elem_bytes, ctypes.byref(d))
+    return st, d.value
+
+
+def sw_smm(h, A, lda, B, ldb, C, ldc, m, n, k, cutoff, variant, stream=None) -> int:
+    return load().sw_smm(h, A, lda, B, ldb, C, ldc, m, n, k, cutoff, variant, stream)
+
+
+def sw_dmm(h, A, lda, B, ldb, C, ldc, m, n, k, cutoff, variant, stream=None) -> int:
+    return load().sw_dmm(h, A, lda, B, ldb, C, ldc, m, n, k, cutoff, variant, stream)
+
+
+def sw_smm_host(h, A, lda, B, ldb, C, ldc, m, n, k, cutoff, variant, stream=None) -> int:
+    return load().sw_smm_host(h, A, lda, B, ldb, C, ldc, m, n, k, cutoff, variant, stream)
+
+
+def sw_sync(h, stream=None) -> int:
+    return load().sw_sync(h, stream)
+
+
+def sw_error_norms(h, elem_bytes, m, n, k, A, lda, B, ldb, C, ldc, R, ldr, stream=None):
+    out = (ctypes.c_double * 3)()
+    st = load().sw_error_norms(h, elem_bytes, m, n, k, A, lda, B, ldb, C, ldc, R, ldr, out, stream)
+    return st, [out[0], out[1], out[2]]
+
+
+def check(h, status: int) -> None:
+    """Raise SwError for a non-OK status, with the handle's last error message."""
+    if status != SW_OK:
+        raise SwError(status, sw_last_error(h))
+
+
+# ------------------------------------------------------------------ torch marshalling
+def _stream_ptr(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def mm(h, A, B, cutoff: int = 0, variant: int = SW_ALGO_WINOGRAD, out=None, stream=None, sync: bool = False):
+    """C = A @ B for row-major CUDA tensors (float32 -> sw_smm, float64 -> sw_dmm)."""
+    import torch
+    assert A.is_cuda and B.is_cuda and A.dim() == 2 and B.dim() == 2 and A.dtype == B.dtype
+    m, k = A.shape
+    k2, n = B.shape
+    assert k == k2
+    assert A.stride(1) == 1 and B.stride(1) == 1
+    C = out if out is not None else torch.empty((m, n), dtype=A.dtype, device=A.device)
+    fn = sw_smm if A.dtype == torch.float32 else sw_dmm
+    st = fn(h, ctypes.c_void_p(A.data_ptr()), max(A.stride(0), 1), ctypes.c_void_p(B.data_ptr()), max(B.stride(0), 1),
+            ctypes.c_void_p(C.data_ptr()), max(C.stride(0), 1), m, n, k, cutoff, variant, _stream_ptr(stream))
+    check(h, st)
+    if sync:
+        check(h, sw_sync(h, _stream_ptr(stream)))
+    return C

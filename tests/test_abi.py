@@ -1,0 +1,89 @@
+"""CPU tests of the C-ABI library: it loads, exports every symbol include/swmm.h
+declares, and its host-side planning logic (depth rule, workspace accounting,
+argument checks) agrees with the oracle's counting.  No GPU is touched."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import oracle
+from paper_2309_00628_gb300 import build, swmm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "swmm.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return swmm.load()
+
+
+def declared_symbols():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:sw_status|const char \*|void)\s*\**\s*(sw_\w+)\s*\(", text, re.M)))
+
+
+def test_header_declares_entry_points():
+    syms = declared_symbols()
+    for s in ("sw_create", "sw_destroy", "sw_smm", "sw_dmm", "sw_smm_host", "sw_sync", "sw_mm_workspace_size",
+              "sw_last_error"):
+        assert s in syms
+
+
+def test_library_exports_every_declared_symbol(lib):
+    so = ctypes.CDLL(swmm.library_path())
+    missing = [s for s in declared_symbols() if not hasattr(so, s)]
+    assert not missing, missing
+
+
+@pytest.mark.parametrize("m,n,k,cutoff", [(256, 256, 256, 32), (16, 16, 16, 12), (100, 300, 3000, 32),
+                                          (33, 33, 33, 32), (8192, 8192, 8192, 1024), (5, 7, 9, 1)])
+def test_depth_rule_matches_oracle(lib, m, n, k, cutoff):
+    for v in (swmm.SW_ALGO_WINOGRAD | swmm.SW_SCHED_TWO_TEMP, swmm.SW_ALGO_STRASSEN | swmm.SW_SCHED_ALLOC):
+        st, d = swmm.sw_mm_depth(m, n, k, cutoff, v, 8)
+        assert st == swmm.SW_OK and d == oracle.depth(m, n, k, cutoff)
+    st, d = swmm.sw_mm_depth(m, n, k, cutoff, swmm.SW_ALGO_NAIVE, 4)
+    assert d == 0
+
+
+def test_fused_depth_is_capped_at_three(lib):
+    st, d = swmm.sw_mm_depth(4096, 4096, 4096, 32, swmm.SW_ALGO_WINOGRAD | swmm.SW_SCHED_FUSED, 4)
+    assert st == swmm.SW_OK and d == 3
+
+
+@pytest.mark.parametrize("L", [1, 2, 3])
+def test_workspace_matches_schedule_counts(lib, L):
+    n = 16384
+    cutoff = n >> L  # halve exactly L times
+    for sched, which in ((swmm.SW_SCHED_ALLOC, 0), (swmm.SW_SCHED_TWO_TEMP, 1)):
+        st, b = swmm.sw_mm_workspace_size(n, n, n, cutoff, swmm.SW_ALGO_WINOGRAD | sched, 4)
+        assert st == swmm.SW_OK
+        assert b == pytest.approx(oracle.workspace_elems(which, n, n, n, L) * 4, rel=1e-3)
+    st, b = swmm.sw_mm_workspace_size(n, n, n, cutoff, swmm.SW_ALGO_WINOGRAD | swmm.SW_SCHED_IN_PLACE, 4)
+    assert st == swmm.SW_OK and b == 0
+
+
+def test_fused_workspace_counts_materialised_sums(lib):
+    # Winograd: 7^L - 3^L leaf operands per side are sums (the rest are plain blocks)
+    n = 8192
+    for L in (1, 2, 3):
+        st, b = swmm.sw_mm_workspace_size(n, n, n, n >> L, swmm.SW_ALGO_WINOGRAD | swmm.SW_SCHED_FUSED, 4)
+        blk = (n >> L) ** 2 * 4
+        assert st == swmm.SW_OK
+        assert b == pytest.approx(2 * (7 ** L - 3 ** L) * blk, rel=1e-3)
+
+
+def test_argument_errors_without_gpu(lib):
+    st, _ = swmm.sw_mm_workspace_size(-1, 4, 4, 1, 0, 4)
+    assert st == swmm.SW_EINVAL
+    st, _ = swmm.sw_mm_workspace_size(4, 4, 4, 1, 0, 3)
+    assert st == swmm.SW_EINVAL
+    st, _ = swmm.sw_mm_workspace_size(8, 8, 8, 1, swmm.SW_ALGO_WINOGRAD | swmm.SW_SCHED_IN_PLACE, 4)
+    assert st == swmm.SW_OK
+    st, _ = swmm.sw_mm_workspace_size(8, 4, 8, 1, swmm.SW_ALGO_WINOGRAD | swmm.SW_SCHED_IN_PLACE, 4)
+    assert st == swmm.SW_EUNSUPPORTED
+    st, _ = swmm.sw_mm_workspace_size(8, 8, 8, 1, swmm.SW_ALGO_STRASSEN | swmm.SW_SCHED_TWO_TEMP, 4)
+    assert st == swmm.SW_EUNSUPPORTED
+    assert swmm.load().sw_smm(None, None, 1, None, 1, None, 1, 1, 1, 1, 1, 0, None) == swmm.SW_EINVAL

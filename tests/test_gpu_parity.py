@@ -1,0 +1,256 @@
+"""GPU parity: every path of libswmm against the FP64 CPU oracle.
+
+Bars (the normalised error is max|C - C_ref| / (k max|A| max|B|)):
+  * integer-valued inputs: bit-exact, on sizes where every partial sum the GPU forms is an
+    integer below 2^24 (FP32) -- the bound is computed from the depth and value range;
+  * FP64 path: <= 1e-13;
+  * TF32 path: <= (2^-9 + k 2^-24) * 3^L -- the worst-case bound of one TF32 product with FP32
+    accumulation, times the typical per-level error growth of the 7-product forms.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2309_00628_gb300 import inputs, swmm
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+W, S = swmm.SW_ALGO_WINOGRAD, swmm.SW_ALGO_STRASSEN
+FUSED, TWO, INPL, ALLOC = swmm.SW_SCHED_FUSED, swmm.SW_SCHED_TWO_TEMP, swmm.SW_SCHED_IN_PLACE, swmm.SW_SCHED_ALLOC
+
+
+@pytest.fixture(scope="module")
+def h():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    swmm.load(build_if_missing=True)
+    hd = swmm.sw_create(0)
+    yield hd
+    swmm.sw_destroy(hd)
+
+
+def tol_tf32(k, L):
+    return (2.0 ** -9 + k * 2.0 ** -24) * 3.0 ** L
+
+
+def run(h, A, B, cutoff, variant, dtype=np.float32, lda_pad=0, clobber_ok=False):
+    """C = A B through sw_smm / sw_dmm on device copies of A, B; returns numpy C."""
+    m, k = A.shape
+    n = B.shape[1]
+    tdt = torch.float32 if dtype == np.float32 else torch.float64
+    dA = torch.zeros((m, k + lda_pad), dtype=tdt, device="cuda")
+    dA[:, :k] = torch.from_numpy(A.astype(dtype))
+    dB = torch.from_numpy(B.astype(dtype)).cuda()
+    dC = torch.full((m, n), float("nan"), dtype=tdt, device="cuda")
+    fn = swmm.sw_smm if dtype == np.float32 else swmm.sw_dmm
+    st = fn(h, ctypes.c_void_p(dA.data_ptr()), k + lda_pad, ctypes.c_void_p(dB.data_ptr()), max(n, 1),
+            ctypes.c_void_p(dC.data_ptr()), max(n, 1), m, n, k, cutoff, variant, None)
+    swmm.check(h, st)
+    swmm.check(h, swmm.sw_sync(h, None))
+    return dC.cpu().numpy().astype(np.float64)
+
+
+def depth(h, m, n, k, cutoff, variant, eb):
+    st, d = swmm.sw_mm_depth(m, n, k, cutoff, variant, eb)
+    assert st == swmm.SW_OK
+    return d
+
+
+def exact_int_safe(lim, k, L, growth=4):
+    # worst case |partial sum| of an integer product at depth L: operand sums grow <= growth^L,
+    # a leaf sums k/2^L products, and a C block receives up to 4^L leaf results
+    s = lim * growth ** L
+    return s * s * (k / 2 ** L + 32) * 4 ** L < 2 ** 24
+
+
+# ------------------------------------------------------------------ plain product (Alg. 1)
+@pytest.mark.parametrize("m,n,k", [(1, 1, 1), (128, 256, 32), (300, 500, 200), (129, 257, 33), (1000, 1000, 1000),
+                                   (64, 2000, 7), (5, 3, 4000)])
+def test_plain_tf32_integers_bit_exact(h, m, n, k):
+    A, B = inputs.pair(m, n, k, "int", seed=0, dtype=np.float64)
+    C = run(h, A, B, 0, swmm.SW_ALGO_NAIVE)
+    assert np.array_equal(C, oracle.naive(A, B))
+
+
+def test_plain_tf32_float_within_bound_and_deterministic(h):
+    m, n, k = 777, 640, 1500
+    A, B = inputs.pair(m, n, k, "uniform", seed=3, dtype=np.float32)
+    C1 = run(h, A, B, 0, swmm.SW_ALGO_NAIVE)
+    C2 = run(h, A, B, 0, swmm.SW_ALGO_NAIVE)
+    assert np.array_equal(C1, C2)
+    R = oracle.naive(A.astype(np.float64), B.astype(np.float64))
+    err = oracle.err_norm(C1, R, A, B)
+    assert err <= tol_tf32(k, 0), err
+    assert err > 0  # the tensor core really ran at TF32, not FP32
+
+
+def test_plain_unaligned_leading_dimension(h):
+    m, n, k = 70, 90, 61
+    A, B = inputs.pair(m, n, k, "int", seed=4, dtype=np.float64)
+    C = run(h, A, B, 0, swmm.SW_ALGO_NAIVE, lda_pad=3)
+    assert np.array_equal(C, oracle.naive(A, B))
+
+
+def test_degenerate_sizes(h):
+    for m, n, k in [(0, 5, 5), (5, 0, 5), (3, 4, 0)]:
+        A, B = np.ones((m, k)), np.ones((k, n))
+        for v in (swmm.SW_ALGO_NAIVE, W | FUSED, W | TWO):
+            if m == 0 or n == 0:
+                continue
+            C = run(h, A, B, 1, v)
+            assert np.array_equal(C, np.zeros((m, n)))
+
+
+# ------------------------------------------------------------------ FUSED recursion
+@pytest.mark.parametrize("algo", [W, S])
+@pytest.mark.parametrize("m,n,k,cutoff", [(256, 256, 256, 128), (256, 256, 256, 64), (384, 384, 384, 32),
+                                          (300, 260, 200, 64), (97, 131, 203, 40), (512, 128, 1024, 32),
+                                          (1024, 1024, 1024, 256)])
+def test_fused_integers_bit_exact(h, algo, m, n, k, cutoff):
+    v = algo | FUSED
+    L = depth(h, m, n, k, cutoff, v, 4)
+    assert L >= 1
+    lim = 1 if L >= 2 else 4
+    assert exact_int_safe(lim, k, L)
+    A, B = inputs.pair(m, n, k, "int", seed=L, dtype=np.float64, lim=lim)
+    C = run(h, A, B, cutoff, v)
+    assert np.array_equal(C, oracle.naive(A, B)), (algo, L)
+
+
+@pytest.mark.parametrize("algo", [W, S])
+@pytest.mark.parametrize("L", [1, 2, 3])
+def test_fused_float_within_bound(h, algo, L):
+    n = 1024
+    A, B = inputs.pair(n, n, n, "uniform", seed=10 + L, dtype=np.float32)
+    R = oracle.naive_mt(A.astype(np.float64), B.astype(np.float64))
+    C = run(h, A, B, n >> L, algo | FUSED)
+    assert depth(h, n, n, n, n >> L, algo | FUSED, 4) == L
+    err = oracle.err_norm(C, R, A, B)
+    assert err <= tol_tf32(n, L), (L, err)
+
+
+# ------------------------------------------------------------------ materialised schedules
+@pytest.mark.parametrize("sched", [TWO, INPL, ALLOC])
+@pytest.mark.parametrize("n,cutoff", [(256, 128), (256, 64), (512, 64)])
+def test_schedules_integers_bit_exact(h, sched, n, cutoff):
+    v = W | sched
+    L = depth(h, n, n, n, cutoff, v, 4)
+    lim = 1 if L >= 2 else 4
+    assert exact_int_safe(lim, n, L)
+    A, B = inputs.pair(n, n, n, "int", seed=20 + L, dtype=np.float64, lim=lim)
+    C = run(h, A, B, cutoff, v)
+    assert np.array_equal(C, oracle.naive(A, B)), (sched, L)
+
+
+def test_strassen_alloc_integers_bit_exact(h):
+    n = 512
+    A, B = inputs.pair(n, n, n, "int", seed=30, dtype=np.float64, lim=1)
+    C = run(h, A, B, 64, S | ALLOC)
+    assert np.array_equal(C, oracle.naive(A, B))
+
+
+@pytest.mark.parametrize("odd", [swmm.SW_PAD, swmm.SW_PEEL])
+@pytest.mark.parametrize("sched", [TWO, ALLOC, INPL])
+def test_schedules_odd_sizes(h, odd, sched):
+    shapes = [(300, 300, 300)] if sched == INPL else [(300, 260, 200), (97, 131, 203), (260, 100, 300)]
+    for m, n, k in shapes:
+        A, B = inputs.pair(m, n, k, "int", seed=40, dtype=np.float64, lim=2)
+        C = run(h, A, B, 40, W | sched | odd)
+        assert np.array_equal(C, oracle.naive(A, B)), (m, n, k, sched, odd)
+
+
+def test_schedules_float_within_bound(h):
+    n = 512
+    A, B = inputs.pair(n, n, n, "uniform", seed=50, dtype=np.float32)
+    R = oracle.naive(A.astype(np.float64), B.astype(np.float64))
+    for sched in (TWO, INPL, ALLOC):
+        C = run(h, A, B, 64, W | sched)
+        L = depth(h, n, n, n, 64, W | sched, 4)
+        assert oracle.err_norm(C, R, A, B) <= tol_tf32(n, L), sched
+
+
+# ------------------------------------------------------------------ FP64 path (n = 256, cutoff 32, L = 3)
+CONFIG1 = [(swmm.SW_ALGO_NAIVE, FUSED), (S, FUSED), (S, ALLOC), (W, FUSED), (W, TWO), (W, INPL), (W, ALLOC)]
+
+
+@pytest.mark.parametrize("algo,sched", CONFIG1)
+def test_fp64_n256_cutoff32(h, algo, sched):
+    n = 256
+    v = algo | sched
+    if algo != swmm.SW_ALGO_NAIVE:
+        assert depth(h, n, n, n, 32, v, 8) == 3
+    Ai, Bi = inputs.pair(n, n, n, "int", seed=0, dtype=np.float64)
+    assert np.array_equal(run(h, Ai, Bi, 32, v, dtype=np.float64), oracle.naive(Ai, Bi))
+    A, B = inputs.pair(n, n, n, "uniform", seed=0, dtype=np.float64)
+    C = run(h, A, B, 32, v, dtype=np.float64)
+    assert oracle.err_norm(C, oracle.naive(A, B), A, B) <= 1e-13
+
+
+@pytest.mark.parametrize("odd", [swmm.SW_PAD, swmm.SW_PEEL])
+def test_fp64_odd_sizes(h, odd):
+    for m, n, k in [(255, 257, 129), (33, 65, 17)]:
+        A, B = inputs.pair(m, n, k, "uniform", seed=1, dtype=np.float64)
+        R = oracle.naive(A, B)
+        for v in (W | FUSED, W | TWO, S | ALLOC):
+            C = run(h, A, B, 16, v | odd, dtype=np.float64)
+            assert oracle.err_norm(C, R, A, B) <= 1e-13, (m, n, k, v)
+
+
+# ------------------------------------------------------------------ host entry point, norms, errors
+def test_host_entry_point_matches_device_path(h):
+    m, n, k = 500, 300, 700
+    A, B = inputs.pair(m, n, k, "uniform", seed=60, dtype=np.float32)
+    C = np.zeros((m, n), np.float32)
+    st = swmm.sw_smm_host(h, A.ctypes.data_as(ctypes.c_void_p), k, B.ctypes.data_as(ctypes.c_void_p), n,
+                          C.ctypes.data_as(ctypes.c_void_p), n, m, n, k, 256, W | FUSED, None)
+    swmm.check(h, st)
+    Cd = run(h, A, B, 256, W | FUSED)
+    R = oracle.naive(A.astype(np.float64), B.astype(np.float64))
+    assert oracle.err_norm(C, R, A, B) <= tol_tf32(k, 1)
+    assert np.max(np.abs(C - Cd)) <= 1e-3
+
+
+def test_error_norms_match_numpy(h):
+    m, n, k = 300, 200, 100
+    A, B = inputs.pair(m, n, k, "uniform", seed=61, dtype=np.float32)
+    C = (A.astype(np.float64) @ B.astype(np.float64)).astype(np.float32)
+    R = A.astype(np.float64) @ B.astype(np.float64) + 1e-3
+    dA, dB, dC = (torch.from_numpy(x).cuda() for x in (A, B, C))
+    dR = torch.from_numpy(R).cuda()
+    p = lambda t: ctypes.c_void_p(t.data_ptr())
+    st, out = swmm.sw_error_norms(h, 4, m, n, k, p(dA), k, p(dB), n, p(dC), n, p(dR), n, None)
+    swmm.check(h, st)
+    assert out[0] == pytest.approx(np.max(np.abs(C - R)), rel=1e-12)
+    assert out[1] == np.max(np.abs(A)) and out[2] == np.max(np.abs(B))
+
+
+def test_argument_errors(h):
+    lib = swmm.load()
+    assert lib.sw_smm(h, None, 4, None, 4, None, 4, 4, 4, 4, 1, 0, None) == swmm.SW_EINVAL
+    d = torch.zeros(64, device="cuda")
+    p = ctypes.c_void_p(d.data_ptr())
+    assert lib.sw_smm(h, p, 2, p, 4, p, 4, 4, 4, 4, 1, 0, None) == swmm.SW_EINVAL
+    assert lib.sw_smm(h, p, 8, p, 4, p, 4, 4, 4, 8, 1, W | INPL, None) == swmm.SW_EUNSUPPORTED
+    assert "m == n == k" in swmm.sw_last_error(h)
+    assert swmm.sw_sync(h, None) == swmm.SW_OK
+
+
+# ------------------------------------------------------------------ full size (n = 8192), sampled rows
+@pytest.mark.parametrize("L", [0, 1, 2, 3])
+def test_full_size_sampled_rows(h, L):
+    n = 8192
+    A, B = inputs.pair(n, n, n, "uniform", seed=0, dtype=np.float32)
+    v = swmm.SW_ALGO_NAIVE if L == 0 else W | FUSED
+    cutoff = n >> L if L else 0
+    if L:
+        assert depth(h, n, n, n, cutoff, v, 4) == L
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    C = swmm.mm(h, dA, dB, cutoff, v, sync=True)
+    rows = np.random.Generator(np.random.PCG64(99)).choice(n, 8, replace=False)
+    R = oracle.naive_mt(A[rows].astype(np.float64), B.astype(np.float64))
+    Cr = C[torch.from_numpy(rows).cuda()].cpu().numpy().astype(np.float64)
+    err = oracle.err_norm(Cr, R, A, B)
+    assert err <= tol_tf32(n, L), err
