@@ -66,7 +66,7 @@ inline long long round_up(long long x, long long a) { return (x + a - 1) / a * a
 inline long long ceil_div(long long x, long long a) { return (x + a - 1) / a; }
 
 // ------------------------------------------------------------------ plan
-enum OpKind { OP_GEMM_TF32, OP_GEMM_F64, OP_ADDSUB, OP_COPY_PAD, OP_PREADD, OP_MEMSET };
+enum OpKind { OP_GEMM_TF32, OP_GEMM_SIMT, OP_ADDSUB, OP_COPY_PAD, OP_PREADD, OP_MEMSET, OP_TRANSPOSE, OP_TRANSPOSE_SQ };
 
 struct Op {
     OpKind kind;
@@ -102,8 +102,14 @@ struct View {
     int rows, cols;
 };
 
+// Lowers one product to ops.  On the FP32 path the tensor cores take B as B^T (K-major), so
+// every B-side value -- B itself, its quadrants, the T sums and the B-side temporaries -- is
+// held transposed ("bt" storage): a logical B quadrant Bij lives at position ji of the stored
+// matrix, and a k x n block is stored n x k.  Elementwise steps are orientation-free as long
+// as all their operands share it, which the schedules below guarantee.
 struct Planner {
     int eb;                 // 4 = FP32 (TF32 leaves), 8 = FP64
+    bool bt;                // B side stored transposed (FP32 path)
     uint32_t variant;
     bool dry;               // size only: no pointers, no maps
     char* ws_base;
@@ -121,6 +127,16 @@ struct Planner {
         r.cols = w;
         return r;
     }
+    // logical quadrant q of a B-side block held in bt storage
+    View quadB(View v, int q) const { return quad(v, bt ? (q == 1 ? 2 : q == 2 ? 1 : q) : q); }
+
+    static View sub(View v, long long r0, long long c0, long long rows, long long cols, int eb) {
+        View s = v;
+        s.p = v.p + (r0 * v.ld + c0) * eb;
+        s.rows = (int)rows;
+        s.cols = (int)cols;
+        return s;
+    }
 
     View talloc(int rows, int cols) {
         const long long ld = round_up(std::max(cols, 1), 4);
@@ -134,6 +150,8 @@ struct Planner {
         ws_peak = std::max(ws_peak, ws_top);
         return v;
     }
+    // a logical k x n B-side temporary
+    View tallocB(int k, int n) { return bt ? talloc(n, k) : talloc(k, n); }
 
     size_t put_blob(const void* src, size_t bytes) {
         size_t off = round_up(plan->blob.size(), 64);
@@ -142,8 +160,11 @@ struct Planner {
         return off;
     }
 
+    void push(const Op& o) {
+        if (!dry) plan->ops.push_back(o);
+    }
+
     void add(View z, View x, View y, float sy) {
-        if (dry) return;
         Op o;
         o.kind = OP_ADDSUB;
         o.eb = eb;
@@ -156,11 +177,10 @@ struct Planner {
         o.y = y.p;
         o.ldy = y.ld;
         o.sy = sy;
-        plan->ops.push_back(o);
+        push(o);
     }
 
     void copy_pad(View z, View x) {  // z (its full extent) <- x, zero outside x's extent
-        if (dry) return;
         Op o;
         o.kind = OP_COPY_PAD;
         o.eb = eb;
@@ -172,11 +192,35 @@ struct Planner {
         o.ldx = x.ld;
         o.src_rows = x.rows;
         o.src_cols = x.cols;
-        plan->ops.push_back(o);
+        push(o);
+    }
+
+    void transpose_into(View z, View x) {  // z (its full extent) <- x^T, zero outside
+        Op o;
+        o.kind = OP_TRANSPOSE;
+        o.eb = 4;
+        o.rows = z.rows;
+        o.cols = z.cols;
+        o.z = z.p;
+        o.ldz = z.ld;
+        o.x = x.p;
+        o.ldx = x.ld;
+        o.src_rows = x.rows;
+        o.src_cols = x.cols;
+        push(o);
+    }
+
+    void transpose_square(View z) {
+        Op o;
+        o.kind = OP_TRANSPOSE_SQ;
+        o.eb = 4;
+        o.rows = z.rows;
+        o.z = z.p;
+        o.ldz = z.ld;
+        push(o);
     }
 
     void memset0(View z) {
-        if (dry) return;
         Op o;
         o.kind = OP_MEMSET;
         o.eb = eb;
@@ -184,29 +228,37 @@ struct Planner {
         o.cols = z.cols;
         o.z = z.p;
         o.ldz = z.ld;
-        plan->ops.push_back(o);
+        push(o);
     }
 
     static bool vec_ok(const View& v) {
         return ((reinterpret_cast<uintptr_t>(v.p) & 15) == 0) && (v.ld % 4) == 0;
     }
 
-    // One leaf product c (=|+=) a b.
-    bool gemm(View a, View b, View c, int mode) {
-        if (dry || c.rows <= 0 || c.cols <= 0) return true;
-        if (a.cols == 0) {
-            if (mode == TGT_STORE) memset0(c);
-            return true;
-        }
+    static Target make_target(View c, float sign, int mode) {
         Target t;
         t.c = c.p;
         t.ldc = c.ld;
         t.rows = c.rows;
         t.cols = c.cols;
-        t.sign = 1.f;
+        t.sign = sign;
         t.mode = mode;
         t.vec_ok = vec_ok(c) ? 1 : 0;
         t.pad_ = 0;
+        return t;
+    }
+
+    // One leaf product c (=|+=) a b on the tensor cores (FP32: b is held as B^T) or, for FP64,
+    // on the SIMT kernel.
+    bool gemm(View a, View b, View c, int mode) {
+        if (c.rows <= 0 || c.cols <= 0) return true;
+        if (a.cols == 0) {
+            if (mode == TGT_STORE) memset0(c);
+            return true;
+        }
+        if (dry) return true;
+        if (eb == 8) return simt(a, b, c, mode);
+        Target t = make_target(c, 1.f, mode);
         Leaf lf;
         memset(&lf, 0, sizeof(lf));
         lf.a_map = 0;
@@ -217,29 +269,51 @@ struct Planner {
         lf.tgt_count = 1;
         lf.tile_begin = 0;
         Op o;
-        if (eb == 4) {
-            o.kind = OP_GEMM_TF32;
-            o.bn = c.cols <= 128 ? 128 : 256;
-            lf.kblocks = (int)ceil_div(a.cols, tf32_tile_k());
-            lf.tiles_n = (int)ceil_div(c.cols, o.bn);
-            if (!make_map_f32(&o.maps.m[0], a.p, a.rows, a.cols, a.ld, 32, tf32_tile_m()) ||
-                !make_map_f32(&o.maps.m[1], b.p, b.rows, b.cols, b.ld, 32, 32)) {
-                err = "tensor map encoding failed (alignment?)";
-                return false;
-            }
-            o.items = (int)(ceil_div(c.rows, tf32_tile_m()) * lf.tiles_n);
-        } else {
-            o.kind = OP_GEMM_F64;
-            lf.kblocks = a.cols;
-            lf.tiles_n = (int)ceil_div(c.cols, F64_BN);
-            MatRef refs[2] = {{a.p, a.ld, a.rows, a.cols}, {b.p, b.ld, b.rows, b.cols}};
-            o.refs_off = put_blob(refs, sizeof(refs));
-            o.items = (int)(ceil_div(c.rows, F64_BM) * lf.tiles_n);
+        o.kind = OP_GEMM_TF32;
+        o.bn = c.cols <= 128 ? 128 : 256;
+        lf.kblocks = (int)ceil_div(a.cols, tf32_tile_k());
+        lf.tiles_n = (int)ceil_div(c.cols, o.bn);
+        if (!make_map_f32(&o.maps.m[0], a.p, a.rows, a.cols, a.ld, 32, tf32_tile_m()) ||
+            !make_map_f32(&o.maps.m[1], b.p, b.rows, b.cols, b.ld, 32, o.bn)) {
+            err = "tensor map encoding failed (alignment?)";
+            return false;
         }
+        o.items = (int)(ceil_div(c.rows, tf32_tile_m()) * lf.tiles_n);
         o.nleaves = 1;
         o.leaves_off = put_blob(&lf, sizeof(lf));
         o.targets_off = put_blob(&t, sizeof(t));
-        plan->ops.push_back(o);
+        push(o);
+        return true;
+    }
+
+    // SIMT product c (=|+=) a b with b in logical orientation (k x n).
+    bool simt(View a, View b, View c, int mode) {
+        if (c.rows <= 0 || c.cols <= 0) return true;
+        if (a.cols == 0) {
+            if (mode == TGT_STORE) memset0(c);
+            return true;
+        }
+        if (dry) return true;
+        Target t = make_target(c, 1.f, mode);
+        Leaf lf;
+        memset(&lf, 0, sizeof(lf));
+        lf.a_map = 0;
+        lf.b_map = 1;
+        lf.m = c.rows;
+        lf.n = c.cols;
+        lf.kblocks = a.cols;
+        lf.tiles_n = (int)ceil_div(c.cols, F64_BN);
+        lf.tgt_count = 1;
+        Op o;
+        o.kind = OP_GEMM_SIMT;
+        o.eb = eb;
+        MatRef refs[2] = {{a.p, a.ld, a.rows, a.cols}, {b.p, b.ld, b.rows, b.cols}};
+        o.refs_off = put_blob(refs, sizeof(refs));
+        o.items = (int)(ceil_div(c.rows, F64_BM) * lf.tiles_n);
+        o.nleaves = 1;
+        o.leaves_off = put_blob(&lf, sizeof(lf));
+        o.targets_off = put_blob(&t, sizeof(t));
+        push(o);
         return true;
     }
 
@@ -254,10 +328,11 @@ struct Planner {
     // Alg. 2 (Sec. 2.2) with fresh temporaries: two operand sums, seven products.
     bool alloc_strassen(View a, View b, View c, int L) {
         View A11 = quad(a, 0), A12 = quad(a, 1), A21 = quad(a, 2), A22 = quad(a, 3);
-        View B11 = quad(b, 0), B12 = quad(b, 1), B21 = quad(b, 2), B22 = quad(b, 3);
+        View B11 = quadB(b, 0), B12 = quadB(b, 1), B21 = quadB(b, 2), B22 = quadB(b, 3);
         View C11 = quad(c, 0), C12 = quad(c, 1), C21 = quad(c, 2), C22 = quad(c, 3);
+        const int k2 = A11.cols;
         const size_t mark = ws_top;
-        View sa = talloc(A11.rows, A11.cols), sb = talloc(B11.rows, B11.cols), P[7];
+        View sa = talloc(A11.rows, k2), sb = tallocB(k2, C11.cols), P[7];
         for (int i = 0; i < 7; ++i) P[i] = talloc(C11.rows, C11.cols);
         bool ok = true;
         add(sa, A11, A22, +1); add(sb, B11, B22, +1); ok &= product(sa, sb, P[0], L - 1);
@@ -280,15 +355,14 @@ struct Planner {
     // level; the U chain reuses the P blocks once they are consumed.
     bool alloc_winograd(View a, View b, View c, int L) {
         View A11 = quad(a, 0), A12 = quad(a, 1), A21 = quad(a, 2), A22 = quad(a, 3);
-        View B11 = quad(b, 0), B12 = quad(b, 1), B21 = quad(b, 2), B22 = quad(b, 3);
+        View B11 = quadB(b, 0), B12 = quadB(b, 1), B21 = quadB(b, 2), B22 = quadB(b, 3);
         View C11 = quad(c, 0), C12 = quad(c, 1), C21 = quad(c, 2), C22 = quad(c, 3);
+        const int m2 = A11.rows, k2 = A11.cols, n2 = C11.cols;
         const size_t mark = ws_top;
-        View S1 = talloc(A11.rows, A11.cols), S2 = talloc(A11.rows, A11.cols), S3 = talloc(A11.rows, A11.cols),
-             S4 = talloc(A11.rows, A11.cols);
-        View T1 = talloc(B11.rows, B11.cols), T2 = talloc(B11.rows, B11.cols), T3 = talloc(B11.rows, B11.cols),
-             T4 = talloc(B11.rows, B11.cols);
+        View S1 = talloc(m2, k2), S2 = talloc(m2, k2), S3 = talloc(m2, k2), S4 = talloc(m2, k2);
+        View T1 = tallocB(k2, n2), T2 = tallocB(k2, n2), T3 = tallocB(k2, n2), T4 = tallocB(k2, n2);
         View P[7];
-        for (int i = 0; i < 7; ++i) P[i] = talloc(C11.rows, C11.cols);
+        for (int i = 0; i < 7; ++i) P[i] = talloc(m2, n2);
         bool ok = true;
         add(S1, A21, A22, +1);
         add(S2, S1, A11, -1);
@@ -319,17 +393,17 @@ struct Planner {
     // Table 2 (Sec. 3.3): two temporaries per level, X (A-quadrant sums, then P1) and Y.
     bool two_temp(View a, View b, View c, int L) {
         View A11 = quad(a, 0), A12 = quad(a, 1), A21 = quad(a, 2), A22 = quad(a, 3);
-        View B11 = quad(b, 0), B12 = quad(b, 1), B21 = quad(b, 2), B22 = quad(b, 3);
+        View B11 = quadB(b, 0), B12 = quadB(b, 1), B21 = quadB(b, 2), B22 = quadB(b, 3);
         View C11 = quad(c, 0), C12 = quad(c, 1), C21 = quad(c, 2), C22 = quad(c, 3);
-        const int m2 = A11.rows, k2 = A11.cols, n2 = B11.cols;
+        const int m2 = A11.rows, k2 = A11.cols, n2 = C11.cols;
         const size_t mark = ws_top;
         View X = talloc(m2, std::max(k2, n2));
-        X.cols = k2;                       // X as an A-quadrant sum
-        View Xp = X;
+        View Xp = X;                           // X as P1 (m2 x n2)
         Xp.cols = n2;
-        Xp.ld = round_up(std::max(n2, 1), 4);  // X as P1 (m2 x n2)
+        Xp.ld = round_up(std::max(n2, 1), 4);
+        X.cols = k2;                           // X as an A-quadrant sum (m2 x k2)
         X.ld = round_up(std::max(k2, 1), 4);
-        View Y = talloc(k2, n2);
+        View Y = tallocB(k2, n2);
         bool ok = true;
         add(X, A11, A21, -1);                  //  1  S3 = A11 - A21      -> X
         add(Y, B22, B12, -1);                  //  2  T3 = B22 - B12      -> Y
@@ -359,10 +433,11 @@ struct Planner {
 
     // Table 3 (Sec. 3.3): temporaries stored in the quadrants of A, B and C.  Sub-products
     // recurse in place too, so each one may overwrite its two operand blocks; the table's
-    // order never reads a block after such a product consumed it.
+    // order never reads a block after such a product consumed it.  Square only: the C22
+    // quadrant holds the B-side values T1 and T4 (held transposed like every B-side value).
     bool in_place(View a, View b, View c, int L) {
         View A11 = quad(a, 0), A12 = quad(a, 1), A21 = quad(a, 2), A22 = quad(a, 3);
-        View B11 = quad(b, 0), B12 = quad(b, 1), B21 = quad(b, 2), B22 = quad(b, 3);
+        View B11 = quadB(b, 0), B12 = quadB(b, 1), B21 = quadB(b, 2), B22 = quadB(b, 3);
         View C11 = quad(c, 0), C12 = quad(c, 1), C21 = quad(c, 2), C22 = quad(c, 3);
         bool ok = true;
         add(C11, A11, A21, -1);                //  1  S3 = A11 - A21      -> C11
@@ -429,7 +504,8 @@ struct Planner {
         return algo == SW_ALGO_STRASSEN ? str : win;
     }
 
-    // FUSED plan for C (m x n) <- A (m x k) B (k x n) at depth L (1..3).
+    // FUSED plan for C (m x n) <- A (m x k) B (k x n) at depth L (1..3).  `B` is in bt storage
+    // on the FP32 path (B^T, n x k).
     bool fused(View A, View B, View C, int L) {
         const ProdTab& T = table(algo);
         const int m = C.rows, n = C.cols, k = A.cols;
@@ -445,8 +521,8 @@ struct Planner {
         for (int w = 0; w < nleaf; ++w) {
             bool pa = true, pb = true;
             int r_a = 0, c_a = 0, r_b = 0, c_b = 0;
-            for (int l = 0, ww = w, div = nleaf / 7; l < L; ++l, div /= 7) {
-                const int p = (ww / div) % 7;
+            for (int l = 0, div = nleaf / 7; l < L; ++l, div /= 7) {
+                const int p = (w / div) % 7;
                 const int qa = T.pure_a_q[p], qb = T.pure_b_q[p];
                 if (qa < 0) pa = false;
                 if (qb < 0) pb = false;
@@ -456,17 +532,22 @@ struct Planner {
                 c_b = c_b * 2 + (qb >= 0 ? (qb & 1) : 0);
             }
             if (pa) { ar[w] = r_a * mb; ac[w] = c_a * kb; } else { slot_a[w] = (short)na++; }
-            if (pb) { br[w] = r_b * kb; bc[w] = c_b * nb; } else { slot_b[w] = (short)nbs++; }
+            if (pb) {  // logical block (r_b, c_b) of B; in bt storage it is block (c_b, r_b) of B^T
+                if (bt) { br[w] = c_b * nb; bc[w] = r_b * kb; } else { br[w] = r_b * kb; bc[w] = c_b * nb; }
+            } else {
+                slot_b[w] = (short)nbs++;
+            }
         }
-        // scratch for the materialised operand sums
+        // scratch for the materialised operand sums: dense slots, row stride = block width
         const size_t mark = ws_top;
         View SA = talloc(std::max(na, 1) * mb, kb);
-        View SB = talloc(std::max(nbs, 1) * kb, nb);
         SA.rows = na * mb;
-        SB.rows = nbs * kb;
-        SA.ld = kb;  // slots are dense: row stride = block width (the pre-add pass writes so)
-        SB.ld = nb;
-        if (dry) { ws_top = mark; return true; }
+        SA.ld = kb;
+        View SB = bt ? talloc(std::max(nbs, 1) * nb, kb) : talloc(std::max(nbs, 1) * kb, nb);
+        SB.rows = bt ? nbs * nb : nbs * kb;
+        SB.ld = bt ? kb : nb;
+        (void)mark;
+        if (dry) return true;
         if (na > 0) {
             Op o;
             o.kind = OP_PREADD;
@@ -474,9 +555,9 @@ struct Planner {
             PreaddArgs& p = o.pre;
             memset(&p, 0, sizeof(p));
             p.x = A.p; p.ldx = A.ld; p.rows = m; p.cols = k; p.brows = mb; p.bcols = kb;
-            p.out = SA.p; p.L = L; p.alg = algo == SW_ALGO_STRASSEN ? 1 : 2; p.bside = 0;
+            p.out = SA.p; p.L = L; p.alg = algo == SW_ALGO_STRASSEN ? 1 : 2; p.bside = 0; p.bt = 0;
             for (int w = 0; w < 343; ++w) p.slot_of[w] = w < nleaf ? slot_a[w] : (short)-1;
-            plan->ops.push_back(o);
+            push(o);
         }
         if (nbs > 0) {
             Op o;
@@ -484,10 +565,12 @@ struct Planner {
             o.eb = eb;
             PreaddArgs& p = o.pre;
             memset(&p, 0, sizeof(p));
-            p.x = B.p; p.ldx = B.ld; p.rows = k; p.cols = n; p.brows = kb; p.bcols = nb;
-            p.out = SB.p; p.L = L; p.alg = algo == SW_ALGO_STRASSEN ? 1 : 2; p.bside = 1;
+            p.x = B.p; p.ldx = B.ld;
+            if (bt) { p.rows = n; p.cols = k; p.brows = nb; p.bcols = kb; }
+            else { p.rows = k; p.cols = n; p.brows = kb; p.bcols = nb; }
+            p.out = SB.p; p.L = L; p.alg = algo == SW_ALGO_STRASSEN ? 1 : 2; p.bside = 1; p.bt = bt ? 1 : 0;
             for (int w = 0; w < 343; ++w) p.slot_of[w] = w < nleaf ? slot_b[w] : (short)-1;
-            plan->ops.push_back(o);
+            push(o);
         }
         memset0(C);
         // leaves (leaf-major order) and their Kronecker-product targets
@@ -502,14 +585,13 @@ struct Planner {
             if (slot_a[w] < 0) { lf.a_map = 0; lf.a_row = ar[w]; lf.a_col = ac[w]; }
             else { lf.a_map = 2; lf.a_row = slot_a[w] * mb; lf.a_col = 0; }
             if (slot_b[w] < 0) { lf.b_map = 1; lf.b_row = br[w]; lf.b_col = bc[w]; }
-            else { lf.b_map = 3; lf.b_row = slot_b[w] * kb; lf.b_col = 0; }
+            else { lf.b_map = 3; lf.b_row = slot_b[w] * (bt ? nb : kb); lf.b_col = 0; }
             lf.m = mb;
             lf.n = nb;
             lf.kblocks = eb == 4 ? kb / tf32_tile_k() : kb;
             lf.tiles_n = (int)ceil_div(nb, bn);
             lf.tile_begin = items;
             lf.tgt_begin = (int)tg.size();
-            // enumerate target combinations over the levels
             int digits[3] = {0, 0, 0};
             for (int l = 0, div = nleaf / 7; l < L; ++l, div /= 7) digits[l] = (w / div) % 7;
             int idx[3] = {0, 0, 0};
@@ -522,18 +604,9 @@ struct Planner {
                     c = c * 2 + (t.q & 1);
                     sg *= (float)t.s;
                 }
-                Target t;
-                t.c = C.p + ((long long)r * mb * C.ld + (long long)c * nb) * eb;
-                t.ldc = C.ld;
-                t.rows = std::min(mb, m - r * mb);
-                t.cols = std::min(nb, n - c * nb);
-                t.sign = sg;
-                t.mode = TGT_ATOMIC;
-                t.vec_ok = 0;
-                t.pad_ = 0;
-                View tv = {static_cast<char*>(t.c), C.ld, 0, 0};
-                t.vec_ok = vec_ok(tv) ? 1 : 0;
-                if (t.rows > 0 && t.cols > 0) tg.push_back(t);
+                View cv = sub(C, (long long)r * mb, (long long)c * nb, std::min(mb, m - r * mb),
+                              std::min(nb, n - c * nb), eb);
+                if (cv.rows > 0 && cv.cols > 0) tg.push_back(make_target(cv, sg, TGT_ATOMIC));
                 int l = L - 1;
                 while (l >= 0 && ++idx[l] == T.ntgt[digits[l]]) { idx[l] = 0; --l; }
                 if (l < 0) break;
@@ -551,19 +624,20 @@ struct Planner {
             o.kind = OP_GEMM_TF32;
             o.bn = bn;
             if (!make_map_f32(&o.maps.m[0], A.p, m, k, A.ld, 32, tf32_tile_m()) ||
-                !make_map_f32(&o.maps.m[1], B.p, k, n, B.ld, 32, 32) ||
+                !make_map_f32(&o.maps.m[1], B.p, n, k, B.ld, 32, bn) ||
                 !make_map_f32(&o.maps.m[2], SA.p, std::max(SA.rows, 1), kb, SA.ld, 32, tf32_tile_m()) ||
-                !make_map_f32(&o.maps.m[3], SB.p, std::max(SB.rows, 1), nb, SB.ld, 32, 32)) {
+                !make_map_f32(&o.maps.m[3], SB.p, std::max(SB.rows, 1), kb, SB.ld, 32, bn)) {
                 err = "tensor map encoding failed";
                 return false;
             }
         } else {
-            o.kind = OP_GEMM_F64;
+            o.kind = OP_GEMM_SIMT;
+            o.eb = 8;
             MatRef refs[4] = {{A.p, A.ld, m, k}, {B.p, B.ld, k, n}, {SA.p, SA.ld, SA.rows, kb},
                               {SB.p, SB.ld, SB.rows, nb}};
             o.refs_off = put_blob(refs, sizeof(refs));
         }
-        plan->ops.push_back(o);
+        push(o);
         return true;
     }
 };
@@ -649,6 +723,7 @@ static sw_status build_plan(sw_handle h, int eb, const void* A, int lda, const v
 
     Planner P;
     P.eb = eb;
+    P.bt = eb == 4;
     P.variant = variant;
     P.dry = dry;
     P.ws_base = h->ws;
@@ -659,67 +734,79 @@ static sw_status build_plan(sw_handle h, int eb, const void* A, int lda, const v
     plan->depth = L;
 
     View Av = {(char*)A, lda, m, k}, Bv = {(char*)B, ldb, k, n}, Cv = {(char*)C, ldc, m, n};
-    const bool aligned = eb == 8 || (Planner::vec_ok(Av) && Planner::vec_ok(Bv) && Planner::vec_ok(Cv));
+    const bool a_ok = eb == 8 || Planner::vec_ok(Av), c_ok = eb == 8 || Planner::vec_ok(Cv);
+    // B in the storage the leaves want: B^T in workspace (FP32), B itself (FP64)
+    auto stage_b = [&](View b, int rows_pad, int cols_pad) -> View {  // logical k x n -> storage
+        if (!P.bt) {
+            if (rows_pad == b.rows && cols_pad == b.cols) return b;
+            View b2 = P.talloc(rows_pad, cols_pad);
+            P.copy_pad(b2, b);
+            return b2;
+        }
+        View bt = P.talloc(cols_pad, rows_pad);
+        P.transpose_into(bt, b);
+        return bt;
+    };
     bool ok = true;
     if (m == 0 || n == 0) {
         ok = true;
     } else if (k == 0) {
         P.memset0(Cv);
-    } else if (L == 0 || algo == SW_ALGO_NAIVE) {
-        if (aligned) {
-            ok = P.gemm(Av, Bv, Cv, TGT_STORE);
-        } else {  // pack into aligned workspace
-            View a2 = P.talloc(m, k), b2 = P.talloc(k, n), c2 = P.talloc(m, n);
-            P.copy_pad(a2, Av); P.copy_pad(b2, Bv);
-            ok = P.gemm(a2, b2, c2, TGT_STORE);
-            P.copy_pad(Cv, c2);
-        }
-    } else if (sched == SW_SCHED_FUSED) {
-        if (aligned) {
-            ok = P.fused(Av, Bv, Cv, L);
-        } else {
-            View a2 = P.talloc(m, k), b2 = P.talloc(k, n), c2 = P.talloc(m, n);
-            P.copy_pad(a2, Av); P.copy_pad(b2, Bv);
-            ok = P.fused(a2, b2, c2, L);
-            P.copy_pad(Cv, c2);
-        }
+    } else if (L == 0 || algo == SW_ALGO_NAIVE || sched == SW_SCHED_FUSED) {
+        View a2 = Av, c2 = Cv;
+        if (!a_ok) { a2 = P.talloc(m, k); P.copy_pad(a2, Av); }
+        if (!c_ok) c2 = P.talloc(m, n);
+        View b2 = stage_b(Bv, k, n);
+        if (L == 0 || algo == SW_ALGO_NAIVE) ok = P.gemm(a2, b2, c2, TGT_STORE);
+        else ok = P.fused(a2, b2, c2, L);
+        if (!c_ok) P.copy_pad(Cv, c2);
     } else if (L > 5) {
         return fail(h, SW_EUNSUPPORTED, "materialised schedules stop at depth 5 (7^5 leaf launches); raise the cutoff");
     } else {
-        // materialised schedules: halve exactly; column splits must stay 16-byte aligned (FP32)
+        // materialised schedules: halve exactly; FP32 column splits must stay 16-byte aligned
         const long long gm = 1LL << L, gk = eb == 4 ? 4LL << L : 1LL << L, gn = gk;
         const bool exact = m % gm == 0 && k % gk == 0 && n % gn == 0;
-        if (exact && aligned) {
-            ok = P.product(Av, Bv, Cv, L);
-        } else if (odd == SW_PEEL && aligned) {
+        const bool inpl = sched == SW_SCHED_IN_PLACE;
+        if (exact && a_ok && c_ok && (eb == 8 || Planner::vec_ok(Bv))) {
+            View bs = Bv;
+            if (P.bt) {
+                if (inpl) { P.transpose_square(Bv); bs.rows = n; bs.cols = k; }  // B <- B^T in place
+                else bs = stage_b(Bv, k, n);
+            }
+            ok = P.product(Av, bs, Cv, L);
+        } else if (odd == SW_PEEL && a_ok && c_ok && (eb == 8 || Planner::vec_ok(Bv))) {
             long long me = m / gm * gm, ke = k / gk * gk, ne = n / gn * gn;
-            if (sched == SW_SCHED_IN_PLACE) { me = ke = ne = std::min(me, std::min(ke, ne)); }
+            if (inpl) me = ke = ne = std::min(me, std::min(ke, ne));
             auto sub = [&](View v, long long r0, long long c0, long long rows, long long cols) {
-                View s = v;
-                s.p = v.p + (r0 * v.ld + c0) * eb;
-                s.rows = (int)rows;
-                s.cols = (int)cols;
-                return s;
+                return Planner::sub(v, r0, c0, rows, cols, eb);
             };
-            // edge products first: they read the even blocks, which IN_PLACE overwrites
-            if (me < m) ok &= P.gemm(sub(Av, me, 0, m - me, k), Bv, sub(Cv, me, 0, m - me, n), TGT_STORE);
-            if (ne < n) ok &= P.gemm(sub(Av, 0, 0, me, k), sub(Bv, 0, ne, k, n - ne), sub(Cv, 0, ne, me, n - ne),
+            // edge products first (SIMT: thin, and they read the even blocks IN_PLACE overwrites)
+            if (me < m) ok &= P.simt(sub(Av, me, 0, m - me, k), Bv, sub(Cv, me, 0, m - me, n), TGT_STORE);
+            if (ne < n) ok &= P.simt(sub(Av, 0, 0, me, k), sub(Bv, 0, ne, k, n - ne), sub(Cv, 0, ne, me, n - ne),
                                      TGT_STORE);
             if (me > 0 && ne > 0) {
-                if (ke > 0) ok &= P.product(sub(Av, 0, 0, me, ke), sub(Bv, 0, 0, ke, ne), sub(Cv, 0, 0, me, ne), L);
-                else P.memset0(sub(Cv, 0, 0, me, ne));
+                if (ke > 0) {
+                    View be = sub(Bv, 0, 0, ke, ne), bs = be;
+                    if (P.bt) {
+                        if (inpl) { P.transpose_square(be); bs.rows = (int)ne; bs.cols = (int)ke; }
+                        else bs = stage_b(be, (int)ke, (int)ne);
+                    }
+                    ok &= P.product(sub(Av, 0, 0, me, ke), bs, sub(Cv, 0, 0, me, ne), L);
+                } else {
+                    P.memset0(sub(Cv, 0, 0, me, ne));
+                }
                 if (ke < k)
-                    ok &= P.gemm(sub(Av, 0, ke, me, k - ke), sub(Bv, ke, 0, k - ke, ne), sub(Cv, 0, 0, me, ne),
+                    ok &= P.simt(sub(Av, 0, ke, me, k - ke), sub(Bv, ke, 0, k - ke, ne), sub(Cv, 0, 0, me, ne),
                                  ke > 0 ? TGT_ADD : TGT_STORE);
             }
         } else {
-            // pad into aligned copies whose sizes halve exactly L times
-            const int mp = (int)round_up(m, gm), kp = (int)round_up(k, gk), np = (int)round_up(n, gn);
-            const int sq = (int)round_up(std::max(m, std::max(k, n)), std::max(gm, gk));
-            View a2 = P.talloc(sched == SW_SCHED_IN_PLACE ? sq : mp, sched == SW_SCHED_IN_PLACE ? sq : kp);
-            View b2 = P.talloc(sched == SW_SCHED_IN_PLACE ? sq : kp, sched == SW_SCHED_IN_PLACE ? sq : np);
-            View c2 = P.talloc(sched == SW_SCHED_IN_PLACE ? sq : mp, sched == SW_SCHED_IN_PLACE ? sq : np);
-            P.copy_pad(a2, Av); P.copy_pad(b2, Bv);
+            // pad into aligned copies whose sizes halve exactly L times (zero fill, Sec. 3.1)
+            int mp = (int)round_up(m, gm), kp = (int)round_up(k, gk), np = (int)round_up(n, gn);
+            if (inpl) mp = kp = np = (int)round_up(std::max(m, std::max(k, n)), std::max(gm, gk));
+            View a2 = P.talloc(mp, kp);
+            P.copy_pad(a2, Av);
+            View b2 = stage_b(Bv, kp, np);
+            View c2 = P.talloc(mp, np);
             ok = P.product(a2, b2, c2, L);
             View cv = c2;
             cv.rows = m;
@@ -742,10 +829,17 @@ static sw_status run_plan(sw_handle h, Plan* plan, cudaStream_t s) {
                                      o.nleaves, reinterpret_cast<const Target*>(blob + o.targets_off), o.items,
                                      h->d_err, h->sms, s);
                 break;
-            case OP_GEMM_F64:
-                e = launch_gemm_f64(reinterpret_cast<const MatRef*>(blob + o.refs_off),
-                                    reinterpret_cast<const Leaf*>(blob + o.leaves_off), o.nleaves,
-                                    reinterpret_cast<const Target*>(blob + o.targets_off), o.items, h->sms * 8, s);
+            case OP_GEMM_SIMT:
+                e = launch_gemm_simt(o.eb, reinterpret_cast<const MatRef*>(blob + o.refs_off),
+                                     reinterpret_cast<const Leaf*>(blob + o.leaves_off), o.nleaves,
+                                     reinterpret_cast<const Target*>(blob + o.targets_off), o.items, h->sms * 8, s);
+                break;
+            case OP_TRANSPOSE:
+                e = launch_transpose_pad(o.rows, o.cols, static_cast<float*>(o.z), o.ldz,
+                                         static_cast<const float*>(o.x), o.ldx, o.src_rows, o.src_cols, s);
+                break;
+            case OP_TRANSPOSE_SQ:
+                e = launch_transpose_inplace(o.rows, static_cast<float*>(o.z), o.ldz, s);
                 break;
             case OP_ADDSUB:
                 e = launch_addsub(o.eb, o.rows, o.cols, o.z, o.ldz, o.x, o.ldx, o.y, o.ldy, o.sy, s);

@@ -6,10 +6,12 @@
 //
 // FP32 operands are staged by TMA into 128-byte-swizzled shared memory and consumed by
 // tcgen05.mma.kind::tf32 (the tensor core reads each FP32 operand as TF32: its 10 leading
-// mantissa bits); products accumulate in FP32 in tensor memory.
+// mantissa bits); products accumulate in FP32 in tensor memory.  Both operands are K-major:
+// A as stored (m x k, row-major) and B as its transpose B^T (n x k, row-major) -- kind::tf32
+// does not take an N-major B, so the planner hands this kernel B^T views.
 //
 // CTA = 6 warps, persistent over work items (one item = one BM x BN output tile of one leaf):
-//   warp 0      TMA producer: A tile (BM x BK, K-major) + B tile (BK x BN, N-major) per stage
+//   warp 0      TMA producer: A tile (BM x BK) + B^T tile (BN x BK) per stage, both K-major
 //   warp 1      TMEM allocator + MMA issuer (one thread), BK/8 MMAs of K = 8 per stage
 //   warps 2..5  epilogue: tcgen05.ld 32 columns at a time, sign, store / add into the targets
 // Two TMEM accumulators (2 x BN columns) let the epilogue of tile i overlap the MMAs of i+1.
@@ -31,13 +33,13 @@ template <int BN>
 struct TfCfg {
     static constexpr int STAGES = (BN == 256) ? 4 : 6;
     static constexpr int A_BYTES = TF_BM * TF_BK * 4;   // 16 KB
-    static constexpr int B_BYTES = TF_BK * BN * 4;      // 32 KB (BN 256) / 16 KB (BN 128)
+    static constexpr int B_BYTES = BN * TF_BK * 4;      // 32 KB (BN 256) / 16 KB (BN 128)
     static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
     static constexpr int TMEM_COLS = 2 * BN;
     static constexpr int BAR_OFF = STAGES * STAGE_BYTES;
     static constexpr int SMEM_BYTES = BAR_OFF + 256 + 1024;  // + barriers + alignment slack
-    // instruction descriptor: D F32, A/B TF32, A K-major, B MN-major, N = BN, M = 128
-    static constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | (0u << 15) | (1u << 16) |
+    // instruction descriptor: D F32, A/B TF32, both K-major, N = BN, M = 128
+    static constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | (0u << 15) | (0u << 16) |
                                       ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(TF_BM >> 4) << 24);
 };
 
@@ -165,8 +167,8 @@ __global__ void __launch_bounds__(192, 1)
                 const CUtensorMap* mb = pick_map(maps, gmaps, __ldg(&L->b_map));
                 const int a_row = __ldg(&L->a_row) + ip.tm * TF_BM;
                 const int a_col = __ldg(&L->a_col);
-                const int b_row = __ldg(&L->b_row);
-                const int b_col = __ldg(&L->b_col) + ip.tn * BN;
+                const int b_row = __ldg(&L->b_row) + ip.tn * BN;  // B^T: rows are N
+                const int b_col = __ldg(&L->b_col);                // B^T: columns are K
                 const int kb_n = __ldg(&L->kblocks);
                 if (((a_col | b_col) & 3) != 0) {  // TMA x coordinate must be 16-byte aligned
                     set_error(err, ERR_ALIGN);
@@ -179,9 +181,7 @@ __global__ void __launch_bounds__(192, 1)
                     uint8_t* dA = sA + stage * Cfg::A_BYTES;
                     uint8_t* dB = sB + stage * Cfg::B_BYTES;
                     tma_load_2d(dA, ma, &full[stage], a_col + kb * TF_BK, a_row);
-#pragma unroll
-                    for (int c = 0; c < BN / 32; ++c)
-                        tma_load_2d(dB + c * (TF_BK * 128), mb, &full[stage], b_col + c * 32, b_row + kb * TF_BK);
+                    tma_load_2d(dB, mb, &full[stage], b_col + kb * TF_BK, b_row);
                     ++issued;
                     if (++stage == Cfg::STAGES) { stage = 0; phase ^= 1u; }
                 }
@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(192, 1)
 #pragma unroll
                     for (int kk = 0; kk < TF_BK / 8; ++kk) {
                         const uint64_t ad = make_sdesc(a_addr + kk * 32, 16, 1024, SWZ_128B);
-                        const uint64_t bd = make_sdesc(b_addr + kk * 1024, TF_BK * 128, 1024, SWZ_128B);
+                        const uint64_t bd = make_sdesc(b_addr + kk * 32, 16, 1024, SWZ_128B);
                         mma_tf32(d_tmem, ad, bd, Cfg::IDESC, (kb | kk) != 0 ? 1u : 0u);
                     }
                     mma_commit(&empty[stage]);  // stage is free once these MMAs have read it

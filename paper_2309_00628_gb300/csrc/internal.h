@@ -27,10 +27,17 @@ cudaError_t launch_gemm_tf32(int bn, const MapSet& maps, const CUtensorMap* gmap
 int tf32_tile_m();
 int tf32_tile_k();
 
-// FP64 SIMT leaf GEMM: same leaf / target descriptors, a_map / b_map index `refs`.
-cudaError_t launch_gemm_f64(const MatRef* refs, const Leaf* leaves, int nleaves, const Target* targets,
-                            int total_items, int grid, cudaStream_t stream);
+// SIMT leaf GEMM (FP64, or FP32 when elem_bytes == 4): same leaf / target descriptors,
+// a_map / b_map index `refs`, B stored as is (k x n); Leaf::kblocks is the inner dimension.
+cudaError_t launch_gemm_simt(int elem_bytes, const MatRef* refs, const Leaf* leaves, int nleaves,
+                             const Target* targets, int total_items, int grid, cudaStream_t stream);
 constexpr int F64_BM = 64, F64_BN = 64;
+
+// out (out_rows x out_cols) <- x^T, zero outside the source extent (src_rows x src_cols).
+cudaError_t launch_transpose_pad(int out_rows, int out_cols, float* out, long long ldo, const float* x,
+                                 long long ldx, int src_rows, int src_cols, cudaStream_t s);
+// x (n x n view) <- x^T in place.
+cudaError_t launch_transpose_inplace(int n, float* x, long long ld, cudaStream_t s);
 
 // Z = X + sy * Y elementwise on strided views (FP32 or FP64 per elem_bytes).
 cudaError_t launch_addsub(int elem_bytes, int rows, int cols, void* z, long long ldz, const void* x, long long ldx,
@@ -50,6 +57,7 @@ struct PreaddArgs {
     int brows, bcols;    // leaf block extent
     void* out;
     int L, alg, bside;
+    int bt;              // B side stored as B^T (quadrants 12 and 21 swap roles)
     short slot_of[343];  // leaf word -> output slot, -1 = pure (not written)
 };
 cudaError_t launch_preadd(int elem_bytes, const PreaddArgs& a, cudaStream_t stream);

@@ -7,7 +7,10 @@
 //                at once: the S1..S4 / T1..T4 chains of the BDPZ form (Sec. 2.3) or Strassen's
 //                sums (Sec. 2.2), composed over L levels, for every leaf whose operand is not a
 //                plain block.
-//  * gemm_f64    register-tiled FP64 SIMT GEMM for the FP64 path's leaves (Alg. 1 per tile).
+//  * gemm_simt   register-tiled SIMT GEMM: the FP64 path's leaves (Alg. 1 per tile) and the
+//                FP32 peeling fix-ups.
+//  * transposes  B -> B^T (with zero fill) and in-place square transposes: the TF32 tensor-core
+//                path consumes B as B^T.
 //  * norms       FP64 max-reductions for max|C - R|, max|A|, max|B|.
 #include <cuda_runtime.h>
 #include <cstdint>
@@ -175,7 +178,10 @@ struct SlotWriter {
     }
 };
 
-template <int ALG, bool BSIDE, int L, typename V>
+// BT: the grid is stored transposed (B^T), so its top-right quadrant holds the transpose of
+// the logical X21 and its bottom-left the transpose of X12; the forms are linear, so applying
+// them to the transposed blocks yields the transposed operand.
+template <int ALG, bool BSIDE, bool BT, int L, typename V>
 struct Expand {
     template <class W>
     static __device__ __forceinline__ void run(const V (&v)[1 << (2 * L)], int w, W& wr) {
@@ -186,16 +192,19 @@ struct Expand {
 #pragma unroll
             for (int r = 0; r < H; ++r)
 #pragma unroll
-                for (int c = 0; c < H; ++c)
-                    s[r * H + c] = form<ALG, BSIDE, V>(p, v[r * N + c], v[r * N + c + H], v[(r + H) * N + c],
+                for (int c = 0; c < H; ++c) {
+                    const V& tr = v[r * N + c + H];
+                    const V& bl = v[(r + H) * N + c];
+                    s[r * H + c] = form<ALG, BSIDE, V>(p, v[r * N + c], BT ? bl : tr, BT ? tr : bl,
                                                        v[(r + H) * N + c + H]);
-            Expand<ALG, BSIDE, L - 1, V>::run(s, w * 7 + p, wr);
+                }
+            Expand<ALG, BSIDE, BT, L - 1, V>::run(s, w * 7 + p, wr);
         }
     }
 };
 
-template <int ALG, bool BSIDE, typename V>
-struct Expand<ALG, BSIDE, 0, V> {
+template <int ALG, bool BSIDE, bool BT, typename V>
+struct Expand<ALG, BSIDE, BT, 0, V> {
     template <class W>
     static __device__ __forceinline__ void run(const V (&v)[1], int w, W& wr) {
         wr.put(w, v[0]);
@@ -203,7 +212,7 @@ struct Expand<ALG, BSIDE, 0, V> {
 };
 
 // One thread = VEC consecutive columns of one row position inside the leaf block.
-template <typename T, int VEC, int L, int ALG, bool BSIDE>
+template <typename T, int VEC, int L, int ALG, bool BSIDE, bool BT>
 __global__ void __launch_bounds__(256) preadd_kernel(const PreaddArgs a) {
     using V = Vec<T, VEC>;
     constexpr int N = 1 << L;
@@ -240,18 +249,20 @@ __global__ void __launch_bounds__(256) preadd_kernel(const PreaddArgs a) {
         wr.slot_stride = (long long)a.brows * a.bcols * sizeof(T);
         wr.off = ((long long)i * a.bcols + j) * sizeof(T);
         wr.valid = true;
-        Expand<ALG, BSIDE, L, V>::run(v, 0, wr);
+        Expand<ALG, BSIDE, BT, L, V>::run(v, 0, wr);
     }
 }
 
 template <typename T, int VEC, int L>
 static void preadd_dispatch_alg(const PreaddArgs& a, int grid, cudaStream_t s) {
     if (a.alg == 2) {
-        if (a.bside) preadd_kernel<T, VEC, L, 2, true><<<grid, 256, 0, s>>>(a);
-        else preadd_kernel<T, VEC, L, 2, false><<<grid, 256, 0, s>>>(a);
+        if (a.bside && a.bt) preadd_kernel<T, VEC, L, 2, true, true><<<grid, 256, 0, s>>>(a);
+        else if (a.bside) preadd_kernel<T, VEC, L, 2, true, false><<<grid, 256, 0, s>>>(a);
+        else preadd_kernel<T, VEC, L, 2, false, false><<<grid, 256, 0, s>>>(a);
     } else {
-        if (a.bside) preadd_kernel<T, VEC, L, 1, true><<<grid, 256, 0, s>>>(a);
-        else preadd_kernel<T, VEC, L, 1, false><<<grid, 256, 0, s>>>(a);
+        if (a.bside && a.bt) preadd_kernel<T, VEC, L, 1, true, true><<<grid, 256, 0, s>>>(a);
+        else if (a.bside) preadd_kernel<T, VEC, L, 1, true, false><<<grid, 256, 0, s>>>(a);
+        else preadd_kernel<T, VEC, L, 1, false, false><<<grid, 256, 0, s>>>(a);
     }
 }
 
@@ -280,15 +291,16 @@ cudaError_t launch_preadd(int elem_bytes, const PreaddArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// ============================================================== FP64 leaf GEMM (SIMT)
+// ============================================================== SIMT leaf GEMM (FP64 leaves; FP32 thin fix-ups)
 // 64 x 64 output tile per CTA, 256 threads, 4 x 4 outputs per thread, k blocks of 16.
-constexpr int F64_BK = 16;
+constexpr int SIMT_BK = 16;
 
-__global__ void __launch_bounds__(256) gemm_f64_kernel(const MatRef* __restrict__ refs, const Leaf* __restrict__ leaves,
-                                                       int nleaves, const Target* __restrict__ targets,
-                                                       int total_items) {
-    __shared__ double As[F64_BK][F64_BM + 1];
-    __shared__ double Bs[F64_BK][F64_BN + 1];
+template <typename T>
+__global__ void __launch_bounds__(256) gemm_simt_kernel(const MatRef* __restrict__ refs, const Leaf* __restrict__ leaves,
+                                                        int nleaves, const Target* __restrict__ targets,
+                                                        int total_items) {
+    __shared__ T As[SIMT_BK][F64_BM + 1];
+    __shared__ T Bs[SIMT_BK][F64_BN + 1];
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     for (int item = blockIdx.x; item < total_items; item += gridDim.x) {
         int lo = 0, hi = nleaves - 1;
@@ -300,32 +312,31 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const MatRef* __restrict_
         const int local = item - Lf.tile_begin;
         const int tm = local / Lf.tiles_n, tn = local - tm * Lf.tiles_n;
         const MatRef A = refs[Lf.a_map], B = refs[Lf.b_map];
-        const double* Ap = reinterpret_cast<const double*>(A.p);
-        const double* Bp = reinterpret_cast<const double*>(B.p);
+        const T* Ap = reinterpret_cast<const T*>(A.p);
+        const T* Bp = reinterpret_cast<const T*>(B.p);
         const int K = Lf.kblocks;  // for this kernel: the inner dimension in elements
-        double acc[4][4];
+        T acc[4][4];
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
-        for (int k0 = 0; k0 < K; k0 += F64_BK) {
-            // A tile: rows tm*64.., cols k0.. ; B tile: rows k0.., cols tn*64..
-            for (int e = threadIdx.x; e < F64_BM * F64_BK; e += 256) {
-                const int r = e / F64_BK, c = e - r * F64_BK;
+            for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+        for (int k0 = 0; k0 < K; k0 += SIMT_BK) {
+            for (int e = threadIdx.x; e < F64_BM * SIMT_BK; e += 256) {
+                const int r = e / SIMT_BK, c = e - r * SIMT_BK;
                 const int gr = Lf.a_row + tm * F64_BM + r, gc = Lf.a_col + k0 + c;
                 const bool in = (tm * F64_BM + r) < Lf.m && (k0 + c) < K && gr < A.rows && gc < A.cols;
-                As[c][r] = in ? Ap[gr * A.ld + gc] : 0.0;
+                As[c][r] = in ? Ap[gr * A.ld + gc] : T(0);
             }
-            for (int e = threadIdx.x; e < F64_BK * F64_BN; e += 256) {
+            for (int e = threadIdx.x; e < SIMT_BK * F64_BN; e += 256) {
                 const int r = e / F64_BN, c = e - r * F64_BN;
                 const int gr = Lf.b_row + k0 + r, gc = Lf.b_col + tn * F64_BN + c;
                 const bool in = (k0 + r) < K && (tn * F64_BN + c) < Lf.n && gr < B.rows && gc < B.cols;
-                Bs[r][c] = in ? Bp[gr * B.ld + gc] : 0.0;
+                Bs[r][c] = in ? Bp[gr * B.ld + gc] : T(0);
             }
             __syncthreads();
 #pragma unroll
-            for (int kk = 0; kk < F64_BK; ++kk) {
-                double a[4], b[4];
+            for (int kk = 0; kk < SIMT_BK; ++kk) {
+                T a[4], b[4];
 #pragma unroll
                 for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
 #pragma unroll
@@ -339,8 +350,8 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const MatRef* __restrict_
         }
         for (int t = 0; t < Lf.tgt_count; ++t) {
             const Target tg = targets[Lf.tgt_begin + t];
-            double* c = reinterpret_cast<double*>(tg.c);
-            const double s = (double)tg.sign;
+            T* c = reinterpret_cast<T*>(tg.c);
+            const T s = (T)tg.sign;
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 const int r = tm * F64_BM + ty * 4 + i;
@@ -349,8 +360,8 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const MatRef* __restrict_
                 for (int j = 0; j < 4; ++j) {
                     const int cc = tn * F64_BN + tx * 4 + j;
                     if (cc >= tg.cols || cc >= Lf.n) continue;
-                    double* p = c + (long long)r * tg.ldc + cc;
-                    const double v = s * acc[i][j];
+                    T* p = c + (long long)r * tg.ldc + cc;
+                    const T v = s * acc[i][j];
                     if (tg.mode == TGT_STORE) *p = v;
                     else if (tg.mode == TGT_ATOMIC) atomicAdd(p, v);
                     else *p += v;
@@ -360,11 +371,67 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const MatRef* __restrict_
     }
 }
 
-cudaError_t launch_gemm_f64(const MatRef* refs, const Leaf* leaves, int nleaves, const Target* targets,
-                            int total_items, int grid, cudaStream_t stream) {
+cudaError_t launch_gemm_simt(int elem_bytes, const MatRef* refs, const Leaf* leaves, int nleaves,
+                             const Target* targets, int total_items, int grid, cudaStream_t stream) {
     if (total_items <= 0) return cudaSuccess;
     if (grid > total_items) grid = total_items;
-    gemm_f64_kernel<<<grid, 256, 0, stream>>>(refs, leaves, nleaves, targets, total_items);
+    if (elem_bytes == 8) gemm_simt_kernel<double><<<grid, 256, 0, stream>>>(refs, leaves, nleaves, targets, total_items);
+    else gemm_simt_kernel<float><<<grid, 256, 0, stream>>>(refs, leaves, nleaves, targets, total_items);
+    return cudaGetLastError();
+}
+
+// ============================================================== transposes (FP32)
+// out (out_rows x out_cols) <- x^T with zero fill: out[r][c] = x[c][r] if c < src_rows and
+// r < src_cols, else 0.  32 x 32 tiles through shared memory, coalesced on both sides.
+__global__ void transpose_pad_kernel(float* __restrict__ out, long long ldo, int out_rows, int out_cols,
+                                     const float* __restrict__ x, long long ldx, int src_rows, int src_cols) {
+    __shared__ float t[32][33];
+    const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+    for (int i = threadIdx.y; i < 32; i += 8) {
+        const int c = c0 + i, r = r0 + threadIdx.x;  // x row c, column r
+        t[i][threadIdx.x] = (c < src_rows && r < src_cols) ? x[c * ldx + r] : 0.f;
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += 8) {
+        const int r = r0 + i, c = c0 + threadIdx.x;
+        if (r < out_rows && c < out_cols) out[r * ldo + c] = t[threadIdx.x][i];
+    }
+}
+
+cudaError_t launch_transpose_pad(int out_rows, int out_cols, float* out, long long ldo, const float* x,
+                                 long long ldx, int src_rows, int src_cols, cudaStream_t s) {
+    if (out_rows <= 0 || out_cols <= 0) return cudaSuccess;
+    dim3 grid((out_cols + 31) / 32, (out_rows + 31) / 32), block(32, 8);
+    transpose_pad_kernel<<<grid, block, 0, s>>>(out, ldo, out_rows, out_cols, x, ldx, src_rows, src_cols);
+    return cudaGetLastError();
+}
+
+// In-place transpose of an n x n view: tile pair (bi, bj), bi <= bj, swapped through shared memory.
+__global__ void transpose_inplace_kernel(float* __restrict__ x, long long ld, int n) {
+    const int bi = blockIdx.y, bj = blockIdx.x;
+    if (bi > bj) return;
+    __shared__ float t1[32][33], t2[32][33];
+    for (int i = threadIdx.y; i < 32; i += 8) {
+        const int r = bi * 32 + i, c = bj * 32 + threadIdx.x;
+        if (r < n && c < n) t1[i][threadIdx.x] = x[r * ld + c];
+        const int r2 = bj * 32 + i, c2 = bi * 32 + threadIdx.x;
+        if (bi != bj && r2 < n && c2 < n) t2[i][threadIdx.x] = x[r2 * ld + c2];
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += 8) {
+        // block (bi, bj) <- (block (bj, bi))^T ; block (bj, bi) <- (block (bi, bj))^T
+        const int r = bi * 32 + i, c = bj * 32 + threadIdx.x;
+        if (r < n && c < n) x[r * ld + c] = (bi == bj) ? t1[threadIdx.x][i] : t2[threadIdx.x][i];
+        const int r2 = bj * 32 + i, c2 = bi * 32 + threadIdx.x;
+        if (bi != bj && r2 < n && c2 < n) x[r2 * ld + c2] = t1[threadIdx.x][i];
+    }
+}
+
+cudaError_t launch_transpose_inplace(int n, float* x, long long ld, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const int nb = (n + 31) / 32;
+    dim3 grid(nb, nb), block(32, 8);
+    transpose_inplace_kernel<<<grid, block, 0, s>>>(x, ld, n);
     return cudaGetLastError();
 }
 

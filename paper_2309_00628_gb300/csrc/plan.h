@@ -42,7 +42,8 @@ struct Target {
 struct Leaf {
     int a_map, b_map;  // tensor-map indices
     int a_row, a_col;  // origin of the A operand in its map (row, column)
-    int b_row, b_col;  // origin of the B operand in its map
+    int b_row, b_col;  // origin of the B operand in its map; for the TF32 kernel the map holds
+                       // B^T, so b_row indexes N and b_col indexes K
     int m, n;          // extent of the product (tiles_m = ceil(m/BM), tiles_n = ceil(n/BN))
     int kblocks;       // number of BK-deep k blocks
     int tgt_begin, tgt_count;
