@@ -1,0 +1,353 @@
+#!/usr/bin/env python3
+"""Effective TFLOP/s (2 m n k / t) of the Strassen-Winograd product on one GB300, beside the
+plain tensor-core GEMM of the same library and the FP64 CPU oracle.
+
+Workload (default): one FP32 product C = A B, square n = 8192, A and B i.i.d. uniform[-1, 1]
+(PCG64 seeds 0 and 1), TF32 leaves with FP32 accumulation.  A step is one whole product
+through the C ABI (sw_smm): B -> B^T, the operand-sum pass, the grouped leaf GEMM with the
+post-additions in its epilogue.  Inputs (256 MiB each) exceed the 129 MB L2, so no flush is
+needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank runs its own product on its own GPU (replicas, weak scaling);
+rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2309_00628_gb300 import inputs  # noqa: E402
+
+TF32_OVER_BF16 = 1.1 / 2.25  # nominal dense TF32 : BF16 tensor rate of the GB300
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--n", type=int, default=8192)
+    p.add_argument("--algo", choices=["winograd", "strassen", "naive"], default="winograd")
+    p.add_argument("--sched", choices=["fused", "two_temp", "in_place", "alloc"], default="fused")
+    p.add_argument("--cutoff", type=int, default=0, help="recursion cutoff; 0 = the library's choice")
+    p.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-oracle sample budget")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--sweep", action="store_true", help="print plain and L = 1..3 timings, no JSON line")
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------- helpers
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[5], f[6], f[7], f[8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[2 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def traffic_from_profiles(kernel_file: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary, if it matches the current kernel."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", f"{workload}.md")
+    src = os.path.join(ROOT, "paper_2309_00628_gb300", "csrc", kernel_file)
+    try:
+        text = open(path).read()
+        sha = hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
+    except OSError:
+        return None
+    m = re.search(r"kernel_source_sha1:\s*([0-9a-f]+)", text)
+    t = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not m or not t or m.group(1) != sha:
+        return None
+    return float(t.group(1))
+
+
+def leaf_flops(n: int, L: int) -> float:
+    return 2.0 * (n >> L) ** 3 * 7 ** L
+
+
+# ---------------------------------------------------------------- reference arm: the CPU oracle
+def run_reference(args, rank: int):
+    if rank != 0:
+        return
+    import oracle
+    n = args.n
+    A, B = inputs.pair(n, n, n, "uniform", seed=0, dtype=np.float32)
+    A64, B64 = A.astype(np.float64), B.astype(np.float64)
+    threads = oracle.max_threads()
+    t0 = time.perf_counter()
+    oracle.naive_mt(A64[:threads], B64, threads)
+    rate = 2.0 * threads * n * n / max(time.perf_counter() - t0, 1e-6)
+    budget = max(2.0, min(args.cpu_seconds, 150.0 / max(args.steps + args.warmup, 1)))
+    rows = int(max(threads, min(n, rate * budget / (2.0 * n * n))))
+    rng = np.random.Generator(np.random.PCG64(7))
+    times = []
+    for i in range(args.warmup + args.steps):
+        sel = rng.choice(n, rows, replace=False)
+        t0 = time.perf_counter()
+        oracle.naive_mt(A64[sel], B64, threads)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    tot = sum(times)
+    value = 2.0 * rows * n * n * len(times) / tot / 1e12
+    line = {
+        "impl": "reference", "metric": "effective TFLOP/s (2mnk/t), Winograd vs plain GEMM, same error",
+        "value": value, "unit": "TFLOP/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * tot / len(times), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"FP32 product n={n} (uniform[-1,1]); CPU oracle sample", "n": n},
+        "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": threads, "kind": "oracle",
+                         "sample": f"{rows} of {n} rows of C = A B per step (Alg. 1, FP64, OpenMP over rows)"},
+        "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- our arm
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+    from paper_2309_00628_gb300 import swmm
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl", rank=rank, world_size=world)
+    swmm.load(build_if_missing=True)
+    h = swmm.sw_create(0)
+    stream = torch.cuda.current_stream()
+    sp = swmm._stream_ptr(stream)
+    n = args.n
+    algo = {"winograd": swmm.SW_ALGO_WINOGRAD, "strassen": swmm.SW_ALGO_STRASSEN, "naive": swmm.SW_ALGO_NAIVE}[args.algo]
+    sched = {"fused": swmm.SW_SCHED_FUSED, "two_temp": swmm.SW_SCHED_TWO_TEMP, "in_place": swmm.SW_SCHED_IN_PLACE,
+             "alloc": swmm.SW_SCHED_ALLOC}[args.sched]
+    variant = algo | sched | swmm.SW_LEAF_TF32
+    st, L = swmm.sw_mm_depth(n, n, n, args.cutoff, variant, 4)
+    swmm.check(h, st)
+
+    A, B = inputs.pair(n, n, n, "uniform", seed=0, dtype=np.float32)
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    dC = torch.empty((n, n), dtype=torch.float32, device="cuda")
+    p = lambda t: __import__("ctypes").c_void_p(t.data_ptr())
+
+    def product(v, cutoff):
+        swmm.check(h, swmm.sw_smm(h, p(dA), n, p(dB), n, p(dC), n, n, n, n, cutoff, v, sp))
+
+    def timed(v, cutoff, steps, warmup, clocks=None, profile=False):
+        for _ in range(warmup):
+            product(v, cutoff)
+        swmm.check(h, swmm.sw_sync(h, sp))
+        if profile:
+            swmm.sw_profile(h, True)
+            swmm.sw_profile_read(h)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        if clocks:
+            clocks.start()
+            time.sleep(0.3)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+        ev[0].record(stream)
+        for i in range(steps):
+            product(v, cutoff)
+            ev[i + 1].record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        clk = clocks.stop() if clocks else None
+        swmm.check(h, swmm.sw_sync(h, sp))
+        prof = None
+        if profile:
+            _, prof = swmm.sw_profile_read(h)
+            swmm.sw_profile(h, False)
+        per = [ev[i].elapsed_time(ev[i + 1]) for i in range(steps)]
+        total = ev[0].elapsed_time(ev[steps])
+        return total, per, clk, prof
+
+    if args.sweep:
+        rows = []
+        for name, v, c in [("plain", swmm.SW_ALGO_NAIVE, 0)] + [
+                (f"{a}-L{l}", alg | swmm.SW_SCHED_FUSED, n >> l)
+                for a, alg in (("winograd", swmm.SW_ALGO_WINOGRAD), ("strassen", swmm.SW_ALGO_STRASSEN))
+                for l in (1, 2, 3)]:
+            tot, per, _, prof = timed(v, c, max(args.steps // 4, 10), args.warmup, profile=True)
+            ms = tot / max(args.steps // 4, 10)
+            g = prof["gemm_tf32"]
+            row = {"variant": name, "ms": round(ms, 4), "eff_tflops": round(2 * n ** 3 / ms / 1e9, 1),
+                   "gemm_ms_per_launch": round(g[1] / max(g[0], 1), 4),
+                   "kernels": {k: [a, round(b, 3)] for k, a, b in ((k, *prof[k]) for k in prof) if a}}
+            rows.append(row)
+            if rank == 0:
+                print(json.dumps(row), flush=True)
+        return
+
+    K, W = args.steps, max(args.warmup, 3)
+    clocks = ClockSampler(local)
+    total, per, clk, prof = timed(variant, args.cutoff, K, W, clocks=clocks, profile=True)
+    # plain tensor-core GEMM of the same library, same size, same timing
+    total0, per0, _, prof0 = timed(swmm.SW_ALGO_NAIVE, 0, K, W, profile=True)
+    if dist:
+        t = torch.tensor([total, total0], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total, total0 = float(t[0]), float(t[1])
+    flop = 2.0 * n ** 3
+    value = flop * K * world / (total / 1e3) / 1e12
+    value0 = flop * K * world / (total0 / 1e3) / 1e12
+
+    # dominant kernel: the grouped TF32 leaf GEMM
+    gl, gms = prof["gemm_tf32"]
+    launches = sum(v[0] for k, v in prof.items() if k != "memset")
+    achieved = leaf_flops(n, L) / (gms / gl / 1e3) / 1e12 if gl else None
+    pk = peaks()
+    peak, peak_src = (pk["bf16_tflops"] * TF32_OVER_BF16, "of measured (bf16 burst x nominal TF32/BF16)") \
+        if pk else (1900.0 * TF32_OVER_BF16, "of fallback")
+
+    # end to end: host operands, copies inside the timed region (rank-local)
+    e2e = None
+    if not args.no_e2e:
+        hA = torch.from_numpy(A).pin_memory()
+        hB = torch.from_numpy(B).pin_memory()
+        hC = torch.empty((n, n), dtype=torch.float32).pin_memory()
+        ke = max(min(K // 4, 50), 5)
+        for i in range(W + ke):
+            if i == W:
+                t0 = time.perf_counter()
+            swmm.check(h, swmm.sw_smm_host(h, p(hA), n, p(hB), n, p(hC), n, n, n, n, args.cutoff, variant, sp))
+        te = time.perf_counter() - t0
+        e2e = {"value": flop * ke * world / te / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": 2 * n * n * 4,
+               "d2h_bytes_per_step": n * n * 4}
+
+    # CPU oracle on this machine: timed sample rows, also the reference for the error report
+    cpu = None
+    err = {}
+    if rank == 0:
+        import oracle
+        threads = oracle.max_threads()
+        A64, B64 = A.astype(np.float64), B.astype(np.float64)
+        t0 = time.perf_counter()
+        oracle.naive_mt(A64[:threads], B64, threads)
+        rate = 2.0 * threads * n * n / max(time.perf_counter() - t0, 1e-6)
+        rows = int(max(threads, min(n, rate * args.cpu_seconds / (2.0 * n * n))))
+        sel = np.sort(np.random.Generator(np.random.PCG64(7)).choice(n, rows, replace=False))
+        t0 = time.perf_counter()
+        R = oracle.naive_mt(A64[sel], B64, threads)
+        tc = time.perf_counter() - t0
+        cpu = {"value": 2.0 * rows * n * n / tc / 1e12, "unit": "TFLOP/s", "cores": threads, "kind": "oracle",
+               "sample": f"{rows} random rows of the n={n} product (Alg. 1, FP64, OpenMP over rows), {tc:.1f} s"}
+        amax, bmax = float(np.max(np.abs(A))), float(np.max(np.abs(B)))
+        idx = torch.from_numpy(sel).cuda()
+        for name, v, c in (("winograd", variant, args.cutoff), ("plain", swmm.SW_ALGO_NAIVE, 0)):
+            product(v, c)
+            swmm.check(h, swmm.sw_sync(h, sp))
+            Cr = dC[idx].double().cpu().numpy()
+            err[name] = float(np.max(np.abs(Cr - R)) / (n * amax * bmax))
+
+    if rank == 0:
+        traffic = traffic_from_profiles("gemm_tf32.cu", f"gemm_tf32_winograd_n{n}_L{L}")
+        lat = sorted(per)
+        line = {
+            "metric": "effective TFLOP/s (2mnk/t), Winograd vs plain GEMM, same error",
+            "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": total / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "tf32", "data": "synthetic",
+            "config": {"workload": f"single FP32 product n={n}, uniform[-1,1], {args.algo} {args.sched} "
+                                   f"L={L}, TF32 leaves, FP32 accumulation",
+                       "n": n, "depth": L, "algo": args.algo, "schedule": args.sched,
+                       "l2": "inputs 256 MiB each exceed the 129 MB L2; no flush"},
+            "p50_ms": statistics.median(lat), "p99_ms": lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)],
+            "plain_gemm": {"value": value0, "unit": "TFLOP/s", "ms_per_step": total0 / K,
+                           "p50_ms": statistics.median(per0)},
+            "speedup_vs_plain": value / value0,
+            "error": {"winograd": err.get("winograd"), "plain": err.get("plain"),
+                      "metric": "max|C - C_oracle| / (n max|A| max|B|) on the sampled rows"},
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                         "kernel": "gemm_tf32_kernel (grouped leaf GEMM)", "peak_source": peak_src,
+                         "algorithmic_flops_per_launch": leaf_flops(n, L),
+                         "avg_launch_ms": gms / gl if gl else None},
+            "kernels_in_step": {k: {"launches_per_step": v[0] / K, "ms_per_step": v[1] / K}
+                                for k, v in prof.items() if v[0]},
+            "gpu_launches": launches,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    swmm.sw_destroy(h)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

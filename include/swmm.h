@@ -33,8 +33,9 @@
  *               SW_PEEL           peel the trailing rows / columns / inner indices that are not a
  *                                 multiple of the split granularity and fix them up with thin
  *                                 products
- *   leaf        SW_LEAF_TF32      FP32 inputs, TF32 tensor-core products (operands rounded to
- *                                 nearest), FP32 accumulation
+ *   leaf        SW_LEAF_TF32      FP32 inputs, TF32 tensor-core products (the tensor core reads
+ *                                 each FP32 operand as TF32, keeping its 10 leading mantissa
+ *                                 bits), FP32 accumulation
  *               SW_LEAF_BF16X3    FP32 inputs split as hi = bf16(x), lo = bf16(x - hi); products
  *                                 hi*hi + hi*lo + lo*hi with FP32 accumulation (FP32-level accuracy)
  *   The FP64 entry points ignore the leaf group and always use FP64 leaves.
@@ -130,6 +131,16 @@ sw_status sw_sync(sw_handle h, void *stream);
 sw_status sw_error_norms(sw_handle h, int elem_bytes, int m, int n, int k, const void *A, int lda,
                          const void *B, int ldb, const void *C, int ldc, const double *R, int ldr,
                          double *out, void *stream);
+
+/* Measurement support.  While profiling is on, every kernel the library launches is bracketed by
+ * a pair of CUDA events on its launch stream.  sw_profile_read() waits for them and returns, per
+ * kernel kind, the number of launches and the summed device time in milliseconds since the last
+ * read (then resets).  Kinds: 0 tensor-core leaf GEMM, 1 SIMT leaf GEMM, 2 block addition,
+ * 3 padded copy, 4 operand-sum pass, 5 memset, 6 transpose, 7 in-place transpose.
+ * `nkinds` is the length of both output arrays (entries beyond 8 are set to 0). */
+#define SW_PROFILE_KINDS 8
+sw_status sw_profile(sw_handle h, int enable);
+sw_status sw_profile_read(sw_handle h, int nkinds, int *launches, double *ms);
 
 #ifdef __cplusplus
 }

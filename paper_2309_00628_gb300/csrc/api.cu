@@ -658,8 +658,24 @@ struct sw_handle_s {
     // device buffers of the host-operand entry point
     char* io = nullptr;
     size_t io_bytes = 0;
+    // profiling: event pairs around every launch while enabled
+    bool prof = false;
+    struct ProfRec { int kind; cudaEvent_t e0, e1; };
+    std::vector<ProfRec> prof_live;
+    std::vector<cudaEvent_t> prof_free;
     std::mutex mu;
 };
+
+static cudaEvent_t prof_event(sw_handle h) {
+    if (!h->prof_free.empty()) {
+        cudaEvent_t e = h->prof_free.back();
+        h->prof_free.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
 
 static sw_status fail(sw_handle h, sw_status s, const std::string& msg) {
     if (h) h->last_error = msg;
@@ -823,6 +839,12 @@ static sw_status run_plan(sw_handle h, Plan* plan, cudaStream_t s) {
     char* blob = static_cast<char*>(plan->d_blob);
     for (const Op& o : plan->ops) {
         cudaError_t e = cudaSuccess;
+        sw_handle_s::ProfRec rec = {(int)o.kind, nullptr, nullptr};
+        if (h->prof) {
+            rec.e0 = prof_event(h);
+            rec.e1 = prof_event(h);
+            cudaEventRecord(rec.e0, s);
+        }
         switch (o.kind) {
             case OP_GEMM_TF32:
                 e = launch_gemm_tf32(o.bn, o.maps, nullptr, reinterpret_cast<const Leaf*>(blob + o.leaves_off),
@@ -853,6 +875,10 @@ static sw_status run_plan(sw_handle h, Plan* plan, cudaStream_t s) {
             case OP_MEMSET:
                 e = cudaMemset2DAsync(o.z, (size_t)o.ldz * o.eb, 0, (size_t)o.cols * o.eb, (size_t)o.rows, s);
                 break;
+        }
+        if (h->prof) {
+            cudaEventRecord(rec.e1, s);
+            h->prof_live.push_back(rec);
         }
         if (e != cudaSuccess) return cuda_fail(h, e, "kernel launch");
     }
@@ -925,6 +951,8 @@ sw_status sw_destroy(sw_handle h) {
     if (h->ws) cudaFree(h->ws);
     if (h->io) cudaFree(h->io);
     if (h->d_err) cudaFree(h->d_err);
+    for (auto& r : h->prof_live) { cudaEventDestroy(r.e0); cudaEventDestroy(r.e1); }
+    for (auto e : h->prof_free) cudaEventDestroy(e);
     delete h;
     return SW_OK;
 }
@@ -1011,6 +1039,32 @@ sw_status sw_sync(sw_handle h, void* stream) {
         if (code == ERR_ALIGN) return fail(h, SW_ECUDA, "kernel rejected a misaligned TMA coordinate");
         return fail(h, SW_ETIMEOUT, "bounded device wait expired (code " + std::to_string(code) + ")");
     }
+    return SW_OK;
+}
+
+sw_status sw_profile(sw_handle h, int enable) {
+    if (!h) return SW_EINVAL;
+    std::lock_guard<std::mutex> lock(h->mu);
+    h->prof = enable != 0;
+    return SW_OK;
+}
+
+sw_status sw_profile_read(sw_handle h, int nkinds, int* launches, double* ms) {
+    if (!h || nkinds < 0 || (nkinds > 0 && (!launches || !ms))) return SW_EINVAL;
+    std::lock_guard<std::mutex> lock(h->mu);
+    for (int i = 0; i < nkinds; ++i) { launches[i] = 0; ms[i] = 0.0; }
+    cudaError_t err = cudaSuccess;
+    for (auto& r : h->prof_live) {
+        cudaError_t e = cudaEventSynchronize(r.e1);
+        float t = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, r.e0, r.e1);
+        if (e != cudaSuccess) err = e;
+        if (r.kind >= 0 && r.kind < nkinds) { launches[r.kind] += 1; ms[r.kind] += t; }
+        h->prof_free.push_back(r.e0);
+        h->prof_free.push_back(r.e1);
+    }
+    h->prof_live.clear();
+    if (err != cudaSuccess) return cuda_fail(h, err, "profile read");
     return SW_OK;
 }
 

@@ -57,8 +57,10 @@ def load(build_if_missing: bool = False):
     lib.sw_smm_host.argtypes = mm
     lib.sw_sync.argtypes = [_V, _V]
     lib.sw_error_norms.argtypes = [_V, _I, _I, _I, _I, _V, _I, _V, _I, _V, _I, _V, _I, _P(ctypes.c_double), _V]
+    lib.sw_profile.argtypes = [_V, _I]
+    lib.sw_profile_read.argtypes = [_V, _I, _P(_I), _P(ctypes.c_double)]
     for name in ("sw_create", "sw_destroy", "sw_mm_workspace_size", "sw_mm_depth", "sw_smm", "sw_dmm",
-                 "sw_smm_host", "sw_sync", "sw_error_norms"):
+                 "sw_smm_host", "sw_sync", "sw_error_norms", "sw_profile", "sw_profile_read"):
         getattr(lib, name).restype = _I
     _lib = lib
     return lib
@@ -114,6 +116,22 @@ def sw_error_norms(h, elem_bytes, m, n, k, A, lda, B, ldb, C, ldc, R, ldr, strea
     out = (ctypes.c_double * 3)()
     st = load().sw_error_norms(h, elem_bytes, m, n, k, A, lda, B, ldb, C, ldc, R, ldr, out, stream)
     return st, [out[0], out[1], out[2]]
+
+
+PROFILE_KINDS = ["gemm_tf32", "gemm_simt", "addsub", "copy_pad", "preadd", "memset", "transpose", "transpose_sq"]
+
+
+def sw_profile(h, enable: bool) -> int:
+    return load().sw_profile(h, 1 if enable else 0)
+
+
+def sw_profile_read(h):
+    """(status, {kind: (launches, total_ms)}) since the last read."""
+    n = len(PROFILE_KINDS)
+    launches = (ctypes.c_int * n)()
+    ms = (ctypes.c_double * n)()
+    st = load().sw_profile_read(h, n, launches, ms)
+    return st, {PROFILE_KINDS[i]: (launches[i], ms[i]) for i in range(n)}
 
 
 def check(h, status: int) -> None:
