@@ -163,3 +163,13 @@ def mm(h, A, B, cutoff: int = 0, variant: int = SW_ALGO_WINOGRAD, out=None, stre
     if sync:
         check(h, sw_sync(h, _stream_ptr(stream)))
     return C
+
+
+def sw_smm_noalloc(A, lda, B, ldb, C, ldc, m, n, k, stream=None) -> int:
+    """The no-allocation FP32 Winograd product (see include/swmm.h): all temporaries live in
+    the library's static device array, so callers that cannot allocate device memory can use it."""
+    fn = load().sw_smm_noalloc
+    if fn.argtypes is None:
+        fn.argtypes = [_V, _I, _V, _I, _V, _I, _I, _I, _I, _V]
+        fn.restype = _I
+    return fn(A, lda, B, ldb, C, ldc, m, n, k, stream)
