@@ -14,6 +14,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -63,6 +64,17 @@ bool make_map_f32(CUtensorMap* m, const void* base, int rows, int cols, long lon
 }
 
 inline long long round_up(long long x, long long a) { return (x + a - 1) / a * a; }
+
+// Tile-width override for tuning sweeps (SWMM_TF32_BN = 128 or 256); 0 = the planner's choice.
+int bn_override() {
+    static int v = -1;
+    if (v < 0) {
+        const char* e = getenv("SWMM_TF32_BN");
+        v = e ? atoi(e) : 0;
+        if (v != 128 && v != 256) v = 0;
+    }
+    return v;
+}
 inline long long ceil_div(long long x, long long a) { return (x + a - 1) / a; }
 
 // ------------------------------------------------------------------ plan
@@ -72,8 +84,8 @@ struct Op {
     OpKind kind;
     // grouped GEMM
     MapSet maps;
-    int bn = 256, nleaves = 0, items = 0;
-    size_t leaves_off = 0, targets_off = 0, refs_off = 0;
+    int bn = 256, nleaves = 0, items = 0, ntmaps = 0;
+    size_t leaves_off = 0, targets_off = 0, refs_off = 0, tmaps_off = 0;
     // elementwise
     int eb = 4, rows = 0, cols = 0, src_rows = 0, src_cols = 0;
     void* z = nullptr;
@@ -235,7 +247,7 @@ struct Planner {
         return ((reinterpret_cast<uintptr_t>(v.p) & 15) == 0) && (v.ld % 4) == 0;
     }
 
-    static Target make_target(View c, float sign, int mode) {
+    static Target make_target(View c, float sign, int mode, int map = -1) {
         Target t;
         t.c = c.p;
         t.ldc = c.ld;
@@ -244,8 +256,31 @@ struct Planner {
         t.sign = sign;
         t.mode = mode;
         t.vec_ok = vec_ok(c) ? 1 : 0;
-        t.pad_ = 0;
+        t.map = map;
         return t;
+    }
+
+    // Tensor maps of the target blocks of one GEMM launch (TMA store / reduce-add epilogue),
+    // one per distinct block.
+    std::vector<CUtensorMap> tmaps;
+    std::vector<View> tmap_views;
+    int target_map(View c) {
+        if (eb != 4 || !vec_ok(c) || c.rows <= 0 || c.cols <= 0) return -1;
+        for (size_t i = 0; i < tmap_views.size(); ++i) {
+            const View& v = tmap_views[i];
+            if (v.p == c.p && v.ld == c.ld && v.rows == c.rows && v.cols == c.cols) return (int)i;
+        }
+        CUtensorMap m;
+        if (!make_map_f32(&m, c.p, c.rows, c.cols, c.ld, 32, 32)) return -1;
+        tmaps.push_back(m);
+        tmap_views.push_back(c);
+        return (int)tmaps.size() - 1;
+    }
+    void flush_tmaps(Op& o) {
+        o.ntmaps = (int)tmaps.size();
+        o.tmaps_off = tmaps.empty() ? 0 : put_blob(tmaps.data(), tmaps.size() * sizeof(CUtensorMap));
+        tmaps.clear();
+        tmap_views.clear();
     }
 
     // One leaf product c (=|+=) a b on the tensor cores (FP32: b is held as B^T) or, for FP64,
@@ -258,7 +293,7 @@ struct Planner {
         }
         if (dry) return true;
         if (eb == 8) return simt(a, b, c, mode);
-        Target t = make_target(c, 1.f, mode);
+        Target t = make_target(c, 1.f, mode, target_map(c));
         Leaf lf;
         memset(&lf, 0, sizeof(lf));
         lf.a_map = 0;
@@ -270,7 +305,7 @@ struct Planner {
         lf.tile_begin = 0;
         Op o;
         o.kind = OP_GEMM_TF32;
-        o.bn = c.cols <= 128 ? 128 : 256;
+        o.bn = bn_override() ? bn_override() : (c.cols <= 128 ? 128 : 256);
         lf.kblocks = (int)ceil_div(a.cols, tf32_tile_k());
         lf.tiles_n = (int)ceil_div(c.cols, o.bn);
         if (!make_map_f32(&o.maps.m[0], a.p, a.rows, a.cols, a.ld, 32, tf32_tile_m()) ||
@@ -282,6 +317,7 @@ struct Planner {
         o.nleaves = 1;
         o.leaves_off = put_blob(&lf, sizeof(lf));
         o.targets_off = put_blob(&t, sizeof(t));
+        flush_tmaps(o);
         push(o);
         return true;
     }
@@ -573,12 +609,11 @@ struct Planner {
             push(o);
         }
         memset0(C);
-        // leaves (leaf-major order) and their Kronecker-product targets
-        std::vector<Leaf> leaves;
+        // leaves and their Kronecker-product targets
+        std::vector<Leaf> base_leaves;
         std::vector<Target> tg;
-        int items = 0;
         const int tm_sz = eb == 4 ? tf32_tile_m() : F64_BM;
-        const int bn = eb == 4 ? (nb <= 128 ? 128 : 256) : F64_BN;
+        const int bn = eb == 4 ? (bn_override() ? bn_override() : (nb <= 128 ? 128 : 256)) : F64_BN;
         for (int w = 0; w < nleaf; ++w) {
             Leaf lf;
             memset(&lf, 0, sizeof(lf));
@@ -590,7 +625,6 @@ struct Planner {
             lf.n = nb;
             lf.kblocks = eb == 4 ? kb / tf32_tile_k() : kb;
             lf.tiles_n = (int)ceil_div(nb, bn);
-            lf.tile_begin = items;
             lf.tgt_begin = (int)tg.size();
             int digits[3] = {0, 0, 0};
             for (int l = 0, div = nleaf / 7; l < L; ++l, div /= 7) digits[l] = (w / div) % 7;
@@ -606,20 +640,44 @@ struct Planner {
                 }
                 View cv = sub(C, (long long)r * mb, (long long)c * nb, std::min(mb, m - r * mb),
                               std::min(nb, n - c * nb), eb);
-                if (cv.rows > 0 && cv.cols > 0) tg.push_back(make_target(cv, sg, TGT_ATOMIC));
+                if (cv.rows > 0 && cv.cols > 0) tg.push_back(make_target(cv, sg, TGT_ATOMIC, target_map(cv)));
                 int l = L - 1;
                 while (l >= 0 && ++idx[l] == T.ntgt[digits[l]]) { idx[l] = 0; --l; }
                 if (l < 0) break;
             }
             lf.tgt_count = (int)tg.size() - lf.tgt_begin;
-            leaves.push_back(lf);
-            items += (int)ceil_div(mb, tm_sz) * lf.tiles_n;
+            base_leaves.push_back(lf);
         }
+        // Work order: position groups of GM x GN tiles, then leaves, then tiles in the group, so
+        // the C tiles every leaf of a group adds into stay in L2 while the group is processed.
+        std::vector<Leaf> leaves;
+        int items = 0;
+        const int tiles_m = (int)ceil_div(mb, tm_sz), tiles_n = (int)ceil_div(nb, bn);
+        const int GM = eb == 8 ? tiles_m : (L == 1 ? 8 : L == 2 ? 4 : 2);
+        const int GN = eb == 8 ? tiles_n : (L == 1 ? 4 : L == 2 ? 4 : 2);
+        for (int gm = 0; gm < tiles_m; gm += GM)
+            for (int gn = 0; gn < tiles_n; gn += GN)
+                for (const Leaf& b0 : base_leaves) {
+                    Leaf lf = b0;
+                    const int r0 = gm * tm_sz, c0 = gn * bn;
+                    lf.m = std::min(GM * tm_sz, mb - r0);
+                    lf.n = std::min(GN * bn, nb - c0);
+                    lf.a_row += r0;
+                    if (bt) lf.b_row += c0;  // B^T: rows are N
+                    else lf.b_col += c0;
+                    lf.c_row0 = r0;
+                    lf.c_col0 = c0;
+                    lf.tiles_n = (int)ceil_div(lf.n, bn);
+                    lf.tile_begin = items;
+                    items += (int)ceil_div(lf.m, tm_sz) * lf.tiles_n;
+                    leaves.push_back(lf);
+                }
         Op o;
         o.nleaves = (int)leaves.size();
         o.items = items;
         o.leaves_off = put_blob(leaves.data(), leaves.size() * sizeof(Leaf));
         o.targets_off = put_blob(tg.data(), tg.size() * sizeof(Target));
+        flush_tmaps(o);
         if (eb == 4) {
             o.kind = OP_GEMM_TF32;
             o.bn = bn;
@@ -848,8 +906,9 @@ static sw_status run_plan(sw_handle h, Plan* plan, cudaStream_t s) {
         switch (o.kind) {
             case OP_GEMM_TF32:
                 e = launch_gemm_tf32(o.bn, o.maps, nullptr, reinterpret_cast<const Leaf*>(blob + o.leaves_off),
-                                     o.nleaves, reinterpret_cast<const Target*>(blob + o.targets_off), o.items,
-                                     h->d_err, h->sms, s);
+                                     o.nleaves, reinterpret_cast<const Target*>(blob + o.targets_off),
+                                     o.ntmaps ? reinterpret_cast<const CUtensorMap*>(blob + o.tmaps_off) : nullptr,
+                                     o.items, h->d_err, h->sms, s);
                 break;
             case OP_GEMM_SIMT:
                 e = launch_gemm_simt(o.eb, reinterpret_cast<const MatRef*>(blob + o.refs_off),

@@ -13,7 +13,10 @@
 // CTA = 6 warps, persistent over work items (one item = one BM x BN output tile of one leaf):
 //   warp 0      TMA producer: A tile (BM x BK) + B^T tile (BN x BK) per stage, both K-major
 //   warp 1      TMEM allocator + MMA issuer (one thread), BK/8 MMAs of K = 8 per stage
-//   warps 2..5  epilogue: tcgen05.ld 32 columns at a time, sign, store / add into the targets
+//   warps 2..5  epilogue: tcgen05.ld 32 columns at a time; each warp stages its 32 x 32 chunk
+//               (with the target's sign) in 128-byte-swizzled shared memory and one lane issues a
+//               TMA store (first writer) or TMA reduce-add (further contributions) per target;
+//               targets without a tensor map fall back to per-thread stores / atomics.
 // Two TMEM accumulators (2 x BN columns) let the epilogue of tile i overlap the MMAs of i+1.
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -36,7 +39,9 @@ struct TfCfg {
     static constexpr int B_BYTES = BN * TF_BK * 4;      // 32 KB (BN 256) / 16 KB (BN 128)
     static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
     static constexpr int TMEM_COLS = 2 * BN;
-    static constexpr int BAR_OFF = STAGES * STAGE_BYTES;
+    static constexpr int STG_OFF = STAGES * STAGE_BYTES;      // epilogue staging: 4 warps x 2 x 4 KB
+    static constexpr int STG_BYTES = 4 * 2 * 4096;
+    static constexpr int BAR_OFF = STG_OFF + STG_BYTES;
     static constexpr int SMEM_BYTES = BAR_OFF + 256 + 1024;  // + barriers + alignment slack
     // instruction descriptor: D F32, A/B TF32, both K-major, N = BN, M = 128
     static constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | (0u << 15) | (0u << 16) |
@@ -113,7 +118,7 @@ template <int BN>
 __global__ void __launch_bounds__(192, 1)
     gemm_tf32_kernel(const __grid_constant__ MapSet maps, const CUtensorMap* __restrict__ gmaps,
                      const Leaf* __restrict__ leaves, int nleaves, const Target* __restrict__ targets,
-                     int total_items, int* err) {
+                     const CUtensorMap* __restrict__ tmaps, int total_items, int* err) {
     using Cfg = TfCfg<BN>;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw_addr = smem_u32(smem_raw);
@@ -233,7 +238,9 @@ __global__ void __launch_bounds__(192, 1)
     } else {
         // ------------------------------------------------------------ epilogue (warps 2..5)
         const int q = warp & 3;  // TMEM lane quarter this warp may access
-        int local = 0;
+        uint8_t* stg = base + Cfg::STG_OFF + (warp - 2) * 8192;  // two 4 KB swizzled buffers
+        int local = 0, chunk_ctr = 0;
+        bool issued_bulk = false;
         for (int item = blockIdx.x; item < total_items; item += gridDim.x, ++local) {
             const ItemPos ip = decode_item(leaves, nleaves, item, BN);
             const Leaf* L = &leaves[ip.leaf];
@@ -242,23 +249,75 @@ __global__ void __launch_bounds__(192, 1)
             if (!mbar_wait(&tfull[acc], acc_phase, err, ERR_WAIT_ACC)) break;
             tc_fence_after();
             const int tb = __ldg(&L->tgt_begin), tc = __ldg(&L->tgt_count);
-            const int row = ip.tm * TF_BM + q * 32 + lane;
+            bool has_pos = false, has_neg = false, all_tma = tmaps != nullptr;
+            for (int t = 0; t < tc; ++t) {
+                const float sg = __ldg(&targets[tb + t].sign);
+                has_pos |= sg > 0.f;
+                has_neg |= sg < 0.f;
+                all_tma &= __ldg(&targets[tb + t].map) >= 0;
+            }
+            const int row_w = __ldg(&L->c_row0) + ip.tm * TF_BM + q * 32;  // this warp's first row
             const uint32_t t_base = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN);
 #pragma unroll 1
             for (int chunk = 0; chunk < BN / 32; ++chunk) {
                 uint32_t r[32];
                 tmem_ld32(t_base + chunk * 32, r);
                 tmem_ld_wait();
-                const int col0 = ip.tn * BN + chunk * 32;
-                for (int t = 0; t < tc; ++t) {
-                    Target tg = targets[tb + t];
-                    store_row32(tg, row, col0, r);
+                const int col0 = __ldg(&L->c_col0) + ip.tn * BN + chunk * 32;
+                if (all_tma) {
+                    const bool mixed = has_pos && has_neg;
+                    uint8_t* bpos;
+                    uint8_t* bneg;
+                    if (mixed) {
+                        if (lane == 0) bulk_wait_read<0>();
+                        bpos = stg;
+                        bneg = stg + 4096;
+                    } else {
+                        if (lane == 0) bulk_wait_read<1>();
+                        bpos = bneg = stg + (chunk_ctr & 1) * 4096;
+                    }
+                    __syncwarp();
+                    // row `lane` of the chunk; 16-byte piece j sits at piece j ^ (row & 7)
+                    const uint32_t row_off = (uint32_t)lane * 128u;
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const uint32_t off = row_off + ((uint32_t)(j ^ (lane & 7)) << 4);
+                        const float4 v = make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
+                                                     __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3]));
+                        if (has_pos) *reinterpret_cast<float4*>(bpos + off) = v;
+                        if (has_neg && (mixed || !has_pos))
+                            *reinterpret_cast<float4*>(bneg + off) = make_float4(-v.x, -v.y, -v.z, -v.w);
+                    }
+                    fence_async_shared();
+                    __syncwarp();
+                    if (lane == 0) {
+                        for (int t = 0; t < tc; ++t) {
+                            const Target& tg = targets[tb + t];
+                            if (row_w >= tg.rows || col0 >= tg.cols) continue;
+                            const CUtensorMap* m = tmaps + tg.map;
+                            const uint8_t* src = tg.sign > 0.f ? bpos : bneg;
+                            if (tg.mode == TGT_STORE) tma_store_2d(m, src, col0, row_w);
+                            else tma_reduce_add_2d(m, src, col0, row_w);
+                        }
+                        bulk_commit();
+                        issued_bulk = true;
+                    }
+                    __syncwarp();
+                    ++chunk_ctr;
+                } else {
+                    for (int t = 0; t < tc; ++t) {
+                        Target tg = targets[tb + t];
+                        store_row32(tg, row_w + lane, col0, r);
+                    }
                 }
             }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&tempty[acc]);
         }
+        // all bulk stores / reductions must be complete before the CTA (and its shared memory) ends
+        if (lane == 0 && issued_bulk) bulk_wait<0>();
+        __syncwarp();
     }
 
     tc_fence_before();
@@ -271,8 +330,8 @@ __global__ void __launch_bounds__(192, 1)
 
 template <int BN>
 static cudaError_t launch_tf32_impl(const MapSet& maps, const CUtensorMap* gmaps, const Leaf* leaves, int nleaves,
-                                    const Target* targets, int total_items, int* err, int grid,
-                                    cudaStream_t stream) {
+                                    const Target* targets, const CUtensorMap* tmaps, int total_items, int* err,
+                                    int grid, cudaStream_t stream) {
     using Cfg = TfCfg<BN>;
     static bool attr_set = false;
     if (!attr_set) {
@@ -283,15 +342,17 @@ static cudaError_t launch_tf32_impl(const MapSet& maps, const CUtensorMap* gmaps
     }
     if (total_items <= 0) return cudaSuccess;
     if (grid > total_items) grid = total_items;
-    gemm_tf32_kernel<BN><<<grid, 192, Cfg::SMEM_BYTES, stream>>>(maps, gmaps, leaves, nleaves, targets,
+    gemm_tf32_kernel<BN><<<grid, 192, Cfg::SMEM_BYTES, stream>>>(maps, gmaps, leaves, nleaves, targets, tmaps,
                                                                   total_items, err);
     return cudaGetLastError();
 }
 
 cudaError_t launch_gemm_tf32(int bn, const MapSet& maps, const CUtensorMap* gmaps, const Leaf* leaves, int nleaves,
-                             const Target* targets, int total_items, int* err, int grid, cudaStream_t stream) {
-    if (bn == 256) return launch_tf32_impl<256>(maps, gmaps, leaves, nleaves, targets, total_items, err, grid, stream);
-    return launch_tf32_impl<128>(maps, gmaps, leaves, nleaves, targets, total_items, err, grid, stream);
+                             const Target* targets, const CUtensorMap* tmaps, int total_items, int* err, int grid,
+                             cudaStream_t stream) {
+    if (bn == 256)
+        return launch_tf32_impl<256>(maps, gmaps, leaves, nleaves, targets, tmaps, total_items, err, grid, stream);
+    return launch_tf32_impl<128>(maps, gmaps, leaves, nleaves, targets, tmaps, total_items, err, grid, stream);
 }
 
 int tf32_tile_m() { return TF_BM; }

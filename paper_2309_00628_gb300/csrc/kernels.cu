@@ -398,9 +398,42 @@ __global__ void transpose_pad_kernel(float* __restrict__ out, long long ldo, int
     }
 }
 
+// Fast path: 64 x 64 tiles, 16-byte loads and stores, when every tile is interior, all leading
+// dimensions are multiples of 4 and both bases are 16-byte aligned.
+__global__ void __launch_bounds__(256) transpose64_kernel(float* __restrict__ out, long long ldo,
+                                                          const float* __restrict__ x, long long ldx) {
+    __shared__ float t[64][65];
+    const int r0 = blockIdx.y * 64, c0 = blockIdx.x * 64;  // tile origin in `out`
+    const int tc = threadIdx.x & 15, tr = threadIdx.x >> 4; // 16 float4 per 64-wide row, 16 rows per pass
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        const int i = tr + 16 * p;  // x row c0 + i, columns r0 + 4 tc ..
+        const float4 v = *reinterpret_cast<const float4*>(x + (long long)(c0 + i) * ldx + r0 + 4 * tc);
+        t[4 * tc + 0][i] = v.x;
+        t[4 * tc + 1][i] = v.y;
+        t[4 * tc + 2][i] = v.z;
+        t[4 * tc + 3][i] = v.w;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        const int r = tr + 16 * p;
+        float4 v = make_float4(t[r][4 * tc + 0], t[r][4 * tc + 1], t[r][4 * tc + 2], t[r][4 * tc + 3]);
+        *reinterpret_cast<float4*>(out + (long long)(r0 + r) * ldo + c0 + 4 * tc) = v;
+    }
+}
+
 cudaError_t launch_transpose_pad(int out_rows, int out_cols, float* out, long long ldo, const float* x,
                                  long long ldx, int src_rows, int src_cols, cudaStream_t s) {
     if (out_rows <= 0 || out_cols <= 0) return cudaSuccess;
+    const bool fast = out_rows == src_cols && out_cols == src_rows && out_rows % 64 == 0 && out_cols % 64 == 0 &&
+                      (ldo % 4) == 0 && (ldx % 4) == 0 &&
+                      ((reinterpret_cast<uintptr_t>(out) | reinterpret_cast<uintptr_t>(x)) & 15) == 0;
+    if (fast) {
+        dim3 grid(out_cols / 64, out_rows / 64);
+        transpose64_kernel<<<grid, 256, 0, s>>>(out, ldo, x, ldx);
+        return cudaGetLastError();
+    }
     dim3 grid((out_cols + 31) / 32, (out_rows + 31) / 32), block(32, 8);
     transpose_pad_kernel<<<grid, block, 0, s>>>(out, ldo, out_rows, out_cols, x, ldx, src_rows, src_cols);
     return cudaGetLastError();

@@ -136,7 +136,8 @@ __global__ void noalloc_describe(swk::Leaf* leaves, swk::Target* targets, float*
         lf.tiles_n = tiles_n;
         lf.tile_begin = p * tiles_per_leaf;
         lf.tgt_begin = t;
-        lf.pad_ = 0;
+        lf.c_row0 = 0;
+        lf.c_col0 = 0;
         int cnt = 0;
         for (int i = 0; i < ntg[p]; ++i) {
             const int q = tq[p][i], r = q >> 1, c = q & 1;
@@ -150,7 +151,7 @@ __global__ void noalloc_describe(swk::Leaf* leaves, swk::Target* targets, float*
             tg.sign = ts[p][i];
             tg.mode = swk::TGT_ATOMIC;
             tg.vec_ok = vec_ok;
-            tg.pad_ = 0;
+            tg.map = -1;
             ++cnt;
         }
         lf.tgt_count = cnt;
@@ -219,7 +220,7 @@ extern "C" sw_status sw_smm_noalloc(const float* A, int lda, const float* B, int
     int sms = 148;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
-        e = swk::launch_gemm_tf32(bn, maps, nullptr, leaves, 7, targets, 7 * tiles_per_leaf, err, sms, s);
+        e = swk::launch_gemm_tf32(bn, maps, nullptr, leaves, 7, targets, nullptr, 7 * tiles_per_leaf, err, sms, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     int code = 0;
     if (e == cudaSuccess) e = cudaMemcpy(&code, err, sizeof(int), cudaMemcpyDeviceToHost);

@@ -36,7 +36,7 @@ struct Target {
     float sign;       // +1 or -1
     int mode;         // TargetMode
     int vec_ok;       // 1 when c is 16-byte aligned and ldc is a multiple of 4 (FP32)
-    int pad_;
+    int map;          // index of the block's tensor map for TMA store / reduce-add (-1: none)
 };
 
 struct Leaf {
@@ -49,7 +49,7 @@ struct Leaf {
     int tgt_begin, tgt_count;
     int tile_begin;    // index of the leaf's first work item
     int tiles_n;
-    int pad_;
+    int c_row0, c_col0;  // position of the leaf's tile (0, 0) inside its target blocks
 };
 
 }  // namespace swk
