@@ -48,6 +48,8 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-oracle sample budget")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--sweep", action="store_true", help="print plain and L = 1..3 timings, no JSON line")
+    p.add_argument("--profile-case", action="store_true",
+                   help="only --warmup products plus one more of the chosen variant (for ncu captures)")
     return p.parse_args()
 
 
@@ -234,6 +236,15 @@ def main():
         per = [ev[i].elapsed_time(ev[i + 1]) for i in range(steps)]
         total = ev[0].elapsed_time(ev[steps])
         return total, per, clk, prof
+
+    if args.profile_case:
+        for _ in range(args.warmup + 1):
+            product(variant, args.cutoff)
+        swmm.check(h, swmm.sw_sync(h, sp))
+        if rank == 0:
+            print(json.dumps({"profile_case": args.algo, "schedule": args.sched, "n": n, "depth": L}), flush=True)
+        swmm.sw_destroy(h)
+        return
 
     if args.sweep:
         rows = []

@@ -84,8 +84,9 @@ struct Op {
     OpKind kind;
     // grouped GEMM
     MapSet maps;
-    int bn = 256, nleaves = 0, items = 0, ntmaps = 0;
-    size_t leaves_off = 0, targets_off = 0, refs_off = 0, tmaps_off = 0;
+    int bn = 256, nleaves = 0, items = 0, ntmaps = 0, nflags = 0;
+    size_t leaves_off = 0, targets_off = 0, refs_off = 0, tmaps_off = 0, flags_off = 0;
+    unsigned epoch = 0;  // launches of this op so far (its ordering counters grow by 4 per launch)
     // elementwise
     int eb = 4, rows = 0, cols = 0, src_rows = 0, src_cols = 0;
     void* z = nullptr;
@@ -257,6 +258,8 @@ struct Planner {
         t.mode = mode;
         t.vec_ok = vec_ok(c) ? 1 : 0;
         t.map = map;
+        t.flag_base = -1;
+        t.flag_cols = 0;
         return t;
     }
 
@@ -608,12 +611,21 @@ struct Planner {
             for (int w = 0; w < 343; ++w) p.slot_of[w] = w < nleaf ? slot_b[w] : (short)-1;
             push(o);
         }
-        memset0(C);
+        // Each C block's first writer (the first leaf, in leaf order, that adds into it) stores
+        // instead of adding; later leaves wait for it tile by tile.  Used at depth 1 on the TF32
+        // path, where the first writer's tiles lead their position group and the waits are short;
+        // deeper levels (many leaves queue behind one writer) and the SIMT FP64 leaf keep a zeroed
+        // C and reduce-adds only.
+        const bool ordered = eb == 4 && L == 1;
+        if (!ordered) memset0(C);
+        const int bn_o = eb == 4 ? (bn_override() ? bn_override() : (nb <= 128 ? 128 : 256)) : F64_BN;
+        std::vector<int> first_writer(1 << (2 * L), -1), flag_base(1 << (2 * L), -1), flag_cols(1 << (2 * L), 0);
+        int nflags = 0;
         // leaves and their Kronecker-product targets
         std::vector<Leaf> base_leaves;
         std::vector<Target> tg;
         const int tm_sz = eb == 4 ? tf32_tile_m() : F64_BM;
-        const int bn = eb == 4 ? (bn_override() ? bn_override() : (nb <= 128 ? 128 : 256)) : F64_BN;
+        const int bn = bn_o;
         for (int w = 0; w < nleaf; ++w) {
             Leaf lf;
             memset(&lf, 0, sizeof(lf));
@@ -640,7 +652,22 @@ struct Planner {
                 }
                 View cv = sub(C, (long long)r * mb, (long long)c * nb, std::min(mb, m - r * mb),
                               std::min(nb, n - c * nb), eb);
-                if (cv.rows > 0 && cv.cols > 0) tg.push_back(make_target(cv, sg, TGT_ATOMIC, target_map(cv)));
+                if (cv.rows > 0 && cv.cols > 0) {
+                    Target t = make_target(cv, sg, TGT_ATOMIC, target_map(cv));
+                    if (ordered) {
+                        const int blk = r * (1 << L) + c;
+                        if (first_writer[blk] < 0) {
+                            first_writer[blk] = w;
+                            flag_cols[blk] = (int)ceil_div(cv.cols, bn_o);
+                            flag_base[blk] = nflags;
+                            nflags += (int)ceil_div(cv.rows, tm_sz) * flag_cols[blk];
+                        }
+                        t.mode = first_writer[blk] == w ? TGT_STORE : TGT_ATOMIC;
+                        t.flag_base = flag_base[blk];
+                        t.flag_cols = flag_cols[blk];
+                    }
+                    tg.push_back(t);
+                }
                 int l = L - 1;
                 while (l >= 0 && ++idx[l] == T.ntgt[digits[l]]) { idx[l] = 0; --l; }
                 if (l < 0) break;
@@ -678,6 +705,11 @@ struct Planner {
         o.leaves_off = put_blob(leaves.data(), leaves.size() * sizeof(Leaf));
         o.targets_off = put_blob(tg.data(), tg.size() * sizeof(Target));
         flush_tmaps(o);
+        if (nflags > 0) {
+            std::vector<unsigned> zeros(nflags, 0u);
+            o.nflags = nflags;
+            o.flags_off = put_blob(zeros.data(), zeros.size() * sizeof(unsigned));
+        }
         if (eb == 4) {
             o.kind = OP_GEMM_TF32;
             o.bn = bn;
@@ -895,7 +927,7 @@ static sw_status build_plan(sw_handle h, int eb, const void* A, int lda, const v
 
 static sw_status run_plan(sw_handle h, Plan* plan, cudaStream_t s) {
     char* blob = static_cast<char*>(plan->d_blob);
-    for (const Op& o : plan->ops) {
+    for (Op& o : plan->ops) {
         cudaError_t e = cudaSuccess;
         sw_handle_s::ProfRec rec = {(int)o.kind, nullptr, nullptr};
         if (h->prof) {
@@ -908,7 +940,8 @@ static sw_status run_plan(sw_handle h, Plan* plan, cudaStream_t s) {
                 e = launch_gemm_tf32(o.bn, o.maps, nullptr, reinterpret_cast<const Leaf*>(blob + o.leaves_off),
                                      o.nleaves, reinterpret_cast<const Target*>(blob + o.targets_off),
                                      o.ntmaps ? reinterpret_cast<const CUtensorMap*>(blob + o.tmaps_off) : nullptr,
-                                     o.items, h->d_err, h->sms, s);
+                                     o.nflags ? reinterpret_cast<unsigned*>(blob + o.flags_off) : nullptr,
+                                     o.nflags ? ++o.epoch : 0u, o.items, h->d_err, h->sms, s);
                 break;
             case OP_GEMM_SIMT:
                 e = launch_gemm_simt(o.eb, reinterpret_cast<const MatRef*>(blob + o.refs_off),
@@ -1095,6 +1128,10 @@ sw_status sw_sync(sw_handle h, void* stream) {
     if (e != cudaSuccess) return cuda_fail(h, e, "error word read");
     if (code != 0) {
         cudaMemset(h->d_err, 0, sizeof(int));
+        {   // an aborted launch leaves ordering counters out of step: rebuild every plan
+            std::lock_guard<std::mutex> lock(h->mu);
+            flush_plans(h);
+        }
         if (code == ERR_ALIGN) return fail(h, SW_ECUDA, "kernel rejected a misaligned TMA coordinate");
         return fail(h, SW_ETIMEOUT, "bounded device wait expired (code " + std::to_string(code) + ")");
     }

@@ -118,7 +118,8 @@ template <int BN>
 __global__ void __launch_bounds__(192, 1)
     gemm_tf32_kernel(const __grid_constant__ MapSet maps, const CUtensorMap* __restrict__ gmaps,
                      const Leaf* __restrict__ leaves, int nleaves, const Target* __restrict__ targets,
-                     const CUtensorMap* __restrict__ tmaps, int total_items, int* err) {
+                     const CUtensorMap* __restrict__ tmaps, unsigned* __restrict__ flags, unsigned epoch,
+                     int total_items, int* err) {
     using Cfg = TfCfg<BN>;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw_addr = smem_u32(smem_raw);
@@ -256,14 +257,34 @@ __global__ void __launch_bounds__(192, 1)
                 has_neg |= sg < 0.f;
                 all_tma &= __ldg(&targets[tb + t].map) >= 0;
             }
-            const int row_w = __ldg(&L->c_row0) + ip.tm * TF_BM + q * 32;  // this warp's first row
+            const int row_t = __ldg(&L->c_row0) + ip.tm * TF_BM;   // the tile's first row in its blocks
+            const int col_t = __ldg(&L->c_col0) + ip.tn * BN;      // the tile's first column
+            const int row_w = row_t + q * 32;                        // this warp's first row
             const uint32_t t_base = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN);
+            // contributions after a block's first write wait for that tile's write to complete
+            bool ordered_ok = true, has_first = false;
+            if (flags) {
+                for (int t = 0; t < tc; ++t) {
+                    const int fb = __ldg(&targets[tb + t].flag_base);
+                    // no counter for a tile that lies outside a truncated block
+                    if (fb < 0 || row_t >= __ldg(&targets[tb + t].rows) || col_t >= __ldg(&targets[tb + t].cols))
+                        continue;
+                    if (__ldg(&targets[tb + t].mode) == TGT_STORE) { has_first = true; continue; }
+                    if (lane == 0) {
+                        const int idx = fb + (row_t / TF_BM) * __ldg(&targets[tb + t].flag_cols) + col_t / BN;
+                        ordered_ok &= wait_counter(flags + idx, 4u * epoch, err, ERR_ORDER);
+                    }
+                }
+                if (lane == 0) fence_async_global();
+                ordered_ok = __shfl_sync(0xffffffffu, ordered_ok ? 1 : 0, 0) != 0;
+            }
 #pragma unroll 1
             for (int chunk = 0; chunk < BN / 32; ++chunk) {
                 uint32_t r[32];
                 tmem_ld32(t_base + chunk * 32, r);
                 tmem_ld_wait();
-                const int col0 = __ldg(&L->c_col0) + ip.tn * BN + chunk * 32;
+                const int col0 = col_t + chunk * 32;
+                if (!ordered_ok) continue;  // an expired wait: the device error word reports it
                 if (all_tma) {
                     const bool mixed = has_pos && has_neg;
                     uint8_t* bpos;
@@ -314,6 +335,24 @@ __global__ void __launch_bounds__(192, 1)
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&tempty[acc]);
+            // first writes done: publish them tile by tile (one count per epilogue warp)
+            if (flags && has_first) {
+                if (lane == 0 && issued_bulk) bulk_wait<0>();  // this warp's TMA stores are complete
+                fence_async_global();                           // ... and ordered before the count,
+                __threadfence();                                // as are per-thread stores
+                __syncwarp();
+                if (lane == 0) {
+                    for (int t = 0; t < tc; ++t) {
+                        const int fb = __ldg(&targets[tb + t].flag_base);
+                        if (fb < 0 || __ldg(&targets[tb + t].mode) != TGT_STORE) continue;
+                        if (row_t >= __ldg(&targets[tb + t].rows) || col_t >= __ldg(&targets[tb + t].cols)) continue;
+                        red_release_add_u32(flags + fb + (row_t / TF_BM) * __ldg(&targets[tb + t].flag_cols) + col_t / BN,
+                                            1u);
+                    }
+                }
+                __syncwarp();
+            }
+            if (!ordered_ok) break;
         }
         // all bulk stores / reductions must be complete before the CTA (and its shared memory) ends
         if (lane == 0 && issued_bulk) bulk_wait<0>();
@@ -330,8 +369,8 @@ __global__ void __launch_bounds__(192, 1)
 
 template <int BN>
 static cudaError_t launch_tf32_impl(const MapSet& maps, const CUtensorMap* gmaps, const Leaf* leaves, int nleaves,
-                                    const Target* targets, const CUtensorMap* tmaps, int total_items, int* err,
-                                    int grid, cudaStream_t stream) {
+                                    const Target* targets, const CUtensorMap* tmaps, unsigned* flags,
+                                    unsigned epoch, int total_items, int* err, int grid, cudaStream_t stream) {
     using Cfg = TfCfg<BN>;
     static bool attr_set = false;
     if (!attr_set) {
@@ -343,16 +382,18 @@ static cudaError_t launch_tf32_impl(const MapSet& maps, const CUtensorMap* gmaps
     if (total_items <= 0) return cudaSuccess;
     if (grid > total_items) grid = total_items;
     gemm_tf32_kernel<BN><<<grid, 192, Cfg::SMEM_BYTES, stream>>>(maps, gmaps, leaves, nleaves, targets, tmaps,
-                                                                  total_items, err);
+                                                                  flags, epoch, total_items, err);
     return cudaGetLastError();
 }
 
 cudaError_t launch_gemm_tf32(int bn, const MapSet& maps, const CUtensorMap* gmaps, const Leaf* leaves, int nleaves,
-                             const Target* targets, const CUtensorMap* tmaps, int total_items, int* err, int grid,
-                             cudaStream_t stream) {
+                             const Target* targets, const CUtensorMap* tmaps, unsigned* flags, unsigned epoch,
+                             int total_items, int* err, int grid, cudaStream_t stream) {
     if (bn == 256)
-        return launch_tf32_impl<256>(maps, gmaps, leaves, nleaves, targets, tmaps, total_items, err, grid, stream);
-    return launch_tf32_impl<128>(maps, gmaps, leaves, nleaves, targets, tmaps, total_items, err, grid, stream);
+        return launch_tf32_impl<256>(maps, gmaps, leaves, nleaves, targets, tmaps, flags, epoch, total_items, err, grid,
+                                     stream);
+    return launch_tf32_impl<128>(maps, gmaps, leaves, nleaves, targets, tmaps, flags, epoch, total_items, err, grid,
+                                 stream);
 }
 
 int tf32_tile_m() { return TF_BM; }

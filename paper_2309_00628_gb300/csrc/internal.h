@@ -23,10 +23,11 @@ struct MatRef {
 
 // Leaf for the pointer-based (FP64) kernels: operands are MatRef indices.
 // tmaps: tensor maps of the target blocks (Target::map indexes it), or nullptr for the
-// per-thread epilogue only.
+// per-thread epilogue only.  flags / epoch: the ordering counters of the targets (Target::flag_base)
+// and this launch's epoch (1, 2, ... per counter array), or nullptr.
 cudaError_t launch_gemm_tf32(int bn, const MapSet& maps, const CUtensorMap* gmaps, const Leaf* leaves, int nleaves,
-                             const Target* targets, const CUtensorMap* tmaps, int total_items, int* err, int grid,
-                             cudaStream_t stream);
+                             const Target* targets, const CUtensorMap* tmaps, unsigned* flags, unsigned epoch,
+                             int total_items, int* err, int grid, cudaStream_t stream);
 int tf32_tile_m();
 int tf32_tile_k();
 

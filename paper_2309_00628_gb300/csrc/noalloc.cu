@@ -152,6 +152,8 @@ __global__ void noalloc_describe(swk::Leaf* leaves, swk::Target* targets, float*
             tg.mode = swk::TGT_ATOMIC;
             tg.vec_ok = vec_ok;
             tg.map = -1;
+            tg.flag_base = -1;
+            tg.flag_cols = 0;
             ++cnt;
         }
         lf.tgt_count = cnt;
@@ -220,7 +222,8 @@ extern "C" sw_status sw_smm_noalloc(const float* A, int lda, const float* B, int
     int sms = 148;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
-        e = swk::launch_gemm_tf32(bn, maps, nullptr, leaves, 7, targets, nullptr, 7 * tiles_per_leaf, err, sms, s);
+        e = swk::launch_gemm_tf32(bn, maps, nullptr, leaves, 7, targets, nullptr, nullptr, 0, 7 * tiles_per_leaf, err,
+                                  sms, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     int code = 0;
     if (e == cudaSuccess) e = cudaMemcpy(&code, err, sizeof(int), cudaMemcpyDeviceToHost);

@@ -23,6 +23,9 @@ enum : int {
     ERR_ORDER = 7,          // an ordered epilogue waited too long for its predecessor
 };
 
+// With ordering counters (flag_base >= 0), the STORE of a tile is the block's first write: its
+// epilogue warps each add 1 to the tile's counter once their stores are complete, and every
+// ATOMIC contribution to the same tile waits until the counter reaches 4 * epoch first.
 enum TargetMode : int {
     TGT_STORE = 0,   // C_block  = sign * P
     TGT_ATOMIC = 1,  // C_block += sign * P  (atomic; several leaves may hit the block at once)
@@ -37,6 +40,8 @@ struct Target {
     int mode;         // TargetMode
     int vec_ok;       // 1 when c is 16-byte aligned and ldc is a multiple of 4 (FP32)
     int map;          // index of the block's tensor map for TMA store / reduce-add (-1: none)
+    int flag_base;    // ordering counters of this block's tiles (-1: unordered)
+    int flag_cols;    // tiles per row of the block (counter index = tile_row * flag_cols + tile_col)
 };
 
 struct Leaf {

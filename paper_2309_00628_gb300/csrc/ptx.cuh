@@ -122,6 +122,38 @@ __device__ __forceinline__ void bulk_wait() {
     asm volatile("cp.async.bulk.wait_group %0;" ::"n"(N) : "memory");
 }
 
+// Order global-memory accesses of the generic proxy against those of the async (TMA) proxy.
+__device__ __forceinline__ void fence_async_global() {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void red_release_add_u32(unsigned* p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Wait until *p >= target.  Bounded like mbar_wait.
+__device__ __forceinline__ bool wait_counter(const unsigned* p, unsigned target, int* err, int code) {
+    if ((int)(ld_acquire_u32(p) - target) >= 0) return true;
+    const unsigned long long t0 = globaltimer();
+    for (uint32_t i = 1;; ++i) {
+        if ((int)(ld_acquire_u32(p) - target) >= 0) return true;
+        if ((i & 63u) == 0) {
+            if (error_raised(err)) return false;
+            if (globaltimer() - t0 > SW_WAIT_NS) {
+                set_error(err, code);
+                return false;
+            }
+        }
+        __nanosleep(64);
+    }
+}
+
 // Make generic-proxy writes to shared memory visible to the async (TMA) proxy.
 __device__ __forceinline__ void fence_async_shared() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
