@@ -248,13 +248,17 @@ def main():
 
     if args.sweep:
         rows = []
+        BF = swmm.SW_LEAF_BF16X3
         for name, v, c in [("plain", swmm.SW_ALGO_NAIVE, 0)] + [
                 (f"{a}-L{l}", alg | swmm.SW_SCHED_FUSED, n >> l)
                 for a, alg in (("winograd", swmm.SW_ALGO_WINOGRAD), ("strassen", swmm.SW_ALGO_STRASSEN))
-                for l in (1, 2, 3)]:
+                for l in (1, 2, 3)] + [("plain-bf16x3", swmm.SW_ALGO_NAIVE | BF, 0),
+                                      ("winograd-L1-bf16x3", swmm.SW_ALGO_WINOGRAD | BF, n >> 1),
+                                      ("winograd-L2-two_temp-bf16x3", swmm.SW_ALGO_WINOGRAD | swmm.SW_SCHED_TWO_TEMP | BF,
+                                       n >> 2)]:
             tot, per, _, prof = timed(v, c, max(args.steps // 4, 10), args.warmup, profile=True)
             ms = tot / max(args.steps // 4, 10)
-            g = prof["gemm_tf32"]
+            g = prof["gemm_bf16x3"] if v & BF else prof["gemm_tf32"]
             row = {"variant": name, "ms": round(ms, 4), "eff_tflops": round(2 * n ** 3 / ms / 1e9, 1),
                    "gemm_ms_per_launch": round(g[1] / max(g[0], 1), 4),
                    "kernels": {k: [a, round(b, 3)] for k, a, b in ((k, *prof[k]) for k in prof) if a}}

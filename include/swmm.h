@@ -135,10 +135,11 @@ sw_status sw_error_norms(sw_handle h, int elem_bytes, int m, int n, int k, const
 /* Measurement support.  While profiling is on, every kernel the library launches is bracketed by
  * a pair of CUDA events on its launch stream.  sw_profile_read() waits for them and returns, per
  * kernel kind, the number of launches and the summed device time in milliseconds since the last
- * read (then resets).  Kinds: 0 tensor-core leaf GEMM, 1 SIMT leaf GEMM, 2 block addition,
- * 3 padded copy, 4 operand-sum pass, 5 memset, 6 transpose, 7 in-place transpose.
- * `nkinds` is the length of both output arrays (entries beyond 8 are set to 0). */
-#define SW_PROFILE_KINDS 8
+ * read (then resets).  Kinds: 0 tensor-core leaf GEMM (TF32), 1 SIMT leaf GEMM, 2 block addition,
+ * 3 padded copy, 4 operand-sum pass, 5 memset, 6 transpose, 7 in-place transpose, 8 bf16 split,
+ * 9 tensor-core leaf GEMM (split BF16).
+ * `nkinds` is the length of both output arrays (entries beyond 10 are set to 0). */
+#define SW_PROFILE_KINDS 10
 sw_status sw_profile(sw_handle h, int enable);
 sw_status sw_profile_read(sw_handle h, int nkinds, int *launches, double *ms);
 

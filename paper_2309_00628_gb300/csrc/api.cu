@@ -63,6 +63,21 @@ bool make_map_f32(CUtensorMap* m, const void* base, int rows, int cols, long lon
     return r == CUDA_SUCCESS;
 }
 
+// BF16 row-major view rows x cols (ld elements, a multiple of 8) -> 2-D tensor map with a box of
+// 64 columns (128 bytes) x box_rows, 128-byte swizzle, zero fill out of bounds.
+bool make_map_bf16(CUtensorMap* m, const void* base, int rows, int cols, long long ld, int box_rows) {
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)std::max(cols, 1), (cuuint64_t)std::max(rows, 1)};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
 inline long long round_up(long long x, long long a) { return (x + a - 1) / a * a; }
 
 // Tile-width override for tuning sweeps (SWMM_TF32_BN = 128 or 256); 0 = the planner's choice.
@@ -78,7 +93,10 @@ int bn_override() {
 inline long long ceil_div(long long x, long long a) { return (x + a - 1) / a; }
 
 // ------------------------------------------------------------------ plan
-enum OpKind { OP_GEMM_TF32, OP_GEMM_SIMT, OP_ADDSUB, OP_COPY_PAD, OP_PREADD, OP_MEMSET, OP_TRANSPOSE, OP_TRANSPOSE_SQ };
+enum OpKind {
+    OP_GEMM_TF32, OP_GEMM_SIMT, OP_ADDSUB, OP_COPY_PAD, OP_PREADD, OP_MEMSET, OP_TRANSPOSE, OP_TRANSPOSE_SQ,
+    OP_SPLIT, OP_GEMM_BF16X3
+};
 
 struct Op {
     OpKind kind;
@@ -121,8 +139,9 @@ struct View {
 // matrix, and a k x n block is stored n x k.  Elementwise steps are orientation-free as long
 // as all their operands share it, which the schedules below guarantee.
 struct Planner {
-    int eb;                 // 4 = FP32 (TF32 leaves), 8 = FP64
-    bool bt;                // B side stored transposed (FP32 path)
+    int eb;                 // 4 = FP32 (TF32 or split-BF16 leaves), 8 = FP64
+    bool bf;                // FP32 with split-BF16 leaves
+    bool bt;                // B side stored transposed (TF32 leaves only)
     uint32_t variant;
     bool dry;               // size only: no pointers, no maps
     char* ws_base;
@@ -165,6 +184,39 @@ struct Planner {
     }
     // a logical k x n B-side temporary
     View tallocB(int k, int n) { return bt ? talloc(n, k) : talloc(k, n); }
+
+    // a bf16 rows x cols buffer, leading dimension a multiple of 8 (16-byte TMA rows)
+    View talloc_bf16(int rows, int cols) {
+        const long long ld = round_up(std::max(cols, 1), 8);
+        const size_t bytes = (size_t)round_up((long long)std::max(rows, 1) * ld * 2, 256);
+        View v;
+        v.p = dry ? nullptr : ws_base + ws_top;
+        v.ld = ld;
+        v.rows = rows;
+        v.cols = cols;
+        ws_top += bytes;
+        ws_peak = std::max(ws_peak, ws_top);
+        return v;
+    }
+
+    // FP32 view -> (hi, lo) bf16 halves in workspace
+    void split(View x, View& hi, View& lo) {
+        hi = talloc_bf16(x.rows, x.cols);
+        lo = talloc_bf16(x.rows, x.cols);
+        split_into(x, hi, lo);
+    }
+    void split_into(View x, const View& hi, const View& lo) {
+        Op o;
+        o.kind = OP_SPLIT;
+        o.rows = x.rows;
+        o.cols = x.cols;
+        o.x = x.p;
+        o.ldx = x.ld;
+        o.z = hi.p;
+        o.y = lo.p;
+        o.ldz = hi.ld;
+        push(o);
+    }
 
     size_t put_blob(const void* src, size_t bytes) {
         size_t off = round_up(plan->blob.size(), 64);
@@ -267,8 +319,13 @@ struct Planner {
     // one per distinct block.
     std::vector<CUtensorMap> tmaps;
     std::vector<View> tmap_views;
+    // A TMA store / reduce writes whole 16-byte pieces at a block's right edge, so a block whose
+    // width is not a multiple of 4 FP32 elements would spill into its right-hand neighbour (or a
+    // caller's padding): such blocks keep the per-thread epilogue.
     int target_map(View c) {
-        if (eb != 4 || !vec_ok(c) || c.rows <= 0 || c.cols <= 0) return -1;
+        static const bool no_tma_epilogue = getenv("SWMM_NO_TMA_EPILOGUE") != nullptr;  // diagnostics
+        if (eb != 4 || no_tma_epilogue || !vec_ok(c) || c.rows <= 0 || c.cols <= 0 || (c.cols % 4) != 0)
+            return -1;
         for (size_t i = 0; i < tmap_views.size(); ++i) {
             const View& v = tmap_views[i];
             if (v.p == c.p && v.ld == c.ld && v.rows == c.rows && v.cols == c.cols) return (int)i;
@@ -294,8 +351,12 @@ struct Planner {
             if (mode == TGT_STORE) memset0(c);
             return true;
         }
+        if (eb == 8) {
+            if (dry) return true;
+            return simt(a, b, c, mode);
+        }
+        if (bf) return gemm_bf16x3(a, b, c, mode);
         if (dry) return true;
-        if (eb == 8) return simt(a, b, c, mode);
         Target t = make_target(c, 1.f, mode, target_map(c));
         Leaf lf;
         memset(&lf, 0, sizeof(lf));
@@ -323,6 +384,44 @@ struct Planner {
         flush_tmaps(o);
         push(o);
         return true;
+    }
+
+    // Split-BF16 leaf: both operands split into (hi, lo) bf16 halves in workspace (released once
+    // the launch is queued: later ops run after it on the same stream), then one launch.
+    bool gemm_bf16x3(View a, View b, View c, int mode) {
+        const size_t mark = ws_top;
+        View ah, al, bh, bl;
+        split(a, ah, al);
+        split(b, bh, bl);
+        bool ok = true;
+        if (!dry) {
+            Target t = make_target(c, 1.f, mode, target_map(c));
+            Leaf lf;
+            memset(&lf, 0, sizeof(lf));
+            lf.a_map = 0;
+            lf.b_map = 1;
+            lf.m = c.rows;
+            lf.n = c.cols;
+            lf.tgt_count = 1;
+            Op o;
+            o.kind = OP_GEMM_BF16X3;
+            o.bn = bn_override() ? bn_override() : 128;
+            lf.kblocks = (int)ceil_div(a.cols, bf16x3_tile_k());
+            lf.tiles_n = (int)ceil_div(c.cols, o.bn);
+            ok = make_map_bf16(&o.maps.m[0], ah.p, ah.rows, ah.cols, ah.ld, tf32_tile_m()) &&
+                 make_map_bf16(&o.maps.m[1], al.p, al.rows, al.cols, al.ld, tf32_tile_m()) &&
+                 make_map_bf16(&o.maps.m[2], bh.p, bh.rows, bh.cols, bh.ld, 64) &&
+                 make_map_bf16(&o.maps.m[3], bl.p, bl.rows, bl.cols, bl.ld, 64);
+            if (!ok) err = "bf16 tensor map encoding failed";
+            o.items = (int)(ceil_div(c.rows, tf32_tile_m()) * lf.tiles_n);
+            o.nleaves = 1;
+            o.leaves_off = put_blob(&lf, sizeof(lf));
+            o.targets_off = put_blob(&t, sizeof(t));
+            flush_tmaps(o);
+            push(o);
+        }
+        ws_top = mark;
+        return ok;
     }
 
     // SIMT product c (=|+=) a b with b in logical orientation (k x n).
@@ -550,8 +649,9 @@ struct Planner {
         const int m = C.rows, n = C.cols, k = A.cols;
         const int s = 1 << L;
         const int mb = (int)ceil_div(m, s);
-        const int kb = eb == 4 ? (int)round_up(ceil_div(k, s), tf32_tile_k()) : (int)ceil_div(k, s);
-        const int nb = eb == 4 ? (int)round_up(ceil_div(n, s), 4) : (int)ceil_div(n, s);
+        const int kb = eb == 8 ? (int)ceil_div(k, s)
+                               : (int)round_up(ceil_div(k, s), bf ? bf16x3_tile_k() : tf32_tile_k());
+        const int nb = eb == 8 ? (int)ceil_div(n, s) : (int)round_up(ceil_div(n, s), bf ? 8 : 4);
         int nleaf = 1;
         for (int i = 0; i < L; ++i) nleaf *= 7;
         std::vector<short> slot_a(nleaf, -1), slot_b(nleaf, -1);
@@ -586,6 +686,14 @@ struct Planner {
         SB.rows = bt ? nbs * nb : nbs * kb;
         SB.ld = bt ? kb : nb;
         (void)mark;
+        // split-BF16 leaves: (hi, lo) halves of A, B and the S / T sums (sized in the dry run too)
+        View halves[4][2];
+        if (bf) {
+            const int hr[4] = {m, k, std::max(SA.rows, 1), std::max(SB.rows, 1)};
+            const int hc[4] = {k, n, kb, nb};
+            for (int i = 0; i < 4; ++i)
+                for (int j = 0; j < 2; ++j) halves[i][j] = talloc_bf16(hr[i], hc[i]);
+        }
         if (dry) return true;
         if (na > 0) {
             Op o;
@@ -618,7 +726,8 @@ struct Planner {
         // C and reduce-adds only.
         const bool ordered = eb == 4 && L == 1;
         if (!ordered) memset0(C);
-        const int bn_o = eb == 4 ? (bn_override() ? bn_override() : (nb <= 128 ? 128 : 256)) : F64_BN;
+        const int bn_o = eb == 8 ? F64_BN
+                                 : (bn_override() ? bn_override() : (bf || nb <= 128 ? 128 : 256));
         std::vector<int> first_writer(1 << (2 * L), -1), flag_base(1 << (2 * L), -1), flag_cols(1 << (2 * L), 0);
         int nflags = 0;
         // leaves and their Kronecker-product targets
@@ -635,7 +744,7 @@ struct Planner {
             else { lf.b_map = 3; lf.b_row = slot_b[w] * (bt ? nb : kb); lf.b_col = 0; }
             lf.m = mb;
             lf.n = nb;
-            lf.kblocks = eb == 4 ? kb / tf32_tile_k() : kb;
+            lf.kblocks = eb == 8 ? kb : kb / (bf ? bf16x3_tile_k() : tf32_tile_k());
             lf.tiles_n = (int)ceil_div(nb, bn);
             lf.tgt_begin = (int)tg.size();
             int digits[3] = {0, 0, 0};
@@ -710,7 +819,27 @@ struct Planner {
             o.nflags = nflags;
             o.flags_off = put_blob(zeros.data(), zeros.size() * sizeof(unsigned));
         }
-        if (eb == 4) {
+        if (bf) {
+            // split every operand source once: A, B, and the S / T sums
+            o.kind = OP_GEMM_BF16X3;
+            o.bn = bn;
+            View srcs[4] = {A, B, SA, SB};
+            srcs[0].rows = m; srcs[0].cols = k;
+            srcs[1].rows = k; srcs[1].cols = n;
+            srcs[2].cols = kb;
+            srcs[3].cols = nb;
+            const int box[4] = {tf32_tile_m(), 64, tf32_tile_m(), 64};
+            for (int i = 0; i < 4; ++i) {
+                const View& hi = halves[i][0];
+                const View& lo = halves[i][1];
+                if (srcs[i].rows > 0) split_into(srcs[i], hi, lo);
+                if (!make_map_bf16(&o.maps.m[2 * i], hi.p, hi.rows, hi.cols, hi.ld, box[i]) ||
+                    !make_map_bf16(&o.maps.m[2 * i + 1], lo.p, lo.rows, lo.cols, lo.ld, box[i])) {
+                    err = "bf16 tensor map encoding failed";
+                    return false;
+                }
+            }
+        } else if (eb == 4) {
             o.kind = OP_GEMM_TF32;
             o.bn = bn;
             if (!make_map_f32(&o.maps.m[0], A.p, m, k, A.ld, 32, tf32_tile_m()) ||
@@ -820,16 +949,17 @@ static sw_status build_plan(sw_handle h, int eb, const void* A, int lda, const v
     const uint32_t algo = variant & SW_ALGO_MASK, sched = variant & SW_SCHED_MASK, odd = variant & SW_ODD_MASK;
     if (algo > SW_ALGO_WINOGRAD) return fail(h, SW_EINVAL, "unknown algorithm bits");
     if (sched > SW_SCHED_ALLOC) return fail(h, SW_EINVAL, "unknown schedule bits");
-    if ((variant & SW_LEAF_MASK) != SW_LEAF_TF32 && eb == 4)
-        return fail(h, SW_EUNSUPPORTED, "leaf kind not built yet");
+    if ((variant & SW_LEAF_MASK) > SW_LEAF_BF16X3) return fail(h, SW_EINVAL, "unknown leaf bits");
     if (algo == SW_ALGO_STRASSEN && (sched == SW_SCHED_TWO_TEMP || sched == SW_SCHED_IN_PLACE))
         return fail(h, SW_EUNSUPPORTED, "Tables 2 and 3 are Winograd schedules");
     if (sched == SW_SCHED_IN_PLACE && algo != SW_ALGO_NAIVE && !(m == n && n == k))
         return fail(h, SW_EUNSUPPORTED, "in-place schedule needs m == n == k");
 
+    const bool bf = eb == 4 && (variant & SW_LEAF_MASK) == SW_LEAF_BF16X3;
     Planner P;
     P.eb = eb;
-    P.bt = eb == 4;
+    P.bf = bf;
+    P.bt = eb == 4 && !bf;
     P.variant = variant;
     P.dry = dry;
     P.ws_base = h->ws;
@@ -840,7 +970,9 @@ static sw_status build_plan(sw_handle h, int eb, const void* A, int lda, const v
     plan->depth = L;
 
     View Av = {(char*)A, lda, m, k}, Bv = {(char*)B, ldb, k, n}, Cv = {(char*)C, ldc, m, n};
-    const bool a_ok = eb == 8 || Planner::vec_ok(Av), c_ok = eb == 8 || Planner::vec_ok(Cv);
+    // TF32 leaves read A and write C through TMA (16-byte rows); the SIMT FP64 leaf and the split
+    // pass of the BF16X3 leaves read any layout, and unaligned C blocks take the per-thread epilogue
+    const bool a_ok = eb == 8 || bf || Planner::vec_ok(Av), c_ok = eb == 8 || bf || Planner::vec_ok(Cv);
     // B in the storage the leaves want: B^T in workspace (FP32), B itself (FP64)
     auto stage_b = [&](View b, int rows_pad, int cols_pad) -> View {  // logical k x n -> storage
         if (!P.bt) {
@@ -870,17 +1002,17 @@ static sw_status build_plan(sw_handle h, int eb, const void* A, int lda, const v
         return fail(h, SW_EUNSUPPORTED, "materialised schedules stop at depth 5 (7^5 leaf launches); raise the cutoff");
     } else {
         // materialised schedules: halve exactly; FP32 column splits must stay 16-byte aligned
-        const long long gm = 1LL << L, gk = eb == 4 ? 4LL << L : 1LL << L, gn = gk;
+        const long long gm = 1LL << L, gk = (eb == 4 && !bf) ? 4LL << L : 1LL << L, gn = gk;
         const bool exact = m % gm == 0 && k % gk == 0 && n % gn == 0;
         const bool inpl = sched == SW_SCHED_IN_PLACE;
-        if (exact && a_ok && c_ok && (eb == 8 || Planner::vec_ok(Bv))) {
+        if (exact && a_ok && c_ok && (eb == 8 || bf || Planner::vec_ok(Bv))) {
             View bs = Bv;
             if (P.bt) {
                 if (inpl) { P.transpose_square(Bv); bs.rows = n; bs.cols = k; }  // B <- B^T in place
                 else bs = stage_b(Bv, k, n);
             }
             ok = P.product(Av, bs, Cv, L);
-        } else if (odd == SW_PEEL && a_ok && c_ok && (eb == 8 || Planner::vec_ok(Bv))) {
+        } else if (odd == SW_PEEL && a_ok && c_ok && (eb == 8 || bf || Planner::vec_ok(Bv))) {
             long long me = m / gm * gm, ke = k / gk * gk, ne = n / gn * gn;
             if (inpl) me = ke = ne = std::min(me, std::min(ke, ne));
             auto sub = [&](View v, long long r0, long long c0, long long rows, long long cols) {
@@ -954,6 +1086,17 @@ static sw_status run_plan(sw_handle h, Plan* plan, cudaStream_t s) {
                 break;
             case OP_TRANSPOSE_SQ:
                 e = launch_transpose_inplace(o.rows, static_cast<float*>(o.z), o.ldz, s);
+                break;
+            case OP_SPLIT:
+                e = launch_split_bf16(o.rows, o.cols, static_cast<const float*>(o.x), o.ldx, o.z,
+                                      const_cast<void*>(o.y), o.ldz, s);
+                break;
+            case OP_GEMM_BF16X3:
+                e = launch_gemm_bf16x3(o.bn, o.maps, nullptr, reinterpret_cast<const Leaf*>(blob + o.leaves_off),
+                                       o.nleaves, reinterpret_cast<const Target*>(blob + o.targets_off),
+                                       o.ntmaps ? reinterpret_cast<const CUtensorMap*>(blob + o.tmaps_off) : nullptr,
+                                       o.nflags ? reinterpret_cast<unsigned*>(blob + o.flags_off) : nullptr,
+                                       o.nflags ? ++o.epoch : 0u, o.items, h->d_err, h->sms, s);
                 break;
             case OP_ADDSUB:
                 e = launch_addsub(o.eb, o.rows, o.cols, o.z, o.ldz, o.x, o.ldx, o.y, o.ldy, o.sy, s);

@@ -1,18 +1,22 @@
-// gemm_tf32.cu -- grouped leaf GEMM on the sm_103a tensor cores (tcgen05 + TMEM + TMA).
+// gemm_tc.cu -- grouped leaf GEMM on the sm_103a tensor cores (tcgen05 + TMEM + TMA).
 //
 // Computes the leaf sub-products P = Aop * Bop of the recursion (Sec. 2.2 / 2.3; with a single
 // leaf and a single STORE target it is the plain product of Alg. 1) and adds sign * P into
 // each of the leaf's target blocks of C -- the post-additions folded into the epilogue.
 //
-// FP32 operands are staged by TMA into 128-byte-swizzled shared memory and consumed by
-// tcgen05.mma.kind::tf32 (the tensor core reads each FP32 operand as TF32: its 10 leading
-// mantissa bits); products accumulate in FP32 in tensor memory.  Both operands are K-major:
-// A as stored (m x k, row-major) and B as its transpose B^T (n x k, row-major) -- kind::tf32
-// does not take an N-major B, so the planner hands this kernel B^T views.
+// Two operand modes:
+//  * TF32: FP32 operands staged by TMA into 128-byte-swizzled shared memory and consumed by
+//    tcgen05.mma.kind::tf32 (the tensor core reads each FP32 operand as TF32: its 10 leading
+//    mantissa bits).  Both operands K-major: A as stored (m x k) and B as B^T (n x k) --
+//    kind::tf32 does not take an N-major B, so the planner hands this mode B^T views.
+//  * BF16X3: each FP32 operand arrives split into bf16 halves hi = bf16(x), lo = bf16(x - hi);
+//    per k-step the kernel issues kind::f16 MMAs hi*hi + hi*lo + lo*hi into one FP32
+//    accumulator.  A K-major, B N-major (as stored, k x n).
+// Products accumulate in FP32 in tensor memory.
 //
 // CTA = 6 warps, persistent over work items (one item = one BM x BN output tile of one leaf):
-//   warp 0      TMA producer: A tile (BM x BK) + B^T tile (BN x BK) per stage, both K-major
-//   warp 1      TMEM allocator + MMA issuer (one thread), BK/8 MMAs of K = 8 per stage
+//   warp 0      TMA producer: the A tile(s) and B tile(s) of one k-block per stage
+//   warp 1      TMEM allocator + MMA issuer (one thread)
 //   warps 2..5  epilogue: tcgen05.ld 32 columns at a time; each warp stages its 32 x 32 chunk
 //               (with the target's sign) in 128-byte-swizzled shared memory and one lane issues a
 //               TMA store (first writer) or TMA reduce-add (further contributions) per target;
@@ -29,23 +33,30 @@
 namespace swk {
 
 constexpr int TF_BM = 128;
-constexpr int TF_BK = 32;  // 32 FP32 = 128 bytes: one swizzle row
+constexpr int TF_BK = 32;  // TF32 k-block: 32 FP32 = 128 bytes, one swizzle row
 constexpr int TF_GROUP_M = 8;
+constexpr int MODE_TF32 = 0, MODE_BF16X3 = 1;
 
-template <int BN>
+template <int MODE, int BN>
 struct TfCfg {
-    static constexpr int STAGES = (BN == 256) ? 4 : 6;
-    static constexpr int A_BYTES = TF_BM * TF_BK * 4;   // 16 KB
-    static constexpr int B_BYTES = BN * TF_BK * 4;      // 32 KB (BN 256) / 16 KB (BN 128)
-    static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+    static constexpr int BK = MODE == MODE_TF32 ? 32 : 64;           // elements per 128-byte row
+    static constexpr int A_BYTES = TF_BM * 128;                      // one A tile (16 KB)
+    static constexpr int B_BYTES = BN * 128;                         // one B tile
+    static constexpr int NOPS = MODE == MODE_TF32 ? 1 : 2;           // tiles per operand (hi, lo)
+    static constexpr int STAGE_BYTES = NOPS * (A_BYTES + B_BYTES);
+    static constexpr int STAGES = (4 * 49152) / STAGE_BYTES;         // 192 KB of operand stages
     static constexpr int TMEM_COLS = 2 * BN;
     static constexpr int STG_OFF = STAGES * STAGE_BYTES;      // epilogue staging: 4 warps x 2 x 4 KB
     static constexpr int STG_BYTES = 4 * 2 * 4096;
     static constexpr int BAR_OFF = STG_OFF + STG_BYTES;
     static constexpr int SMEM_BYTES = BAR_OFF + 256 + 1024;  // + barriers + alignment slack
-    // instruction descriptor: D F32, A/B TF32, both K-major, N = BN, M = 128
-    static constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | (0u << 15) | (0u << 16) |
-                                      ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(TF_BM >> 4) << 24);
+    // instruction descriptor: D F32; TF32: A/B TF32, both K-major; BF16X3: A/B BF16, A K-major,
+    // B MN-major; N = BN, M = 128
+    static constexpr uint32_t IDESC =
+        MODE == MODE_TF32
+            ? ((1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(TF_BM >> 4) << 24))
+            : ((1u << 4) | (1u << 7) | (1u << 10) | (1u << 16) | ((uint32_t)(BN >> 3) << 17) |
+               ((uint32_t)(TF_BM >> 4) << 24));
 };
 
 struct ItemPos {
@@ -114,19 +125,22 @@ __device__ __forceinline__ void store_row32(const Target& t, int row, int col0, 
     }
 }
 
-template <int BN>
+template <int MODE, int BN>
 __global__ void __launch_bounds__(192, 1)
-    gemm_tf32_kernel(const __grid_constant__ MapSet maps, const CUtensorMap* __restrict__ gmaps,
+    gemm_tc_kernel(const __grid_constant__ MapSet maps, const CUtensorMap* __restrict__ gmaps,
                      const Leaf* __restrict__ leaves, int nleaves, const Target* __restrict__ targets,
                      const CUtensorMap* __restrict__ tmaps, unsigned* __restrict__ flags, unsigned epoch,
                      int total_items, int* err) {
-    using Cfg = TfCfg<BN>;
+    using Cfg = TfCfg<MODE, BN>;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw_addr = smem_u32(smem_raw);
     const uint32_t base_addr = (raw_addr + 1023u) & ~1023u;
     uint8_t* base = smem_raw + (base_addr - raw_addr);
-    uint8_t* sA = base;                                  // STAGES x A_BYTES
-    uint8_t* sB = base + Cfg::STAGES * Cfg::A_BYTES;     // STAGES x B_BYTES
+    // stage s: [A (hi) | A lo | B (hi) | B lo], 1024-byte aligned pieces
+    auto stage_a = [&](int st, int op) { return base + st * Cfg::STAGE_BYTES + op * Cfg::A_BYTES; };
+    auto stage_b = [&](int st, int op) {
+        return base + st * Cfg::STAGE_BYTES + Cfg::NOPS * Cfg::A_BYTES + op * Cfg::B_BYTES;
+    };
     uint64_t* bars = reinterpret_cast<uint64_t*>(base + Cfg::BAR_OFF);
     uint64_t* full = bars;                       // [STAGES]
     uint64_t* empty = bars + Cfg::STAGES;        // [STAGES]
@@ -169,14 +183,15 @@ __global__ void __launch_bounds__(192, 1)
             for (int item = blockIdx.x; item < total_items && ok; item += gridDim.x) {
                 const ItemPos ip = decode_item(leaves, nleaves, item, BN);
                 const Leaf* L = &leaves[ip.leaf];
-                const CUtensorMap* ma = pick_map(maps, gmaps, __ldg(&L->a_map));
-                const CUtensorMap* mb = pick_map(maps, gmaps, __ldg(&L->b_map));
+                const int am = __ldg(&L->a_map), bm = __ldg(&L->b_map);
                 const int a_row = __ldg(&L->a_row) + ip.tm * TF_BM;
                 const int a_col = __ldg(&L->a_col);
-                const int b_row = __ldg(&L->b_row) + ip.tn * BN;  // B^T: rows are N
-                const int b_col = __ldg(&L->b_col);                // B^T: columns are K
+                // TF32: B^T, rows are N, columns K.  BF16X3: B as stored, rows K, columns N.
+                const int b_row = __ldg(&L->b_row) + (MODE == MODE_TF32 ? ip.tn * BN : 0);
+                const int b_col = __ldg(&L->b_col) + (MODE == MODE_TF32 ? 0 : ip.tn * BN);
                 const int kb_n = __ldg(&L->kblocks);
-                if (((a_col | b_col) & 3) != 0) {  // TMA x coordinate must be 16-byte aligned
+                // TMA x coordinates must be 16-byte aligned (4 FP32 / 8 BF16 elements)
+                if (((a_col | b_col) & (MODE == MODE_TF32 ? 3 : 7)) != 0) {
                     set_error(err, ERR_ALIGN);
                     ok = false;
                     break;
@@ -184,10 +199,20 @@ __global__ void __launch_bounds__(192, 1)
                 for (int kb = 0; kb < kb_n; ++kb) {
                     if (!mbar_wait(&empty[stage], phase ^ 1u, err, ERR_WAIT_EMPTY)) { ok = false; break; }
                     mbar_arrive_expect_tx(&full[stage], Cfg::STAGE_BYTES);
-                    uint8_t* dA = sA + stage * Cfg::A_BYTES;
-                    uint8_t* dB = sB + stage * Cfg::B_BYTES;
-                    tma_load_2d(dA, ma, &full[stage], a_col + kb * TF_BK, a_row);
-                    tma_load_2d(dB, mb, &full[stage], b_col + kb * TF_BK, b_row);
+#pragma unroll
+                    for (int op = 0; op < Cfg::NOPS; ++op) {
+                        const CUtensorMap* ma = pick_map(maps, gmaps, am * Cfg::NOPS + op);
+                        const CUtensorMap* mb = pick_map(maps, gmaps, bm * Cfg::NOPS + op);
+                        tma_load_2d(stage_a(stage, op), ma, &full[stage], a_col + kb * Cfg::BK, a_row);
+                        if (MODE == MODE_TF32) {
+                            tma_load_2d(stage_b(stage, op), mb, &full[stage], b_col + kb * Cfg::BK, b_row);
+                        } else {
+#pragma unroll
+                            for (int c = 0; c < BN / 64; ++c)  // 64 N-columns (128 B) x 64 K-rows per box
+                                tma_load_2d(stage_b(stage, op) + c * 8192, mb, &full[stage], b_col + c * 64,
+                                            b_row + kb * Cfg::BK);
+                        }
+                    }
                     ++issued;
                     if (++stage == Cfg::STAGES) { stage = 0; phase ^= 1u; }
                 }
@@ -218,13 +243,30 @@ __global__ void __launch_bounds__(192, 1)
                 for (int kb = 0; kb < kb_n; ++kb) {
                     if (!mbar_wait(&full[stage], phase, err, ERR_WAIT_FULL)) { ok = false; break; }
                     tc_fence_after();
-                    const uint32_t a_addr = smem_u32(sA + stage * Cfg::A_BYTES);
-                    const uint32_t b_addr = smem_u32(sB + stage * Cfg::B_BYTES);
+                    if (MODE == MODE_TF32) {
+                        const uint32_t a_addr = smem_u32(stage_a(stage, 0));
+                        const uint32_t b_addr = smem_u32(stage_b(stage, 0));
 #pragma unroll
-                    for (int kk = 0; kk < TF_BK / 8; ++kk) {
-                        const uint64_t ad = make_sdesc(a_addr + kk * 32, 16, 1024, SWZ_128B);
-                        const uint64_t bd = make_sdesc(b_addr + kk * 32, 16, 1024, SWZ_128B);
-                        mma_tf32(d_tmem, ad, bd, Cfg::IDESC, (kb | kk) != 0 ? 1u : 0u);
+                        for (int kk = 0; kk < TF_BK / 8; ++kk) {  // K = 8 per MMA, 32 bytes
+                            const uint64_t ad = make_sdesc(a_addr + kk * 32, 16, 1024, SWZ_128B);
+                            const uint64_t bd = make_sdesc(b_addr + kk * 32, 16, 1024, SWZ_128B);
+                            mma_tf32(d_tmem, ad, bd, Cfg::IDESC, (kb | kk) != 0 ? 1u : 0u);
+                        }
+                    } else {
+                        const uint32_t ah = smem_u32(stage_a(stage, 0)), al = smem_u32(stage_a(stage, 1));
+                        const uint32_t bh = smem_u32(stage_b(stage, 0)), bl = smem_u32(stage_b(stage, 1));
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk) {  // K = 16 per MMA: 32 bytes of A, 16 rows of B
+                            // A K-major: +32 B per step.  B N-major: 16 rows x 128 B per step,
+                            // 64-column chunks 8 KB apart (LBO), 8-row groups 1 KB apart (SBO).
+                            const uint64_t dah = make_sdesc(ah + kk * 32, 16, 1024, SWZ_128B);
+                            const uint64_t dal = make_sdesc(al + kk * 32, 16, 1024, SWZ_128B);
+                            const uint64_t dbh = make_sdesc(bh + kk * 2048, 8192, 1024, SWZ_128B);
+                            const uint64_t dbl = make_sdesc(bl + kk * 2048, 8192, 1024, SWZ_128B);
+                            mma_f16(d_tmem, dal, dbh, Cfg::IDESC, (kb | kk) != 0 ? 1u : 0u);  // lo * hi
+                            mma_f16(d_tmem, dah, dbl, Cfg::IDESC, 1u);                           // hi * lo
+                            mma_f16(d_tmem, dah, dbh, Cfg::IDESC, 1u);                           // hi * hi
+                        }
                     }
                     mma_commit(&empty[stage]);  // stage is free once these MMAs have read it
                     if (++stage == Cfg::STAGES) { stage = 0; phase ^= 1u; }
@@ -367,22 +409,23 @@ __global__ void __launch_bounds__(192, 1)
     }
 }
 
-template <int BN>
-static cudaError_t launch_tf32_impl(const MapSet& maps, const CUtensorMap* gmaps, const Leaf* leaves, int nleaves,
-                                    const Target* targets, const CUtensorMap* tmaps, unsigned* flags,
-                                    unsigned epoch, int total_items, int* err, int grid, cudaStream_t stream) {
-    using Cfg = TfCfg<BN>;
+template <int MODE, int BN>
+static cudaError_t launch_tc_impl(const MapSet& maps, const CUtensorMap* gmaps, const Leaf* leaves, int nleaves,
+                                  const Target* targets, const CUtensorMap* tmaps, unsigned* flags, unsigned epoch,
+                                  int total_items, int* err, int grid, cudaStream_t stream) {
+    using Cfg = TfCfg<MODE, BN>;
+    static_assert(Cfg::SMEM_BYTES <= 232448, "shared memory budget");
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(gemm_tf32_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<MODE, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              Cfg::SMEM_BYTES);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     if (total_items <= 0) return cudaSuccess;
     if (grid > total_items) grid = total_items;
-    gemm_tf32_kernel<BN><<<grid, 192, Cfg::SMEM_BYTES, stream>>>(maps, gmaps, leaves, nleaves, targets, tmaps,
-                                                                  flags, epoch, total_items, err);
+    gemm_tc_kernel<MODE, BN><<<grid, 192, Cfg::SMEM_BYTES, stream>>>(maps, gmaps, leaves, nleaves, targets, tmaps,
+                                                                      flags, epoch, total_items, err);
     return cudaGetLastError();
 }
 
@@ -390,13 +433,24 @@ cudaError_t launch_gemm_tf32(int bn, const MapSet& maps, const CUtensorMap* gmap
                              const Target* targets, const CUtensorMap* tmaps, unsigned* flags, unsigned epoch,
                              int total_items, int* err, int grid, cudaStream_t stream) {
     if (bn == 256)
-        return launch_tf32_impl<256>(maps, gmaps, leaves, nleaves, targets, tmaps, flags, epoch, total_items, err, grid,
-                                     stream);
-    return launch_tf32_impl<128>(maps, gmaps, leaves, nleaves, targets, tmaps, flags, epoch, total_items, err, grid,
-                                 stream);
+        return launch_tc_impl<MODE_TF32, 256>(maps, gmaps, leaves, nleaves, targets, tmaps, flags, epoch, total_items,
+                                              err, grid, stream);
+    return launch_tc_impl<MODE_TF32, 128>(maps, gmaps, leaves, nleaves, targets, tmaps, flags, epoch, total_items, err,
+                                          grid, stream);
+}
+
+cudaError_t launch_gemm_bf16x3(int bn, const MapSet& maps, const CUtensorMap* gmaps, const Leaf* leaves, int nleaves,
+                               const Target* targets, const CUtensorMap* tmaps, unsigned* flags, unsigned epoch,
+                               int total_items, int* err, int grid, cudaStream_t stream) {
+    if (bn == 256)
+        return launch_tc_impl<MODE_BF16X3, 256>(maps, gmaps, leaves, nleaves, targets, tmaps, flags, epoch,
+                                                total_items, err, grid, stream);
+    return launch_tc_impl<MODE_BF16X3, 128>(maps, gmaps, leaves, nleaves, targets, tmaps, flags, epoch, total_items,
+                                            err, grid, stream);
 }
 
 int tf32_tile_m() { return TF_BM; }
 int tf32_tile_k() { return TF_BK; }
+int bf16x3_tile_k() { return 64; }
 
 }  // namespace swk

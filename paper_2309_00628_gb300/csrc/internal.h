@@ -8,10 +8,10 @@
 
 namespace swk {
 
-// Up to four tensor maps passed by value (__grid_constant__): A, B and the two operand-sum
-// scratch matrices of one product.
+// Tensor maps passed by value (__grid_constant__): A, B and the two operand-sum scratch
+// matrices of one product -- one map each for TF32, a (hi, lo) pair each for BF16X3.
 struct MapSet {
-    CUtensorMap m[4];
+    CUtensorMap m[8];
 };
 
 // A strided matrix view with its valid extent (reads beyond it return 0).
@@ -30,6 +30,17 @@ cudaError_t launch_gemm_tf32(int bn, const MapSet& maps, const CUtensorMap* gmap
                              int total_items, int* err, int grid, cudaStream_t stream);
 int tf32_tile_m();
 int tf32_tile_k();
+int bf16x3_tile_k();
+
+// Split-BF16 leaves: operand map index i refers to maps 2i (hi) and 2i+1 (lo); B is N-major
+// (k x n as stored); Leaf::kblocks counts 64-deep k blocks.
+cudaError_t launch_gemm_bf16x3(int bn, const MapSet& maps, const CUtensorMap* gmaps, const Leaf* leaves, int nleaves,
+                               const Target* targets, const CUtensorMap* tmaps, unsigned* flags, unsigned epoch,
+                               int total_items, int* err, int grid, cudaStream_t stream);
+
+// hi = bf16(x), lo = bf16(x - hi), elementwise on a rows x cols FP32 view; outputs share ldo.
+cudaError_t launch_split_bf16(int rows, int cols, const float* x, long long ldx, void* hi, void* lo, long long ldo,
+                              cudaStream_t stream);
 
 // SIMT leaf GEMM (FP64, or FP32 when elem_bytes == 4): same leaf / target descriptors,
 // a_map / b_map index `refs`, B stored as is (k x n); Leaf::kblocks is the inner dimension.

@@ -12,6 +12,7 @@
 //  * transposes  B -> B^T (with zero fill) and in-place square transposes: the TF32 tensor-core
 //                path consumes B as B^T.
 //  * norms       FP64 max-reductions for max|C - R|, max|A|, max|B|.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <cstdint>
 
@@ -377,6 +378,60 @@ cudaError_t launch_gemm_simt(int elem_bytes, const MatRef* refs, const Leaf* lea
     if (grid > total_items) grid = total_items;
     if (elem_bytes == 8) gemm_simt_kernel<double><<<grid, 256, 0, stream>>>(refs, leaves, nleaves, targets, total_items);
     else gemm_simt_kernel<float><<<grid, 256, 0, stream>>>(refs, leaves, nleaves, targets, total_items);
+    return cudaGetLastError();
+}
+
+// ============================================================== split into bf16 halves
+// hi = RN_bf16(x), lo = RN_bf16(x - hi): x - hi is exact in FP32, so hi + lo carries x to about
+// 16 significant bits; the split-BF16 leaves multiply hi*hi + hi*lo + lo*hi.
+__global__ void split_bf16_kernel(int rows, int cols, const float* __restrict__ x, long long ldx,
+                                  __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo, long long ldo) {
+    const long long total = (long long)rows * cols;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / cols), j = (int)(e - (long long)i * cols);
+        const float v = x[i * ldx + j];
+        const __nv_bfloat16 h = __float2bfloat16_rn(v);
+        hi[i * ldo + j] = h;
+        lo[i * ldo + j] = __float2bfloat16_rn(v - __bfloat162float(h));
+    }
+}
+
+// Four elements per thread: one 16-byte load, two 8-byte stores (cols, ldx, ldo multiples of 4,
+// 16-byte aligned input, 8-byte aligned outputs).
+__global__ void split_bf16x4_kernel(int rows, int cols4, const float4* __restrict__ x, long long ldx4,
+                                    uint2* __restrict__ hi, uint2* __restrict__ lo, long long ldo4) {
+    const long long total = (long long)rows * cols4;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / cols4), j = (int)(e - (long long)i * cols4);
+        const float4 v = x[i * ldx4 + j];
+        const __nv_bfloat162 h01 = __floats2bfloat162_rn(v.x, v.y), h23 = __floats2bfloat162_rn(v.z, v.w);
+        const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
+        const __nv_bfloat162 l01 = __floats2bfloat162_rn(v.x - f01.x, v.y - f01.y);
+        const __nv_bfloat162 l23 = __floats2bfloat162_rn(v.z - f23.x, v.w - f23.y);
+        uint2 hh, ll;
+        hh.x = *reinterpret_cast<const unsigned*>(&h01);
+        hh.y = *reinterpret_cast<const unsigned*>(&h23);
+        ll.x = *reinterpret_cast<const unsigned*>(&l01);
+        ll.y = *reinterpret_cast<const unsigned*>(&l23);
+        hi[i * ldo4 + j] = hh;
+        lo[i * ldo4 + j] = ll;
+    }
+}
+
+cudaError_t launch_split_bf16(int rows, int cols, const float* x, long long ldx, void* hi, void* lo, long long ldo,
+                              cudaStream_t s) {
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    if (((cols | ldx | ldo) & 3) == 0 && (reinterpret_cast<uintptr_t>(x) & 15) == 0 &&
+        ((reinterpret_cast<uintptr_t>(hi) | reinterpret_cast<uintptr_t>(lo)) & 7) == 0) {
+        split_bf16x4_kernel<<<grid_for((long long)rows * cols / 4, 256), 256, 0, s>>>(
+            rows, cols / 4, reinterpret_cast<const float4*>(x), ldx / 4, static_cast<uint2*>(hi), static_cast<uint2*>(lo),
+            ldo / 4);
+        return cudaGetLastError();
+    }
+    split_bf16_kernel<<<grid_for((long long)rows * cols, 256), 256, 0, s>>>(
+        rows, cols, x, ldx, static_cast<__nv_bfloat16*>(hi), static_cast<__nv_bfloat16*>(lo), ldo);
     return cudaGetLastError();
 }
 

@@ -118,7 +118,8 @@ def sw_error_norms(h, elem_bytes, m, n, k, A, lda, B, ldb, C, ldc, R, ldr, strea
     return st, [out[0], out[1], out[2]]
 
 
-PROFILE_KINDS = ["gemm_tf32", "gemm_simt", "addsub", "copy_pad", "preadd", "memset", "transpose", "transpose_sq"]
+PROFILE_KINDS = ["gemm_tf32", "gemm_simt", "addsub", "copy_pad", "preadd", "memset", "transpose", "transpose_sq",
+                 "split_bf16", "gemm_bf16x3"]
 
 
 def sw_profile(h, enable: bool) -> int:

@@ -266,3 +266,81 @@ def test_full_size_sampled_rows(h, L):
     R = oracle.naive_mt(A[rows].astype(np.float64), B.astype(np.float64))
     Cr = C[torch.from_numpy(rows).cuda()].cpu().numpy().astype(np.float64)
     check_close(Cr, R, A, B, tol_tf32(n, L))
+
+
+# ------------------------------------------------------------------ split-BF16 leaves (hi*hi + hi*lo + lo*hi)
+# hi = bf16(x), lo = bf16(x - hi) carry x to a relative 2^-16, and the dropped lo*lo term is below
+# 2^-16 |a b|: each product term errs by < 3 * 2^-16 |a||b|, so the same Hoeffding argument as
+# for TF32 gives 8 * 3 * 2^-16 * 3^L / sqrt(k) (normalised), 40x tighter than TF32.
+BF = swmm.SW_LEAF_BF16X3
+
+
+def tol_bf16x3(k, L):
+    return 8.0 * 3.0 * 2.0 ** -16 * 3.0 ** L / np.sqrt(k) + 2.0 ** -20
+
+
+@pytest.mark.parametrize("m,n,k", [(128, 128, 64), (300, 500, 200), (1000, 1000, 1000), (129, 257, 33)])
+def test_bf16x3_plain_integers_bit_exact(h, m, n, k):
+    A, B = inputs.pair(m, n, k, "int", seed=70, dtype=np.float64)
+    assert np.array_equal(run(h, A, B, 0, swmm.SW_ALGO_NAIVE | BF), oracle.naive(A, B))
+
+
+def test_bf16x3_plain_float_far_tighter_than_tf32(h):
+    m, n, k = 777, 640, 1500
+    A, B = inputs.pair(m, n, k, "uniform", seed=71, dtype=np.float32)
+    R = oracle.naive(A.astype(np.float64), B.astype(np.float64))
+    e_bf = check_close(run(h, A, B, 0, swmm.SW_ALGO_NAIVE | BF), R, A, B, tol_bf16x3(k, 0))
+    e_tf = check_close(run(h, A, B, 0, swmm.SW_ALGO_NAIVE), R, A, B, tol_tf32(k, 0))
+    assert e_bf < e_tf / 16, (e_bf, e_tf)
+
+
+@pytest.mark.parametrize("algo", [W, S])
+@pytest.mark.parametrize("sched", [FUSED, TWO, INPL, ALLOC])
+def test_bf16x3_recursive(h, algo, sched):
+    if algo == S and sched in (TWO, INPL):
+        pytest.skip("Tables 2 and 3 are Winograd schedules")
+    n, cutoff = 512, 128  # L = 2
+    v = algo | sched | BF
+    L = depth(h, n, n, n, cutoff, v, 4)
+    assert L == 2
+    Ai, Bi = inputs.pair(n, n, n, "int", seed=72, dtype=np.float64, lim=1)
+    assert np.array_equal(run(h, Ai, Bi, cutoff, v), oracle.naive(Ai, Bi))
+    A, B = inputs.pair(n, n, n, "uniform", seed=73, dtype=np.float32)
+    R = oracle.naive(A.astype(np.float64), B.astype(np.float64))
+    check_close(run(h, A, B, cutoff, v), R, A, B, tol_bf16x3(n, L))
+
+
+def test_bf16x3_odd_sizes_fused_and_two_temp(h):
+    for m, n, k in [(300, 260, 200), (97, 131, 203)]:
+        A, B = inputs.pair(m, n, k, "int", seed=74, dtype=np.float64, lim=2)
+        for v in (W | FUSED | BF, W | TWO | BF | swmm.SW_PAD, W | TWO | BF | swmm.SW_PEEL):
+            assert np.array_equal(run(h, A, B, 40, v), oracle.naive(A, B)), (m, n, k, v)
+
+
+def test_bf16x3_two_temp_n16384_normal_sampled_rows(h):
+    # the split-BF16 low-allocation configuration: n = 16384, N(0,1), Table 2 schedule, depth 2
+    n, cutoff = 16384, 4096
+    v = W | TWO | BF
+    assert depth(h, n, n, n, cutoff, v, 4) == 2
+    st, ws = swmm.sw_mm_workspace_size(n, n, n, cutoff, v, 4)
+    assert st == swmm.SW_OK
+    A, B = inputs.pair(n, n, n, "normal", seed=0, dtype=np.float32)
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    C = swmm.mm(h, dA, dB, cutoff, v, sync=True)
+    rows = np.random.Generator(np.random.PCG64(98)).choice(n, 6, replace=False)
+    R = oracle.naive_mt(A[rows].astype(np.float64), B.astype(np.float64))
+    Cr = C[torch.from_numpy(rows).cuda()].cpu().numpy().astype(np.float64)
+    err = check_close(Cr, R, A, B, 2e-6)
+    assert err <= tol_bf16x3(n, 2)
+    del dA, dB, C
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("sched", [TWO, INPL, ALLOC])
+def test_ragged_leaf_widths_do_not_spill_into_neighbours(h, sched):
+    # leaf widths that are not a multiple of 4 FP32 elements (here 18 and 10): each C quadrant must
+    # only be written inside its own columns
+    for n, cutoff in ((36, 18), (40, 16)):
+        A, B = inputs.pair(n, n, n, "int", seed=75, dtype=np.float64, lim=2)
+        C = run(h, A, B, cutoff, W | sched | BF)
+        assert np.array_equal(C, oracle.naive(A, B)), (n, sched)
