@@ -47,6 +47,7 @@ def parse():
     p.add_argument("--cutoff", type=int, default=0, help="recursion cutoff; 0 = the library's choice")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-oracle sample budget")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-batched", action="store_true")
     p.add_argument("--sweep", action="store_true", help="print plain and L = 1..3 timings, no JSON line")
     p.add_argument("--profile-case", action="store_true",
                    help="only --warmup products plus one more of the chosen variant (for ncu captures)")
@@ -303,6 +304,39 @@ def main():
         e2e = {"value": flop * ke * world / te / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": 2 * n * n * 4,
                "d2h_bytes_per_step": n * n * 4}
 
+    # batched workload: 512 uneven FP32 products (m, n, k log-uniform in [96, 3000]) in one grouped
+    # launch, replayed through its CUDA graph
+    batched = None
+    if not args.no_batched:
+        shapes = inputs.batched_shapes(512, seed=2)
+        g = torch.Generator(device="cuda")
+        g.manual_seed(2)
+        keep, probs = [], []
+        for (m, nn, k) in shapes:
+            tA = torch.rand((m, k), generator=g, device="cuda") * 2 - 1
+            tB = torch.rand((k, nn), generator=g, device="cuda") * 2 - 1
+            tC = torch.empty((m, nn), device="cuda")
+            keep.append((tA, tB, tC))
+            probs.append(swmm.sw_problem(tA.data_ptr(), k, tB.data_ptr(), nn, tC.data_ptr(), nn, m, nn, k))
+        arr = (swmm.sw_problem * len(probs))(*probs)
+        vb = swmm.SW_ALGO_WINOGRAD | swmm.SW_SCHED_FUSED
+        for _ in range(W):
+            swmm.check(h, swmm.sw_mm_batched(h, len(probs), arr, 0, vb, sp))
+        swmm.check(h, swmm.sw_sync(h, sp))
+        kb = max(min(K // 4, 50), 5)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(kb):
+            swmm.check(h, swmm.sw_mm_batched(h, len(probs), arr, 0, vb, sp))
+        e1.record(stream)
+        swmm.check(h, swmm.sw_sync(h, sp))
+        tb = e0.elapsed_time(e1) / kb
+        fl = sum(2.0 * m * nn * k for (m, nn, k) in shapes)
+        batched = {"value": fl / (tb / 1e3) / 1e12, "unit": "TFLOP/s", "ms_per_step": tb, "problems": len(shapes),
+                   "workload": "512 FP32 products, m,n,k log-uniform [96,3000], uniform[-1,1], one grouped "
+                               "launch (CUDA graph replay), depth by the tuned cutoff"}
+        del keep
+
     # CPU oracle on this machine: timed sample rows, also the reference for the error report
     cpu = None
     err = {}
@@ -356,6 +390,7 @@ def main():
             "gpu_launches": launches,
             "cpu_baseline": cpu,
             "e2e": e2e,
+            "batched": batched,
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)

@@ -124,6 +124,28 @@ sw_status sw_smm_host(sw_handle h, const float *A_host, int lda, const float *B_
  * Clears the device error word. */
 sw_status sw_sync(sw_handle h, void *stream);
 
+/* One product of a batch: C <- A B, FP32, row-major, device pointers. */
+typedef struct {
+    const float *A;
+    int lda;
+    const float *B;
+    int ldb;
+    float *C;
+    int ldc;
+    int m, n, k;
+} sw_problem;
+
+/* `count` independent FP32 products (different shapes allowed, any alignment), asynchronous on
+ * `stream`.  The tensor-core work of all products runs as ONE persistent grouped launch; the
+ * per-product staging (packing unaligned A, writing B^T) runs as one batched launch each, and
+ * depth >= 1 products add their operand-sum passes.  The whole batch is captured once into a CUDA
+ * graph and replayed on later calls with the same problem list (same pointers and shapes).
+ * Variant: SW_SCHED_FUSED with SW_LEAF_TF32 (other schedules / leaves: SW_EUNSUPPORTED); each
+ * product's depth follows `cutoff` as for sw_smm (<= 0: the tuned choice).  Odd sizes are padded
+ * virtually (TMA out-of-bounds fill). */
+sw_status sw_mm_batched(sw_handle h, int count, const sw_problem *probs, int cutoff, uint32_t variant,
+                        void *stream);
+
 /* Reductions used by the error checks, FP64 on the device (Sec. 2.1 problem's error metric):
  *   out[0] = max_ij |C_ij - R_ij|,  out[1] = max |A|,  out[2] = max |B|
  * C is FP32 (elem_bytes 4) or FP64 (8); A and B have the same type as C; R is FP64.

@@ -95,7 +95,7 @@ inline long long ceil_div(long long x, long long a) { return (x + a - 1) / a; }
 // ------------------------------------------------------------------ plan
 enum OpKind {
     OP_GEMM_TF32, OP_GEMM_SIMT, OP_ADDSUB, OP_COPY_PAD, OP_PREADD, OP_MEMSET, OP_TRANSPOSE, OP_TRANSPOSE_SQ,
-    OP_SPLIT, OP_GEMM_BF16X3
+    OP_SPLIT, OP_GEMM_BF16X3, OP_BATCH_COPY
 };
 
 struct Op {
@@ -105,6 +105,8 @@ struct Op {
     int bn = 256, nleaves = 0, items = 0, ntmaps = 0, nflags = 0;
     size_t leaves_off = 0, targets_off = 0, refs_off = 0, tmaps_off = 0, flags_off = 0;
     unsigned epoch = 0;  // launches of this op so far (its ordering counters grow by 4 per launch)
+    int ngmaps = 0, njobs = 0, tiles = 0, transpose = 0;
+    size_t gmaps_off = 0, jobs_off = 0;  // operand maps in global memory; batched copy jobs
     // elementwise
     int eb = 4, rows = 0, cols = 0, src_rows = 0, src_cols = 0;
     void* z = nullptr;
@@ -121,7 +123,10 @@ struct Plan {
     void* d_blob = nullptr;
     size_t ws_need = 0;
     int depth = 0;
+    bool use_graph = false;               // replay through a captured CUDA graph
+    cudaGraphExec_t gexec = nullptr;
     ~Plan() {
+        if (gexec) cudaGraphExecDestroy(gexec);
         if (d_blob) cudaFree(d_blob);
     }
 };
@@ -149,6 +154,15 @@ struct Planner {
     Plan* plan;
     std::string err;
     int sched, algo;
+
+    // Batch mode: products append their leaves, targets and operand maps to one grouped launch
+    // instead of emitting their own (operand maps then live in global memory).
+    bool batch = false;
+    int force_bn = 0;
+    std::vector<CUtensorMap> bmaps;
+    std::vector<Leaf> bleaves;
+    std::vector<Target> btargets;
+    int bitems = 0;
 
     View quad(View v, int q) const {
         const int h = v.rows / 2, w = v.cols / 2;
@@ -343,6 +357,34 @@ struct Planner {
         tmap_views.clear();
     }
 
+    // Queue a grouped-GEMM op (its maps / refs already set) with its leaves and targets.
+    void emit_grouped(Op& o, std::vector<Leaf>& leaves, std::vector<Target>& tg, int nflags) {
+        if (batch && o.kind == OP_GEMM_TF32) {
+            const int base = (int)bmaps.size(), tbase = (int)btargets.size();
+            for (int i = 0; i < 4; ++i) bmaps.push_back(o.maps.m[i]);
+            for (const Target& t : tg) btargets.push_back(t);  // target-map indices accumulate in tmaps
+            for (Leaf lf : leaves) {
+                lf.a_map += base;
+                lf.b_map += base;
+                lf.tgt_begin += tbase;
+                lf.tile_begin += bitems;
+                bleaves.push_back(lf);
+            }
+            bitems += o.items;
+            return;
+        }
+        o.nleaves = (int)leaves.size();
+        o.leaves_off = put_blob(leaves.data(), leaves.size() * sizeof(Leaf));
+        o.targets_off = put_blob(tg.data(), tg.size() * sizeof(Target));
+        flush_tmaps(o);
+        if (nflags > 0) {
+            std::vector<unsigned> zeros(nflags, 0u);
+            o.nflags = nflags;
+            o.flags_off = put_blob(zeros.data(), zeros.size() * sizeof(unsigned));
+        }
+        push(o);
+    }
+
     // One leaf product c (=|+=) a b on the tensor cores (FP32: b is held as B^T) or, for FP64,
     // on the SIMT kernel.
     bool gemm(View a, View b, View c, int mode) {
@@ -369,7 +411,7 @@ struct Planner {
         lf.tile_begin = 0;
         Op o;
         o.kind = OP_GEMM_TF32;
-        o.bn = bn_override() ? bn_override() : (c.cols <= 128 ? 128 : 256);
+        o.bn = force_bn ? force_bn : bn_override() ? bn_override() : (c.cols <= 128 ? 128 : 256);
         lf.kblocks = (int)ceil_div(a.cols, tf32_tile_k());
         lf.tiles_n = (int)ceil_div(c.cols, o.bn);
         if (!make_map_f32(&o.maps.m[0], a.p, a.rows, a.cols, a.ld, 32, tf32_tile_m()) ||
@@ -378,11 +420,9 @@ struct Planner {
             return false;
         }
         o.items = (int)(ceil_div(c.rows, tf32_tile_m()) * lf.tiles_n);
-        o.nleaves = 1;
-        o.leaves_off = put_blob(&lf, sizeof(lf));
-        o.targets_off = put_blob(&t, sizeof(t));
-        flush_tmaps(o);
-        push(o);
+        std::vector<Leaf> lv(1, lf);
+        std::vector<Target> tv(1, t);
+        emit_grouped(o, lv, tv, 0);
         return true;
     }
 
@@ -724,10 +764,11 @@ struct Planner {
         // path, where the first writer's tiles lead their position group and the waits are short;
         // deeper levels (many leaves queue behind one writer) and the SIMT FP64 leaf keep a zeroed
         // C and reduce-adds only.
-        const bool ordered = eb == 4 && L == 1;
+        const bool ordered = eb == 4 && L == 1 && !batch;
         if (!ordered) memset0(C);
         const int bn_o = eb == 8 ? F64_BN
-                                 : (bn_override() ? bn_override() : (bf || nb <= 128 ? 128 : 256));
+                                 : force_bn ? force_bn
+                                            : (bn_override() ? bn_override() : (bf || nb <= 128 ? 128 : 256));
         std::vector<int> first_writer(1 << (2 * L), -1), flag_base(1 << (2 * L), -1), flag_cols(1 << (2 * L), 0);
         int nflags = 0;
         // leaves and their Kronecker-product targets
@@ -809,16 +850,7 @@ struct Planner {
                     leaves.push_back(lf);
                 }
         Op o;
-        o.nleaves = (int)leaves.size();
         o.items = items;
-        o.leaves_off = put_blob(leaves.data(), leaves.size() * sizeof(Leaf));
-        o.targets_off = put_blob(tg.data(), tg.size() * sizeof(Target));
-        flush_tmaps(o);
-        if (nflags > 0) {
-            std::vector<unsigned> zeros(nflags, 0u);
-            o.nflags = nflags;
-            o.flags_off = put_blob(zeros.data(), zeros.size() * sizeof(unsigned));
-        }
         if (bf) {
             // split every operand source once: A, B, and the S / T sums
             o.kind = OP_GEMM_BF16X3;
@@ -856,7 +888,79 @@ struct Planner {
                               {SB.p, SB.ld, SB.rows, nb}};
             o.refs_off = put_blob(refs, sizeof(refs));
         }
-        push(o);
+        emit_grouped(o, leaves, tg, nflags);
+        return true;
+    }
+
+    // ---------------------------------------------------------- batched (TF32 leaves)
+    // Many independent products in one grouped launch: one batched copy launch packs the A
+    // operands that are not 16-byte aligned, one batched transpose launch writes every B^T, the
+    // depth >= 1 products add their operand-sum passes, and all leaves of all products go into a
+    // single persistent GEMM launch (longest k first).  C needs no staging: unaligned or ragged
+    // C blocks take the per-thread epilogue.
+    bool batched(const sw_problem* probs, int count, const std::vector<int>& depth) {
+        batch = true;
+        force_bn = 256;
+        std::vector<int> order(count);
+        for (int i = 0; i < count; ++i) order[i] = i;
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return probs[x].k > probs[y].k; });
+        std::vector<CopyJob> packs, trans;
+        int pack_tiles = 0, trans_tiles = 0;
+        std::vector<View> As(count), Bs(count), Cs(count);
+        auto job = [](View src, View dst, int& tiles) {
+            CopyJob j;
+            j.x = src.p; j.ldx = src.ld; j.out = dst.p; j.ldo = dst.ld;
+            j.src_rows = src.rows; j.src_cols = src.cols; j.out_rows = dst.rows; j.out_cols = dst.cols;
+            j.tile_begin = tiles;
+            j.pad_ = 0;
+            tiles += (int)(ceil_div(dst.rows, 32) * ceil_div(dst.cols, 32));
+            return j;
+        };
+        for (int i : order) {
+            const sw_problem& q = probs[i];
+            View a = {(char*)q.A, q.lda, q.m, q.k}, b = {(char*)q.B, q.ldb, q.k, q.n}, c = {(char*)q.C, q.ldc, q.m, q.n};
+            if (q.m == 0 || q.n == 0 || q.k == 0) { As[i] = a; Bs[i] = b; Cs[i] = c; continue; }
+            if (!vec_ok(a)) {
+                View a2 = talloc(q.m, q.k);
+                packs.push_back(job(a, a2, pack_tiles));
+                a = a2;
+            }
+            View bt = talloc(q.n, q.k);
+            trans.push_back(job(b, bt, trans_tiles));
+            As[i] = a;
+            Bs[i] = bt;
+            Cs[i] = c;
+        }
+        if (!dry) {
+            for (int t = 0; t < 2; ++t) {
+                std::vector<CopyJob>& jobs = t == 0 ? packs : trans;
+                if (jobs.empty()) continue;
+                Op o;
+                o.kind = OP_BATCH_COPY;
+                o.njobs = (int)jobs.size();
+                o.tiles = t == 0 ? pack_tiles : trans_tiles;
+                o.transpose = t;
+                o.jobs_off = put_blob(jobs.data(), jobs.size() * sizeof(CopyJob));
+                push(o);
+            }
+        }
+        for (int i : order) {
+            const sw_problem& q = probs[i];
+            if (q.m == 0 || q.n == 0) continue;
+            View c = Cs[i];
+            if (q.k == 0) { memset0(c); continue; }
+            const bool ok = depth[i] == 0 ? gemm(As[i], Bs[i], c, TGT_STORE) : fused(As[i], Bs[i], c, depth[i]);
+            if (!ok) return false;
+        }
+        if (dry || bleaves.empty()) return true;
+        Op o;
+        o.kind = OP_GEMM_TF32;
+        o.bn = force_bn;
+        o.items = bitems;
+        o.ngmaps = (int)bmaps.size();
+        o.gmaps_off = put_blob(bmaps.data(), bmaps.size() * sizeof(CUtensorMap));
+        batch = false;  // the combined op itself is emitted normally
+        emit_grouped(o, bleaves, btargets, 0);
         return true;
     }
 };
@@ -882,6 +986,7 @@ struct sw_handle_s {
     struct ProfRec { int kind; cudaEvent_t e0, e1; };
     std::vector<ProfRec> prof_live;
     std::vector<cudaEvent_t> prof_free;
+    cudaStream_t capture_stream = nullptr;  // private stream for CUDA-graph capture
     std::mutex mu;
 };
 
@@ -1069,7 +1174,9 @@ static sw_status run_plan(sw_handle h, Plan* plan, cudaStream_t s) {
         }
         switch (o.kind) {
             case OP_GEMM_TF32:
-                e = launch_gemm_tf32(o.bn, o.maps, nullptr, reinterpret_cast<const Leaf*>(blob + o.leaves_off),
+                e = launch_gemm_tf32(o.bn, o.maps,
+                                     o.ngmaps ? reinterpret_cast<const CUtensorMap*>(blob + o.gmaps_off) : nullptr,
+                                     reinterpret_cast<const Leaf*>(blob + o.leaves_off),
                                      o.nleaves, reinterpret_cast<const Target*>(blob + o.targets_off),
                                      o.ntmaps ? reinterpret_cast<const CUtensorMap*>(blob + o.tmaps_off) : nullptr,
                                      o.nflags ? reinterpret_cast<unsigned*>(blob + o.flags_off) : nullptr,
@@ -1086,6 +1193,10 @@ static sw_status run_plan(sw_handle h, Plan* plan, cudaStream_t s) {
                 break;
             case OP_TRANSPOSE_SQ:
                 e = launch_transpose_inplace(o.rows, static_cast<float*>(o.z), o.ldz, s);
+                break;
+            case OP_BATCH_COPY:
+                e = launch_batched_copy(reinterpret_cast<const CopyJob*>(blob + o.jobs_off), o.njobs, o.tiles,
+                                        o.transpose, s);
                 break;
             case OP_SPLIT:
                 e = launch_split_bf16(o.rows, o.cols, static_cast<const float*>(o.x), o.ldx, o.z,
@@ -1117,6 +1228,54 @@ static sw_status run_plan(sw_handle h, Plan* plan, cudaStream_t s) {
         }
         if (e != cudaSuccess) return cuda_fail(h, e, "kernel launch");
     }
+    return SW_OK;
+}
+
+// Run a plan: eagerly, or (batched plans, profiling off) through its captured CUDA graph.
+static sw_status execute(sw_handle h, Plan* plan, cudaStream_t s) {
+    if (!plan->use_graph || h->prof) return run_plan(h, plan, s);
+    if (!plan->gexec) {
+        if (!h->capture_stream &&
+            cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking) != cudaSuccess)
+            return cuda_fail(h, cudaGetLastError(), "capture stream");
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(h, e, "begin capture");
+        sw_status st = run_plan(h, plan, h->capture_stream);
+        e = cudaStreamEndCapture(h->capture_stream, &g);
+        if (st != SW_OK) { if (g) cudaGraphDestroy(g); return st; }
+        if (e != cudaSuccess) return cuda_fail(h, e, "end capture");
+        e = cudaGraphInstantiate(&plan->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) { plan->gexec = nullptr; return cuda_fail(h, e, "graph instantiate"); }
+    }
+    cudaError_t e = cudaGraphLaunch(plan->gexec, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "graph launch");
+    return SW_OK;
+}
+
+static sw_status build_batched_plan(sw_handle h, int count, const sw_problem* probs, int cutoff, uint32_t variant,
+                                    bool dry, Plan* plan) {
+    Planner P;
+    P.eb = 4;
+    P.bf = false;
+    P.bt = true;
+    P.variant = variant;
+    P.dry = dry;
+    P.ws_base = h->ws;
+    P.plan = plan;
+    P.sched = SW_SCHED_FUSED;
+    P.algo = (int)(variant & SW_ALGO_MASK);
+    std::vector<int> depth(count);
+    int dmax = 0;
+    for (int i = 0; i < count; ++i) {
+        depth[i] = resolve_depth(probs[i].m, probs[i].n, probs[i].k, cutoff, variant, 4);
+        dmax = std::max(dmax, depth[i]);
+    }
+    plan->depth = dmax;
+    if (!P.batched(probs, count, depth)) return fail(h, SW_ECUDA, P.err.empty() ? "batched planning failed" : P.err);
+    plan->ws_need = P.ws_peak;
+    plan->use_graph = true;
     return SW_OK;
 }
 
@@ -1156,7 +1315,7 @@ static sw_status do_mm(sw_handle h, int eb, const void* A, int lda, const void* 
         if (h->plans.size() >= 256) flush_plans(h);
         h->plans[key] = plan;
     }
-    return run_plan(h, plan, static_cast<cudaStream_t>(stream));
+    return execute(h, plan, static_cast<cudaStream_t>(stream));
 }
 
 // ====================================================================== C ABI
@@ -1188,6 +1347,7 @@ sw_status sw_destroy(sw_handle h) {
     if (h->d_err) cudaFree(h->d_err);
     for (auto& r : h->prof_live) { cudaEventDestroy(r.e0); cudaEventDestroy(r.e1); }
     for (auto e : h->prof_free) cudaEventDestroy(e);
+    if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
     delete h;
     return SW_OK;
 }
@@ -1221,6 +1381,52 @@ sw_status sw_smm(sw_handle h, const float* A, int lda, const float* B, int ldb, 
 sw_status sw_dmm(sw_handle h, const double* A, int lda, const double* B, int ldb, double* C, int ldc, int m, int n,
                  int k, int cutoff, uint32_t variant, void* stream) {
     return do_mm(h, 8, A, lda, B, ldb, C, ldc, m, n, k, cutoff, variant, stream);
+}
+
+sw_status sw_mm_batched(sw_handle h, int count, const sw_problem* probs, int cutoff, uint32_t variant, void* stream) {
+    if (!h) return SW_EINVAL;
+    if (count < 0 || (count > 0 && !probs)) return fail(h, SW_EINVAL, "bad problem list");
+    if ((variant & SW_SCHED_MASK) != SW_SCHED_FUSED || (variant & SW_LEAF_MASK) != SW_LEAF_TF32)
+        return fail(h, SW_EUNSUPPORTED, "batched products take the FUSED schedule with TF32 leaves");
+    if ((variant & SW_ALGO_MASK) > SW_ALGO_WINOGRAD) return fail(h, SW_EINVAL, "unknown algorithm bits");
+    for (int i = 0; i < count; ++i) {
+        const sw_problem& q = probs[i];
+        if (q.m < 0 || q.n < 0 || q.k < 0) return fail(h, SW_EINVAL, "negative dimension in problem " + std::to_string(i));
+        if ((q.m && q.k && (!q.A || q.lda < q.k)) || (q.k && q.n && (!q.B || q.ldb < q.n)) ||
+            (q.m && q.n && (!q.C || q.ldc < q.n)))
+            return fail(h, SW_EINVAL, "bad pointer or leading dimension in problem " + std::to_string(i));
+    }
+    if (count == 0) return SW_OK;
+    std::lock_guard<std::mutex> lock(h->mu);
+    cudaSetDevice(h->device);
+    // plan key: the problem list's bytes
+    std::string key = "B|" + std::to_string(count) + "|" + std::to_string(cutoff) + "|" + std::to_string(variant) + "|";
+    key.append(reinterpret_cast<const char*>(probs), sizeof(sw_problem) * (size_t)count);
+    auto it = h->plans.find(key);
+    Plan* plan = nullptr;
+    if (it != h->plans.end()) {
+        plan = it->second;
+    } else {
+        Plan dryp;
+        sw_status st = build_batched_plan(h, count, probs, cutoff, variant, true, &dryp);
+        if (st != SW_OK) return st;
+        st = ensure_ws(h, dryp.ws_need);
+        if (st != SW_OK) return st;
+        plan = new Plan();
+        st = build_batched_plan(h, count, probs, cutoff, variant, false, plan);
+        if (st != SW_OK) { delete plan; return st; }
+        if (!plan->blob.empty()) {
+            if (cudaMalloc(&plan->d_blob, plan->blob.size()) != cudaSuccess) {
+                cudaGetLastError();
+                delete plan;
+                return fail(h, SW_ENOMEM, "descriptor allocation failed");
+            }
+            cudaMemcpy(plan->d_blob, plan->blob.data(), plan->blob.size(), cudaMemcpyHostToDevice);
+        }
+        if (h->plans.size() >= 256) flush_plans(h);
+        h->plans[key] = plan;
+    }
+    return execute(h, plan, static_cast<cudaStream_t>(stream));
 }
 
 sw_status sw_smm_host(sw_handle h, const float* A, int lda, const float* B, int ldb, float* C, int ldc, int m, int n,

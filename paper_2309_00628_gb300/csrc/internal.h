@@ -77,6 +77,18 @@ struct PreaddArgs {
 };
 cudaError_t launch_preadd(int elem_bytes, const PreaddArgs& a, cudaStream_t stream);
 
+// One FP32 copy (or transpose) job of a batched launch: out (out_rows x out_cols) <- x or x^T,
+// zero outside the source extent; tile_begin is the job's first 32 x 32 tile (prefix sum).
+struct CopyJob {
+    const void* x;
+    long long ldx;
+    void* out;
+    long long ldo;
+    int src_rows, src_cols, out_rows, out_cols;
+    int tile_begin, pad_;
+};
+cudaError_t launch_batched_copy(const CopyJob* jobs, int njobs, int total_tiles, int transpose, cudaStream_t s);
+
 // Device reductions for the error metric (results are written to d_out[0..2] as doubles).
 cudaError_t launch_norms(int elem_bytes, int m, int n, int k, const void* A, long long lda, const void* B,
                          long long ldb, const void* C, long long ldc, const double* R, long long ldr,

@@ -523,6 +523,48 @@ cudaError_t launch_transpose_inplace(int n, float* x, long long ld, cudaStream_t
     return cudaGetLastError();
 }
 
+// ============================================================== batched copies / transposes
+// One launch over many independent FP32 copies: job j covers tiles [tile_begin, tile_begin + tiles)
+// of 32 x 32; a block finds its job by binary search.  `transpose` selects out = x^T.
+__global__ void batched_copy_kernel(const CopyJob* __restrict__ jobs, int njobs, int transpose) {
+    int lo = 0, hi = njobs - 1;
+    const int b = blockIdx.x;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (jobs[mid].tile_begin <= b) lo = mid; else hi = mid - 1;
+    }
+    const CopyJob J = jobs[lo];
+    const int t = b - J.tile_begin;
+    const int tiles_c = (J.out_cols + 31) / 32;
+    const int r0 = (t / tiles_c) * 32, c0 = (t % tiles_c) * 32;
+    const float* x = static_cast<const float*>(J.x);
+    float* out = static_cast<float*>(J.out);
+    if (!transpose) {
+        for (int i = threadIdx.y; i < 32; i += 8) {
+            const int r = r0 + i, c = c0 + threadIdx.x;
+            if (r < J.out_rows && c < J.out_cols)
+                out[r * J.ldo + c] = (r < J.src_rows && c < J.src_cols) ? x[r * J.ldx + c] : 0.f;
+        }
+        return;
+    }
+    __shared__ float tt[32][33];
+    for (int i = threadIdx.y; i < 32; i += 8) {
+        const int c = c0 + i, r = r0 + threadIdx.x;  // x row c, column r
+        tt[i][threadIdx.x] = (c < J.src_rows && r < J.src_cols) ? x[c * J.ldx + r] : 0.f;
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += 8) {
+        const int r = r0 + i, c = c0 + threadIdx.x;
+        if (r < J.out_rows && c < J.out_cols) out[r * J.ldo + c] = tt[threadIdx.x][i];
+    }
+}
+
+cudaError_t launch_batched_copy(const CopyJob* jobs, int njobs, int total_tiles, int transpose, cudaStream_t s) {
+    if (njobs <= 0 || total_tiles <= 0) return cudaSuccess;
+    batched_copy_kernel<<<total_tiles, dim3(32, 8), 0, s>>>(jobs, njobs, transpose);
+    return cudaGetLastError();
+}
+
 // ============================================================== norms
 template <typename T>
 __global__ void norms_kernel(int m, int n, int k, const T* A, long long lda, const T* B, long long ldb, const T* C,

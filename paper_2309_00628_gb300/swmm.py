@@ -20,6 +20,13 @@ SW_PAD, SW_PEEL = 0x000, 0x100
 SW_LEAF_TF32, SW_LEAF_BF16X3 = 0x0000, 0x1000
 
 
+class sw_problem(ctypes.Structure):
+    """C <- A B, FP32, row-major, device pointers (include/swmm.h)."""
+    _fields_ = [("A", ctypes.c_void_p), ("lda", ctypes.c_int), ("B", ctypes.c_void_p), ("ldb", ctypes.c_int),
+                ("C", ctypes.c_void_p), ("ldc", ctypes.c_int), ("m", ctypes.c_int), ("n", ctypes.c_int),
+                ("k", ctypes.c_int)]
+
+
 class SwError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 7 else status}: {msg}")
@@ -57,6 +64,8 @@ def load(build_if_missing: bool = False):
     lib.sw_smm_host.argtypes = mm
     lib.sw_sync.argtypes = [_V, _V]
     lib.sw_error_norms.argtypes = [_V, _I, _I, _I, _I, _V, _I, _V, _I, _V, _I, _V, _I, _P(ctypes.c_double), _V]
+    lib.sw_mm_batched.argtypes = [_V, _I, _P(sw_problem), _I, _U, _V]
+    lib.sw_mm_batched.restype = _I
     lib.sw_profile.argtypes = [_V, _I]
     lib.sw_profile_read.argtypes = [_V, _I, _P(_I), _P(ctypes.c_double)]
     for name in ("sw_create", "sw_destroy", "sw_mm_workspace_size", "sw_mm_depth", "sw_smm", "sw_dmm",
@@ -106,6 +115,13 @@ def sw_dmm(h, A, lda, B, ldb, C, ldc, m, n, k, cutoff, variant, stream=None) -> 
 
 def sw_smm_host(h, A, lda, B, ldb, C, ldc, m, n, k, cutoff, variant, stream=None) -> int:
     return load().sw_smm_host(h, A, lda, B, ldb, C, ldc, m, n, k, cutoff, variant, stream)
+
+
+def sw_mm_batched(h, count, probs, cutoff, variant, stream=None) -> int:
+    """probs: a ctypes array of sw_problem (or a list, converted here)."""
+    if not isinstance(probs, ctypes.Array):
+        probs = (sw_problem * len(probs))(*probs)
+    return load().sw_mm_batched(h, count, probs, cutoff, variant, stream)
 
 
 def sw_sync(h, stream=None) -> int:
