@@ -146,6 +146,62 @@ typedef struct {
 sw_status sw_mm_batched(sw_handle h, int count, const sw_problem *probs, int cutoff, uint32_t variant,
                         void *stream);
 
+/* ---------------------------------------------------------------------------------------------
+ * Serving: a request loop with continuous batching.  Requests (FP32 or FP64 products of any
+ * shape) are admitted in arrival order as soon as a completion slot and enough of the serving
+ * arena are free -- also while earlier requests are still running -- and their work overlaps on
+ * the device.  An FP32 request with TF32 leaves whose plan ends in a grouped leaf GEMM (NAIVE and
+ * FUSED schedules on 16-byte aligned operands; the last product of the step-by-step schedules)
+ * runs that GEMM inside one device-resident loop: a persistent kernel on `sm_share` SMs that picks
+ * up newly published tiles while it runs and exits after `idle_us` without work.  Its staging passes
+ * (B^T, operand sums), FP64 requests, split-BF16 leaves and padded or peeled shapes run on side
+ * streams with the SMs the loop leaves free.  A request's result is the same alone and in a mix
+ * (within the tolerance of its leaf precision; bit-identical for the resident TF32 form, whose
+ * tile sums do not depend on the schedule).  The paper has no serving loop: this is the deployment
+ * form of the same products.
+ *
+ * Threading: submit and wait may be called from any thread.  The loop runs on a thread of its own
+ * and uses its own streams, so inputs must be complete on the device when submit is called (the
+ * caller synchronises the stream that wrote them) and C may be read once wait returned SW_OK.
+ * Requests in flight together must not write memory another one reads or writes.  The arena is
+ * allocated at start and is separate from the handle's workspace budget.  When a bounded device
+ * wait expires every request in flight fails with SW_ETIMEOUT and the loop carries on; a CUDA error
+ * fails all current and later requests with SW_ECUDA.
+ */
+typedef struct {
+    int sm_share;        /* SMs (persistent CTAs) of the resident loop; 0: all but 16 */
+    int max_inflight;    /* requests admitted at once; 0: 64 */
+    size_t budget_bytes; /* workspace the admitted requests may hold together; 0: 60 GB or 3/4 of
+                            the free device memory, whichever is less */
+    int idle_us;         /* the resident loop exits after this long without new work; 0: 20000 */
+} sw_server_cfg;
+
+typedef struct {
+    int elem_bytes;      /* 4: FP32 product as sw_smm; 8: FP64 product as sw_dmm */
+    const void *A;
+    int lda;
+    const void *B;
+    int ldb;
+    void *C;
+    int ldc;
+    int m, n, k;
+    int cutoff;
+    uint32_t variant;
+} sw_request;
+
+/* Start the serving loop on the handle (one per handle).  NULL cfg: defaults. */
+sw_status sw_server_start(sw_handle h, const sw_server_cfg *cfg);
+/* Queue a request; the caller keeps A, B and C alive and untouched until sw_server_wait returns
+ * for its ticket.  The workspace is sized here, on the caller's thread: SW_EBUDGET if the request
+ * alone needs more than the arena; SW_EINVAL / SW_EUNSUPPORTED for arguments sw_smm would refuse. */
+sw_status sw_server_submit(sw_handle h, const sw_request *req, uint64_t *ticket);
+/* Wait up to timeout_ns (< 0: no limit) for a ticket: SW_OK once C holds the result, SW_ETIMEOUT if
+ * it is not done yet (the ticket stays valid), or the request's own failure status. */
+sw_status sw_server_wait(sw_handle h, uint64_t ticket, int64_t timeout_ns);
+/* Finish every queued request, stop the loop and release its resources (tickets not yet collected
+ * become invalid).  sw_destroy stops a running loop the same way. */
+sw_status sw_server_stop(sw_handle h);
+
 /* Reductions used by the error checks, FP64 on the device (Sec. 2.1 problem's error metric):
  *   out[0] = max_ij |C_ij - R_ij|,  out[1] = max |A|,  out[2] = max |B|
  * C is FP32 (elem_bytes 4) or FP64 (8); A and B have the same type as C; R is FP64.

@@ -25,6 +25,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <cstring>
 
 #include "plan.h"
 #include "ptx.cuh"
@@ -49,7 +50,7 @@ struct TfCfg {
     static constexpr int STG_OFF = STAGES * STAGE_BYTES;      // epilogue staging: 4 warps x 2 x 4 KB
     static constexpr int STG_BYTES = 4 * 2 * 4096;
     static constexpr int BAR_OFF = STG_OFF + STG_BYTES;
-    static constexpr int SMEM_BYTES = BAR_OFF + 256 + 1024;  // + barriers + alignment slack
+    static constexpr int SMEM_BYTES = BAR_OFF + 512 + 1024;  // + barriers + alignment slack
     // instruction descriptor: D F32; TF32: A/B TF32, both K-major; BF16X3: A/B BF16, A K-major,
     // B MN-major; N = BN, M = 128
     static constexpr uint32_t IDESC =
@@ -84,6 +85,56 @@ __device__ __forceinline__ ItemPos decode_item(const Leaf* __restrict__ leaves, 
     p.tn = r / gsz;
     (void)bn;
     return p;
+}
+
+// Tile position of an item whose leaf is known (resident mode: leaf index from item_leaf).
+__device__ __forceinline__ ItemPos decode_in_leaf(const Leaf* __restrict__ leaves, int leaf, int item) {
+    const Leaf* L = &leaves[leaf];
+    int local = item - __ldg(&L->tile_begin);
+    int tiles_m = (__ldg(&L->m) + TF_BM - 1) / TF_BM;
+    int tiles_n = __ldg(&L->tiles_n);
+    int per_group = TF_GROUP_M * tiles_n;
+    int g = local / per_group;
+    int first_m = g * TF_GROUP_M;
+    int gsz = min(tiles_m - first_m, TF_GROUP_M);
+    int r = local - g * per_group;
+    ItemPos p;
+    p.leaf = leaf;
+    p.tm = first_m + r % gsz;
+    p.tn = r / gsz;
+    return p;
+}
+
+__device__ __forceinline__ unsigned ld_acquire_sys_u32(const volatile unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.sys.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Resident mode: claim the next published item (compare-and-swap, so an exiting CTA never holds
+// an unprocessed claim), or -1 on stop, error or `idle_ns` without new work.  `pub` caches the
+// published count: it only grows while the kernel runs, so host memory is read only when the
+// claims have caught up with the cached value.
+__device__ __forceinline__ int res_claim(const ResidentCtl& c, unsigned& pub, int* err) {
+    const unsigned long long t0 = globaltimer();
+    for (;;) {
+        const unsigned cur = *reinterpret_cast<volatile unsigned*>(c.next);
+        if (cur >= pub) pub = ld_acquire_sys_u32(c.published);
+        if (cur < pub) {
+            if (atomicCAS(c.next, cur, cur + 1u) == cur) return (int)cur;
+            continue;
+        }
+        if (*c.stop) return -1;
+        if (error_raised(err)) return -1;
+        if (globaltimer() - t0 > c.idle_ns) return -1;
+        __nanosleep(1000);
+    }
+}
+
+// Descriptors appended while the kernel runs: order the tensor-map reads after the claim.
+__device__ __forceinline__ void tensormap_acquire(const CUtensorMap* m) {
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(m))
+                 : "memory");
 }
 
 __device__ __forceinline__ const CUtensorMap* pick_map(const MapSet& maps, const CUtensorMap* gmaps, int idx) {
@@ -125,12 +176,12 @@ __device__ __forceinline__ void store_row32(const Target& t, int row, int col0, 
     }
 }
 
-template <int MODE, int BN>
+template <int MODE, int BN, bool RES>
 __global__ void __launch_bounds__(192, 1)
     gemm_tc_kernel(const __grid_constant__ MapSet maps, const CUtensorMap* __restrict__ gmaps,
                      const Leaf* __restrict__ leaves, int nleaves, const Target* __restrict__ targets,
                      const CUtensorMap* __restrict__ tmaps, unsigned* __restrict__ flags, unsigned epoch,
-                     int total_items, int* err) {
+                     int total_items, int* err, const ResidentCtl ctl) {
     using Cfg = TfCfg<MODE, BN>;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw_addr = smem_u32(smem_raw);
@@ -147,7 +198,10 @@ __global__ void __launch_bounds__(192, 1)
     uint64_t* tfull = bars + 2 * Cfg::STAGES;    // [2]
     uint64_t* tempty = tfull + 2;                // [2]
     uint64_t* done = tempty + 2;                 // [1]
-    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(done + 1);
+    uint64_t* ring_full = done + 1;              // [4] resident mode: item ring, producer -> consumers
+    uint64_t* ring_empty = ring_full + 4;        // [4] consumers (MMA + 4 epilogue warps) -> producer
+    volatile int* ring = reinterpret_cast<volatile int*>(ring_empty + 4);  // [4]
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(ring_empty + 4) + 4;
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
@@ -162,6 +216,10 @@ __global__ void __launch_bounds__(192, 1)
             mbar_init(&tempty[a], 4);
         }
         mbar_init(done, 1);
+        for (int r = 0; r < 4; ++r) {
+            mbar_init(&ring_full[r], 1);
+            mbar_init(&ring_empty[r], 5);
+        }
         fence_mbar_init();
     }
     if (warp == 1) {
@@ -180,8 +238,22 @@ __global__ void __launch_bounds__(192, 1)
             uint32_t phase = 0;
             int issued = 0;
             bool ok = true;
-            for (int item = blockIdx.x; item < total_items && ok; item += gridDim.x) {
-                const ItemPos ip = decode_item(leaves, nleaves, item, BN);
+            int rslot = 0;
+            uint32_t rph = 0;
+            unsigned pub = 0;
+            for (int item = RES ? -1 : (int)blockIdx.x;; item += RES ? 0 : gridDim.x) {
+                if (RES) {  // claim a published item and hand it to the consumers
+                    item = res_claim(ctl, pub, err);
+                    if (!mbar_wait(&ring_empty[rslot], rph ^ 1u, err, ERR_WAIT_EMPTY)) break;
+                    ring[rslot] = item;
+                    mbar_arrive(&ring_full[rslot]);
+                    if (++rslot == 4) { rslot = 0; rph ^= 1u; }
+                    if (item < 0) break;
+                } else if (item >= total_items || !ok) {
+                    break;
+                }
+                const ItemPos ip = RES ? decode_in_leaf(leaves, __ldcg(&ctl.item_leaf[item]), item)
+                                       : decode_item(leaves, nleaves, item, BN);
                 const Leaf* L = &leaves[ip.leaf];
                 const int am = __ldg(&L->a_map), bm = __ldg(&L->b_map);
                 const int a_row = __ldg(&L->a_row) + ip.tm * TF_BM;
@@ -195,6 +267,13 @@ __global__ void __launch_bounds__(192, 1)
                     set_error(err, ERR_ALIGN);
                     ok = false;
                     break;
+                }
+                if (RES) {
+#pragma unroll
+                    for (int op = 0; op < Cfg::NOPS; ++op) {
+                        tensormap_acquire(pick_map(maps, gmaps, am * Cfg::NOPS + op));
+                        tensormap_acquire(pick_map(maps, gmaps, bm * Cfg::NOPS + op));
+                    }
                 }
                 for (int kb = 0; kb < kb_n; ++kb) {
                     if (!mbar_wait(&empty[stage], phase ^ 1u, err, ERR_WAIT_EMPTY)) { ok = false; break; }
@@ -216,6 +295,7 @@ __global__ void __launch_bounds__(192, 1)
                     ++issued;
                     if (++stage == Cfg::STAGES) { stage = 0; phase ^= 1u; }
                 }
+                if (!ok) break;
             }
             // drain: every issued copy must have landed before the CTA may exit
             int s = stage;
@@ -232,8 +312,20 @@ __global__ void __launch_bounds__(192, 1)
             uint32_t phase = 0;
             int local = 0;
             bool ok = true;
-            for (int item = blockIdx.x; item < total_items && ok; item += gridDim.x, ++local) {
-                const ItemPos ip = decode_item(leaves, nleaves, item, BN);
+            int rslot = 0;
+            uint32_t rph = 0;
+            for (int item = RES ? -1 : (int)blockIdx.x;; item += RES ? 0 : gridDim.x, ++local) {
+                if (RES) {
+                    if (!mbar_wait(&ring_full[rslot], rph, err, ERR_WAIT_FULL)) break;
+                    item = ring[rslot];
+                    mbar_arrive(&ring_empty[rslot]);
+                    if (++rslot == 4) { rslot = 0; rph ^= 1u; }
+                    if (item < 0) break;
+                } else if (item >= total_items || !ok) {
+                    break;
+                }
+                const ItemPos ip = RES ? decode_in_leaf(leaves, __ldcg(&ctl.item_leaf[item]), item)
+                                       : decode_item(leaves, nleaves, item, BN);
                 const int kb_n = __ldg(&leaves[ip.leaf].kblocks);
                 const int acc = local & 1;
                 const uint32_t acc_phase = (local >> 1) & 1;
@@ -284,8 +376,23 @@ __global__ void __launch_bounds__(192, 1)
         uint8_t* stg = base + Cfg::STG_OFF + (warp - 2) * 8192;  // two 4 KB swizzled buffers
         int local = 0, chunk_ctr = 0;
         bool issued_bulk = false;
-        for (int item = blockIdx.x; item < total_items; item += gridDim.x, ++local) {
-            const ItemPos ip = decode_item(leaves, nleaves, item, BN);
+        int rslot = 0;
+        uint32_t rph = 0;
+        for (int item = RES ? -1 : (int)blockIdx.x;; item += RES ? 0 : gridDim.x, ++local) {
+            if (RES) {
+                int it = -1;
+                if (lane == 0) {
+                    if (mbar_wait(&ring_full[rslot], rph, err, ERR_WAIT_ACC)) it = ring[rslot];
+                    mbar_arrive(&ring_empty[rslot]);
+                }
+                item = __shfl_sync(0xffffffffu, it, 0);
+                if (++rslot == 4) { rslot = 0; rph ^= 1u; }
+                if (item < 0) break;
+            } else if (item >= total_items) {
+                break;
+            }
+            const ItemPos ip = RES ? decode_in_leaf(leaves, __ldcg(&ctl.item_leaf[item]), item)
+                                   : decode_item(leaves, nleaves, item, BN);
             const Leaf* L = &leaves[ip.leaf];
             const int acc = local & 1;
             const uint32_t acc_phase = (local >> 1) & 1;
@@ -358,6 +465,7 @@ __global__ void __launch_bounds__(192, 1)
                             const Target& tg = targets[tb + t];
                             if (row_w >= tg.rows || col0 >= tg.cols) continue;
                             const CUtensorMap* m = tmaps + tg.map;
+                            if (RES) tensormap_acquire(m);
                             const uint8_t* src = tg.sign > 0.f ? bpos : bneg;
                             if (tg.mode == TGT_STORE) tma_store_2d(m, src, col0, row_w);
                             else tma_reduce_add_2d(m, src, col0, row_w);
@@ -394,6 +502,17 @@ __global__ void __launch_bounds__(192, 1)
                 }
                 __syncwarp();
             }
+            // resident mode: report the item once this warp's part of it is stored
+            if (RES) {
+                const int tag = __ldg(&L->tag);
+                if (tag >= 0) {
+                    if (lane == 0 && issued_bulk) bulk_wait<0>();
+                    fence_async_global();
+                    __threadfence();
+                    __syncwarp();
+                    if (lane == 0) red_release_add_u32(ctl.done + tag, 1u);
+                }
+            }
             if (!ordered_ok) break;
         }
         // all bulk stores / reductions must be complete before the CTA (and its shared memory) ends
@@ -409,24 +528,41 @@ __global__ void __launch_bounds__(192, 1)
     }
 }
 
-template <int MODE, int BN>
+template <int MODE, int BN, bool RES = false>
 static cudaError_t launch_tc_impl(const MapSet& maps, const CUtensorMap* gmaps, const Leaf* leaves, int nleaves,
                                   const Target* targets, const CUtensorMap* tmaps, unsigned* flags, unsigned epoch,
-                                  int total_items, int* err, int grid, cudaStream_t stream) {
+                                  int total_items, int* err, int grid, cudaStream_t stream,
+                                  const ResidentCtl* ctl = nullptr) {
     using Cfg = TfCfg<MODE, BN>;
     static_assert(Cfg::SMEM_BYTES <= 232448, "shared memory budget");
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<MODE, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             Cfg::SMEM_BYTES);
+        cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<MODE, BN, RES>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM_BYTES);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    if (total_items <= 0) return cudaSuccess;
-    if (grid > total_items) grid = total_items;
-    gemm_tc_kernel<MODE, BN><<<grid, 192, Cfg::SMEM_BYTES, stream>>>(maps, gmaps, leaves, nleaves, targets, tmaps,
-                                                                      flags, epoch, total_items, err);
+    ResidentCtl c;
+    memset(&c, 0, sizeof(c));
+    if (RES) {
+        if (!ctl) return cudaErrorInvalidValue;
+        c = *ctl;
+    } else {
+        if (total_items <= 0) return cudaSuccess;
+        if (grid > total_items) grid = total_items;
+    }
+    gemm_tc_kernel<MODE, BN, RES><<<grid, 192, Cfg::SMEM_BYTES, stream>>>(maps, gmaps, leaves, nleaves, targets,
+                                                                           tmaps, flags, epoch, total_items, err, c);
     return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_tf32_resident(const CUtensorMap* gmaps, const Leaf* leaves, const Target* targets,
+                                      const CUtensorMap* tmaps, const ResidentCtl& ctl, int* err, int grid,
+                                      cudaStream_t stream) {
+    MapSet none;
+    memset(&none, 0, sizeof(none));
+    return launch_tc_impl<MODE_TF32, 256, true>(none, gmaps, leaves, 0, targets, tmaps, nullptr, 0, 0, err, grid,
+                                                stream, &ctl);
 }
 
 cudaError_t launch_gemm_tf32(int bn, const MapSet& maps, const CUtensorMap* gmaps, const Leaf* leaves, int nleaves,

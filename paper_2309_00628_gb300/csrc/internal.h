@@ -28,6 +28,11 @@ struct MatRef {
 cudaError_t launch_gemm_tf32(int bn, const MapSet& maps, const CUtensorMap* gmaps, const Leaf* leaves, int nleaves,
                              const Target* targets, const CUtensorMap* tmaps, unsigned* flags, unsigned epoch,
                              int total_items, int* err, int grid, cudaStream_t stream);
+// Resident (serving) form of the TF32 grouped GEMM, BN = 256: runs until ctl.stop, an error, or
+// ctl.idle_ns without newly published items.
+cudaError_t launch_gemm_tf32_resident(const CUtensorMap* gmaps, const Leaf* leaves, const Target* targets,
+                                      const CUtensorMap* tmaps, const ResidentCtl& ctl, int* err, int grid,
+                                      cudaStream_t stream);
 int tf32_tile_m();
 int tf32_tile_k();
 int bf16x3_tile_k();

@@ -138,6 +138,7 @@ __global__ void noalloc_describe(swk::Leaf* leaves, swk::Target* targets, float*
         lf.tgt_begin = t;
         lf.c_row0 = 0;
         lf.c_col0 = 0;
+        lf.tag = -1;
         int cnt = 0;
         for (int i = 0; i < ntg[p]; ++i) {
             const int q = tq[p][i], r = q >> 1, c = q & 1;

@@ -55,6 +55,21 @@ struct Leaf {
     int tile_begin;    // index of the leaf's first work item
     int tiles_n;
     int c_row0, c_col0;  // position of the leaf's tile (0, 0) inside its target blocks
+    int tag;             // resident server: completion counter of the leaf's request (-1: none)
+    int pad_[3];
+};
+
+// Work source of the resident (serving) form of the grouped GEMM: items are published by the
+// host while the kernel runs.  `published` and `stop` live in host-mapped memory; each CTA claims
+// published items one at a time (compare-and-swap on `next`) and, after `idle_ns` without new
+// work, exits.  Every epilogue warp adds 1 to done[leaf.tag] when its part of a tile is stored.
+struct ResidentCtl {
+    unsigned* next;                   // device: next unclaimed item
+    const volatile unsigned* published;  // host-mapped: items the host has published
+    const volatile unsigned* stop;       // host-mapped: nonzero asks the kernel to exit
+    const int* item_leaf;             // device: leaf index of every published item
+    unsigned* done;                   // device: per-request completion counters
+    unsigned long long idle_ns;
 };
 
 }  // namespace swk

@@ -27,6 +27,20 @@ class sw_problem(ctypes.Structure):
                 ("k", ctypes.c_int)]
 
 
+class sw_server_cfg(ctypes.Structure):
+    """Serving-loop parameters (include/swmm.h); zero fields take the documented defaults."""
+    _fields_ = [("sm_share", ctypes.c_int), ("max_inflight", ctypes.c_int), ("budget_bytes", ctypes.c_size_t),
+                ("idle_us", ctypes.c_int)]
+
+
+class sw_request(ctypes.Structure):
+    """One served product: elem_bytes 4 (as sw_smm) or 8 (as sw_dmm), device pointers."""
+    _fields_ = [("elem_bytes", ctypes.c_int), ("A", ctypes.c_void_p), ("lda", ctypes.c_int),
+                ("B", ctypes.c_void_p), ("ldb", ctypes.c_int), ("C", ctypes.c_void_p), ("ldc", ctypes.c_int),
+                ("m", ctypes.c_int), ("n", ctypes.c_int), ("k", ctypes.c_int), ("cutoff", ctypes.c_int),
+                ("variant", ctypes.c_uint32)]
+
+
 class SwError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 7 else status}: {msg}")
@@ -68,8 +82,13 @@ def load(build_if_missing: bool = False):
     lib.sw_mm_batched.restype = _I
     lib.sw_profile.argtypes = [_V, _I]
     lib.sw_profile_read.argtypes = [_V, _I, _P(_I), _P(ctypes.c_double)]
+    lib.sw_server_start.argtypes = [_V, _P(sw_server_cfg)]
+    lib.sw_server_submit.argtypes = [_V, _P(sw_request), _P(ctypes.c_uint64)]
+    lib.sw_server_wait.argtypes = [_V, ctypes.c_uint64, ctypes.c_int64]
+    lib.sw_server_stop.argtypes = [_V]
     for name in ("sw_create", "sw_destroy", "sw_mm_workspace_size", "sw_mm_depth", "sw_smm", "sw_dmm",
-                 "sw_smm_host", "sw_sync", "sw_error_norms", "sw_profile", "sw_profile_read"):
+                 "sw_smm_host", "sw_sync", "sw_error_norms", "sw_profile", "sw_profile_read", "sw_server_start",
+                 "sw_server_submit", "sw_server_wait", "sw_server_stop"):
         getattr(lib, name).restype = _I
     _lib = lib
     return lib
@@ -149,6 +168,35 @@ def sw_profile_read(h):
     ms = (ctypes.c_double * n)()
     st = load().sw_profile_read(h, n, launches, ms)
     return st, {PROFILE_KINDS[i]: (launches[i], ms[i]) for i in range(n)}
+
+
+def sw_server_start(h, cfg: sw_server_cfg | None = None) -> int:
+    return load().sw_server_start(h, ctypes.byref(cfg) if cfg is not None else None)
+
+
+def sw_server_submit(h, req: sw_request):
+    """Returns (status, ticket)."""
+    t = ctypes.c_uint64(0)
+    st = load().sw_server_submit(h, ctypes.byref(req), ctypes.byref(t))
+    return st, t.value
+
+
+def sw_server_wait(h, ticket: int, timeout_ns: int = -1) -> int:
+    return load().sw_server_wait(h, ticket, timeout_ns)
+
+
+def sw_server_stop(h) -> int:
+    return load().sw_server_stop(h)
+
+
+def request(A, B, C, cutoff: int = 0, variant: int = SW_ALGO_WINOGRAD) -> sw_request:
+    """sw_request for C = A @ B on row-major CUDA tensors (float32 or float64)."""
+    import torch
+    m, k = A.shape
+    n = B.shape[1]
+    eb = 4 if A.dtype == torch.float32 else 8
+    return sw_request(eb, A.data_ptr(), max(A.stride(0), 1), B.data_ptr(), max(B.stride(0), 1), C.data_ptr(),
+                      max(C.stride(0), 1), m, n, k, cutoff, variant)
 
 
 def check(h, status: int) -> None:
