@@ -48,6 +48,10 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-oracle sample budget")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-batched", action="store_true")
+    p.add_argument("--no-serving", action="store_true")
+    p.add_argument("--serve-rates", default="2,4,8", help="Poisson arrival rates (requests/s) of the serving sweep")
+    p.add_argument("--serve-requests", type=int, default=40, help="requests per rate")
+    p.add_argument("--serve-share", type=int, default=16, help="SMs of the resident leaf-GEMM loop")
     p.add_argument("--sweep", action="store_true", help="print plain and L = 1..3 timings, no JSON line")
     p.add_argument("--profile-case", action="store_true",
                    help="only --warmup products plus one more of the chosen variant (for ncu captures)")
@@ -128,6 +132,111 @@ def traffic_from_profiles(kernel_file: str, workload: str):
 
 def leaf_flops(n: int, L: int) -> float:
     return 2.0 * (n >> L) ** 3 * 7 ** L
+
+
+def serving_bench(h, swmm, torch, rates, count, share, seed=3):
+    """Poisson arrivals of the FP32 / FP64 serving mix through sw_server_*; per rate: achieved
+    throughput, p50 / p99 latency (submit to completion, host clock), Freivalds error; once: the
+    largest difference of a served result from the same request run alone."""
+    import ctypes
+    import threading
+    reqs = inputs.serving_requests(count, seed)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    bufs = []
+    for (m, n, k, eb) in reqs:
+        dt = torch.float32 if eb == 4 else torch.float64
+        A = torch.rand((m, k), generator=g, device="cuda", dtype=dt) * 2 - 1
+        B = torch.rand((k, n), generator=g, device="cuda", dtype=dt) * 2 - 1
+        C = torch.empty((m, n), device="cuda", dtype=dt)
+        var = swmm.SW_ALGO_WINOGRAD | swmm.SW_SCHED_FUSED
+        bufs.append((A, B, C, swmm.request(A, B, C, 0, var), var))
+    torch.cuda.synchronize()
+    flops = sum(2.0 * m * n * k for (m, n, k, _) in reqs)
+    cfg = swmm.sw_server_cfg(share, 64, 60 << 30, 20000)
+    swmm.check(h, swmm.sw_server_start(h, cfg))
+    try:
+        ts = []  # warm-up: every request once (module loads, tensor-map encoders, first launches)
+        for b in bufs:
+            st, t = swmm.sw_server_submit(h, b[3])
+            swmm.check(h, st)
+            ts.append(t)
+        for t in ts:
+            swmm.check(h, swmm.sw_server_wait(h, t, -1))
+        rows = []
+        for rate in rates:
+            arr = np.cumsum(np.random.Generator(np.random.PCG64(seed)).exponential(1.0 / rate, count))
+            lat = [0.0] * count
+            out = {}
+            lock = threading.Lock()
+            t0 = time.perf_counter()
+
+            def submitter():
+                for i in range(count):
+                    d = t0 + arr[i] - time.perf_counter()
+                    if d > 0:
+                        time.sleep(d)
+                    ts_ = time.perf_counter()
+                    st_, t_ = swmm.sw_server_submit(h, bufs[i][3])
+                    with lock:
+                        out[t_] = (i, ts_, st_)
+
+            th = threading.Thread(target=submitter)
+            th.start()
+            done, t_last = 0, t0
+            while done < count:
+                with lock:
+                    pend = list(out.items())
+                for t_, (i, ts_, st_) in pend:
+                    if st_ != swmm.SW_OK:
+                        raise RuntimeError(f"submit failed: {swmm.sw_last_error(h)}")
+                    st_ = swmm.sw_server_wait(h, t_, 0)
+                    if st_ == swmm.SW_ETIMEOUT:
+                        continue
+                    swmm.check(h, st_)
+                    t_last = time.perf_counter()
+                    lat[i] = t_last - ts_
+                    with lock:
+                        del out[t_]
+                    done += 1
+                time.sleep(50e-6)
+            th.join()
+            span = t_last - (t0 + arr[0])
+            ls = sorted(lat)
+            rows.append({"rate_per_s": rate, "requests": count, "achieved_req_per_s": count / span,
+                         "eff_tflops": flops / span / 1e12, "p50_ms": 1e3 * statistics.median(ls),
+                         "p99_ms": 1e3 * ls[min(count - 1, int(math.ceil(0.99 * count)) - 1)],
+                         "max_ms": 1e3 * ls[-1]})
+        # accuracy of the last rate's results: Freivalds with random signs, normalised like the
+        # element-wise metric; then each request alone (sw_smm / sw_dmm) against its served result
+        gx = torch.Generator(device="cuda")
+        gx.manual_seed(seed + 1)
+        worst = {4: 0.0, 8: 0.0}
+        solo_diff = {4: 0.0, 8: 0.0}
+        for (m, n, k, eb), (A, B, C, r, var) in zip(reqs, bufs):
+            x = (torch.randint(0, 2, (n, 1), generator=gx, device="cuda").double() * 2 - 1)
+            Ad, Bd = A.double(), B.double()
+            scale = math.sqrt(n) * k * float(Ad.abs().max()) * float(Bd.abs().max())
+            res = float((C.double() @ x - Ad @ (Bd @ x)).abs().max()) / scale
+            worst[eb] = max(worst[eb], res)
+            S = torch.empty_like(C)
+            fn = swmm.sw_smm if eb == 4 else swmm.sw_dmm
+            pp = lambda t: ctypes.c_void_p(t.data_ptr())
+            swmm.check(h, fn(h, pp(A), k, pp(B), n, pp(S), n, m, n, k, 0, var, None))
+            swmm.check(h, swmm.sw_sync(h, None))
+            d = float((S.double() - C.double()).abs().max()) / (k * float(Ad.abs().max()) * float(Bd.abs().max()))
+            solo_diff[eb] = max(solo_diff[eb], d)
+    finally:
+        swmm.sw_server_stop(h)
+    n64 = sum(1 for r in reqs if r[3] == 8)
+    return {"workload": f"{count} requests per rate, Poisson arrivals (seed {seed}); FP32 (TF32 leaves) / FP64 "
+                        f"50/50 ({count - n64}/{n64}); order s in {{512..8192}}, square or aspect <= 8:1; "
+                        f"Winograd FUSED, library cutoff; uniform[-1,1]",
+            "sm_share": share, "budget_gb": 60, "flops_per_pass": flops, "rates": rows,
+            "freivalds_err": {"fp32": worst[4], "fp64": worst[8],
+                              "metric": "max|C x - A (B x)| / (sqrt(n) k max|A| max|B|), x random signs"},
+            "mix_vs_solo": {"fp32": solo_diff[4], "fp64": solo_diff[8],
+                            "metric": "max|C_served - C_alone| / (k max|A| max|B|)"}}
 
 
 # ---------------------------------------------------------------- reference arm: the CPU oracle
@@ -337,6 +446,11 @@ def main():
                                "launch (CUDA graph replay), depth by the tuned cutoff"}
         del keep
 
+    serving = None
+    if not args.no_serving and world == 1:
+        rates = [float(x) for x in args.serve_rates.split(",") if x]
+        serving = serving_bench(h, swmm, torch, rates, args.serve_requests, args.serve_share)
+
     # CPU oracle on this machine: timed sample rows, also the reference for the error report
     cpu = None
     err = {}
@@ -363,7 +477,7 @@ def main():
             err[name] = float(np.max(np.abs(Cr - R)) / (n * amax * bmax))
 
     if rank == 0:
-        traffic = traffic_from_profiles("gemm_tf32.cu", f"gemm_tf32_winograd_n{n}_L{L}")
+        traffic = traffic_from_profiles("gemm_tc.cu", f"gemm_tf32_winograd_n{n}_L{L}")
         lat = sorted(per)
         line = {
             "metric": "effective TFLOP/s (2mnk/t), Winograd vs plain GEMM, same error",
@@ -391,6 +505,7 @@ def main():
             "cpu_baseline": cpu,
             "e2e": e2e,
             "batched": batched,
+            "serving": serving,
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)

@@ -74,11 +74,13 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, so)
-    for o in objs:
-        try:
-            os.remove(o)
-        except OSError:
-            pass
+    # object files and libraries of older source versions are never loaded again
+    for f in glob.glob(os.path.join(OUT, "*.o")) + glob.glob(os.path.join(OUT, "libswmm_*.so")):
+        if f != so:
+            try:
+                os.remove(f)
+            except OSError:
+                pass
     return so
 
 

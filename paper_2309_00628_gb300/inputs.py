@@ -43,3 +43,29 @@ def batched_shapes(count: int = 512, lo: int = 96, hi: int = 3000, seed: int = 2
     u = g.uniform(math.log(lo), math.log(hi), size=(count, 3))
     dims = np.rint(np.exp(u)).astype(np.int64)
     return [tuple(int(v) for v in row) for row in dims]
+
+
+def serving_requests(count: int = 40, seed: int = 3, sizes=(512, 1024, 2048, 4096, 8192), max_aspect: float = 8.0,
+                     align: int = 32):
+    """The serving mix: (m, n, k, elem_bytes) per request.
+
+    elem_bytes is 4 or 8 with probability 1/2 each; a base order s is drawn uniformly from
+    `sizes`; half the requests are square (s, s, s), the others rectangular with aspect
+    a = exp(U(0, ln max_aspect)) between two of the three dimensions (s sqrt(a) and s / sqrt(a),
+    rounded to a multiple of `align`, the third left at s, the dimensions in random order).
+    """
+    g = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for _ in range(count):
+        eb = 4 if g.uniform() < 0.5 else 8
+        s = int(sizes[int(g.integers(0, len(sizes)))])
+        if g.uniform() < 0.5:
+            dims = [s, s, s]
+        else:
+            a = math.exp(g.uniform(0.0, math.log(max_aspect)))
+            hi = max(align, int(round(s * math.sqrt(a) / align)) * align)
+            lo = max(align, int(round(s / math.sqrt(a) / align)) * align)
+            dims = [hi, lo, s]
+            g.shuffle(dims)
+        out.append((int(dims[0]), int(dims[1]), int(dims[2]), eb))
+    return out
