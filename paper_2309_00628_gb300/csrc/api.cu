@@ -110,6 +110,7 @@ struct Op {
     // grouped GEMM
     MapSet maps;
     int bn = 256, nleaves = 0, items = 0, ntmaps = 0, nflags = 0;
+    bool pair = false;   // TF32: the CTA-pair form (256 x 256 tiles; items count 256-row tiles)
     size_t leaves_off = 0, targets_off = 0, refs_off = 0, tmaps_off = 0, flags_off = 0;
     unsigned epoch = 0;  // launches of this op so far (its ordering counters grow by 4 per launch)
     int ngmaps = 0, njobs = 0, tiles = 0, transpose = 0;
@@ -168,6 +169,24 @@ struct Planner {
     bool batch = false;
     bool server = false;  // plan for the serving loop (no ordering counters)
     int force_bn = 0;
+    // The CTA-pair TF32 GEMM (cta_group::2) serves single products with 256-wide tiles; batched
+    // and serving launches keep the one-CTA form.  SWMM_NO_PAIR=1 disables it (diagnostics).
+    bool pair_ok(int bn) const {
+        static const bool off = getenv("SWMM_NO_PAIR") != nullptr;
+        return !off && bn == 256 && !batch && !server && !bf && eb == 4;
+    }
+    // rows of one B-side TMA box: half the tile width for a CTA pair
+    int b_box(int bn) const { return pair_ok(bn) ? bn / 2 : bn; }
+    // Renumber a TF32 op's work items in 256-row tiles for the pair kernel.
+    void to_pair(Op& o, std::vector<Leaf>& leaves) const {
+        int items = 0;
+        for (Leaf& lf : leaves) {
+            lf.tile_begin = items;
+            items += (int)(ceil_div(lf.m, 2 * tf32_tile_m()) * lf.tiles_n);
+        }
+        o.items = items;
+        o.pair = true;
+    }
     std::vector<CUtensorMap> bmaps;
     std::vector<Leaf> bleaves;
     std::vector<Target> btargets;
@@ -425,13 +444,14 @@ struct Planner {
         lf.kblocks = (int)ceil_div(a.cols, tf32_tile_k());
         lf.tiles_n = (int)ceil_div(c.cols, o.bn);
         if (!make_map_f32(&o.maps.m[0], a.p, a.rows, a.cols, a.ld, 32, tf32_tile_m()) ||
-            !make_map_f32(&o.maps.m[1], b.p, b.rows, b.cols, b.ld, 32, o.bn)) {
+            !make_map_f32(&o.maps.m[1], b.p, b.rows, b.cols, b.ld, 32, b_box(o.bn))) {
             err = "tensor map encoding failed (alignment?)";
             return false;
         }
         o.items = (int)(ceil_div(c.rows, tf32_tile_m()) * lf.tiles_n);
         std::vector<Leaf> lv(1, lf);
         std::vector<Target> tv(1, t);
+        if (pair_ok(o.bn)) to_pair(o, lv);
         emit_grouped(o, lv, tv, 0);
         return true;
     }
@@ -850,6 +870,9 @@ struct Planner {
             int gm_ = 0, gn_ = 0;
             if (sscanf(g, "%dx%d", &gm_, &gn_) == 2 && gm_ > 0 && gn_ > 0 && eb == 4) { GM = gm_; GN = gn_; }
         }
+        // CTA pairs: a group must hold whole 256-row tiles, or a pair's second half would also
+        // compute rows of the next group
+        if (eb == 4 && pair_ok(bn) && (GM & 1)) ++GM;
         for (int gm = 0; gm < tiles_m; gm += GM)
             for (int gn = 0; gn < tiles_n; gn += GN)
                 for (const Leaf& b0 : base_leaves) {
@@ -893,12 +916,13 @@ struct Planner {
             o.kind = OP_GEMM_TF32;
             o.bn = bn;
             if (!make_map_f32(&o.maps.m[0], A.p, m, k, A.ld, 32, tf32_tile_m()) ||
-                !make_map_f32(&o.maps.m[1], B.p, n, k, B.ld, 32, bn) ||
+                !make_map_f32(&o.maps.m[1], B.p, n, k, B.ld, 32, b_box(bn)) ||
                 !make_map_f32(&o.maps.m[2], SA.p, std::max(SA.rows, 1), kb, SA.ld, 32, tf32_tile_m()) ||
-                !make_map_f32(&o.maps.m[3], SB.p, std::max(SB.rows, 1), kb, SB.ld, 32, bn)) {
+                !make_map_f32(&o.maps.m[3], SB.p, std::max(SB.rows, 1), kb, SB.ld, 32, b_box(bn))) {
                 err = "tensor map encoding failed";
                 return false;
             }
+            if (pair_ok(bn)) to_pair(o, leaves);
         } else {
             o.kind = OP_GEMM_SIMT;
             o.eb = 8;
@@ -1210,7 +1234,7 @@ static sw_status run_ops(sw_handle h, Plan* plan, cudaStream_t s, size_t first, 
                                      o.nleaves, reinterpret_cast<const Target*>(blob + o.targets_off),
                                      o.ntmaps ? reinterpret_cast<const CUtensorMap*>(blob + o.tmaps_off) : nullptr,
                                      o.nflags ? reinterpret_cast<unsigned*>(blob + o.flags_off) : nullptr,
-                                     o.nflags ? ++o.epoch : 0u, o.items, h->d_err, h->sms, s);
+                                     o.nflags ? ++o.epoch : 0u, o.items, h->d_err, h->sms, s, o.pair);
                 break;
             case OP_GEMM_SIMT:
                 e = launch_gemm_simt(o.eb, reinterpret_cast<const MatRef*>(blob + o.refs_off),

@@ -25,6 +25,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <algorithm>
 #include <cstring>
 
 #include "plan.h"
@@ -38,11 +39,16 @@ constexpr int TF_BK = 32;  // TF32 k-block: 32 FP32 = 128 bytes, one swizzle row
 constexpr int TF_GROUP_M = 8;
 constexpr int MODE_TF32 = 0, MODE_BF16X3 = 1;
 
-template <int MODE, int BN>
+// PAIR: the TF32 form for a CTA pair (cta_group::2): one 256 x BN tile per pair, each CTA holding
+// 128 rows of A and BN / 2 rows of B^T; the even CTA issues M = 256 MMAs that read both CTAs'
+// shared memory and write 128 accumulator rows into each CTA's tensor memory.
+template <int MODE, int BN, bool PAIR = false>
 struct TfCfg {
     static constexpr int BK = MODE == MODE_TF32 ? 32 : 64;           // elements per 128-byte row
+    static constexpr int TM = PAIR ? 2 * TF_BM : TF_BM;              // tile rows per work item
+    static constexpr int B_ROWS = PAIR ? BN / 2 : BN;                // B rows held by one CTA
     static constexpr int A_BYTES = TF_BM * 128;                      // one A tile (16 KB)
-    static constexpr int B_BYTES = BN * 128;                         // one B tile
+    static constexpr int B_BYTES = B_ROWS * 128;                     // one B tile
     static constexpr int NOPS = MODE == MODE_TF32 ? 1 : 2;           // tiles per operand (hi, lo)
     static constexpr int STAGE_BYTES = NOPS * (A_BYTES + B_BYTES);
     static constexpr int STAGES = (4 * 49152) / STAGE_BYTES;         // 192 KB of operand stages
@@ -55,7 +61,7 @@ struct TfCfg {
     // B MN-major; N = BN, M = 128
     static constexpr uint32_t IDESC =
         MODE == MODE_TF32
-            ? ((1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(TF_BM >> 4) << 24))
+            ? ((1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24))
             : ((1u << 4) | (1u << 7) | (1u << 10) | (1u << 16) | ((uint32_t)(BN >> 3) << 17) |
                ((uint32_t)(TF_BM >> 4) << 24));
 };
@@ -64,26 +70,29 @@ struct ItemPos {
     int leaf, tm, tn;
 };
 
-__device__ __forceinline__ ItemPos decode_item(const Leaf* __restrict__ leaves, int nleaves, int item, int bn) {
+// Work item -> (leaf, tile row, tile column); tiles are TM rows high, taken in groups of
+// 1024 / TM tile rows (column-major inside a group) for L2 reuse of the B tiles.
+template <int TM>
+__device__ __forceinline__ ItemPos decode_item(const Leaf* __restrict__ leaves, int nleaves, int item) {
     int lo = 0, hi = nleaves - 1;
     while (lo < hi) {
         int mid = (lo + hi + 1) >> 1;
         if (__ldg(&leaves[mid].tile_begin) <= item) lo = mid; else hi = mid - 1;
     }
+    constexpr int GROUP = TF_GROUP_M * TF_BM / TM;
     const Leaf* L = &leaves[lo];
     int local = item - __ldg(&L->tile_begin);
-    int tiles_m = (__ldg(&L->m) + TF_BM - 1) / TF_BM;
+    int tiles_m = (__ldg(&L->m) + TM - 1) / TM;
     int tiles_n = __ldg(&L->tiles_n);
-    int per_group = TF_GROUP_M * tiles_n;
+    int per_group = GROUP * tiles_n;
     int g = local / per_group;
-    int first_m = g * TF_GROUP_M;
-    int gsz = min(tiles_m - first_m, TF_GROUP_M);
+    int first_m = g * GROUP;
+    int gsz = min(tiles_m - first_m, GROUP);
     int r = local - g * per_group;
     ItemPos p;
     p.leaf = lo;
     p.tm = first_m + r % gsz;
     p.tn = r / gsz;
-    (void)bn;
     return p;
 }
 
@@ -176,13 +185,14 @@ __device__ __forceinline__ void store_row32(const Target& t, int row, int col0, 
     }
 }
 
-template <int MODE, int BN, bool RES>
+template <int MODE, int BN, bool RES, bool PAIR>
 __global__ void __launch_bounds__(192, 1)
     gemm_tc_kernel(const __grid_constant__ MapSet maps, const CUtensorMap* __restrict__ gmaps,
                      const Leaf* __restrict__ leaves, int nleaves, const Target* __restrict__ targets,
                      const CUtensorMap* __restrict__ tmaps, unsigned* __restrict__ flags, unsigned epoch,
                      int total_items, int* err, const ResidentCtl ctl) {
-    using Cfg = TfCfg<MODE, BN>;
+    static_assert(!PAIR || (MODE == MODE_TF32 && !RES), "CTA pairs: TF32, non-resident only");
+    using Cfg = TfCfg<MODE, BN, PAIR>;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw_addr = smem_u32(smem_raw);
     const uint32_t base_addr = (raw_addr + 1023u) & ~1023u;
@@ -205,6 +215,12 @@ __global__ void __launch_bounds__(192, 1)
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
+    // CTA pairs: work unit = cluster; rank 0 (the leader) issues the MMAs and owns the
+    // operand-full and accumulator-free barriers, rank 1 holds the other half of each tile.
+    const uint32_t rank = PAIR ? cluster_ctarank() : 0u;
+    const bool leader = rank == 0u;
+    const int unit = PAIR ? (int)cluster_id_x() : (int)blockIdx.x;
+    const int nunits = PAIR ? (int)nclusters_x() : (int)gridDim.x;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < Cfg::STAGES; ++s) {
@@ -213,7 +229,7 @@ __global__ void __launch_bounds__(192, 1)
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(&tfull[a], 1);
-            mbar_init(&tempty[a], 4);
+            mbar_init(&tempty[a], PAIR ? 8 : 4);  // epilogue warps (of both CTAs of a pair)
         }
         mbar_init(done, 1);
         for (int r = 0; r < 4; ++r) {
@@ -223,11 +239,17 @@ __global__ void __launch_bounds__(192, 1)
         fence_mbar_init();
     }
     if (warp == 1) {
-        tmem_alloc(tmem_holder, Cfg::TMEM_COLS);
-        tmem_relinquish();
+        if (PAIR) {
+            tmem_alloc_pair(tmem_holder, Cfg::TMEM_COLS);
+            tmem_relinquish_pair();
+        } else {
+            tmem_alloc(tmem_holder, Cfg::TMEM_COLS);
+            tmem_relinquish();
+        }
     }
     tc_fence_before();
-    __syncthreads();
+    if (PAIR) cluster_sync_all();  // the peer's barriers are initialised before any remote arrive
+    else __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *reinterpret_cast<volatile uint32_t*>(tmem_holder);
 
@@ -241,7 +263,7 @@ __global__ void __launch_bounds__(192, 1)
             int rslot = 0;
             uint32_t rph = 0;
             unsigned pub = 0;
-            for (int item = RES ? -1 : (int)blockIdx.x;; item += RES ? 0 : gridDim.x) {
+            for (int item = RES ? -1 : unit;; item += RES ? 0 : nunits) {
                 if (RES) {  // claim a published item and hand it to the consumers
                     item = res_claim(ctl, pub, err);
                     if (!mbar_wait(&ring_empty[rslot], rph ^ 1u, err, ERR_WAIT_EMPTY)) break;
@@ -253,13 +275,13 @@ __global__ void __launch_bounds__(192, 1)
                     break;
                 }
                 const ItemPos ip = RES ? decode_in_leaf(leaves, __ldcg(&ctl.item_leaf[item]), item)
-                                       : decode_item(leaves, nleaves, item, BN);
+                                       : decode_item<Cfg::TM>(leaves, nleaves, item);
                 const Leaf* L = &leaves[ip.leaf];
                 const int am = __ldg(&L->a_map), bm = __ldg(&L->b_map);
-                const int a_row = __ldg(&L->a_row) + ip.tm * TF_BM;
+                const int a_row = __ldg(&L->a_row) + ip.tm * Cfg::TM + (int)rank * TF_BM;
                 const int a_col = __ldg(&L->a_col);
                 // TF32: B^T, rows are N, columns K.  BF16X3: B as stored, rows K, columns N.
-                const int b_row = __ldg(&L->b_row) + (MODE == MODE_TF32 ? ip.tn * BN : 0);
+                const int b_row = __ldg(&L->b_row) + (MODE == MODE_TF32 ? ip.tn * BN + (int)rank * Cfg::B_ROWS : 0);
                 const int b_col = __ldg(&L->b_col) + (MODE == MODE_TF32 ? 0 : ip.tn * BN);
                 const int kb_n = __ldg(&L->kblocks);
                 // TMA x coordinates must be 16-byte aligned (4 FP32 / 8 BF16 elements)
@@ -277,6 +299,18 @@ __global__ void __launch_bounds__(192, 1)
                 }
                 for (int kb = 0; kb < kb_n; ++kb) {
                     if (!mbar_wait(&empty[stage], phase ^ 1u, err, ERR_WAIT_EMPTY)) { ok = false; break; }
+                    if (PAIR) {
+                        // both halves land on the leader's full barrier
+                        if (leader) mbar_arrive_expect_tx(&full[stage], 2 * Cfg::STAGE_BYTES);
+                        const uint32_t fb = mapa_shared(smem_u32(&full[stage]), 0u);
+                        tma_load_2d_pair(stage_a(stage, 0), pick_map(maps, gmaps, am), fb, a_col + kb * Cfg::BK,
+                                         a_row);
+                        tma_load_2d_pair(stage_b(stage, 0), pick_map(maps, gmaps, bm), fb, b_col + kb * Cfg::BK,
+                                         b_row);
+                        ++issued;
+                        if (++stage == Cfg::STAGES) { stage = 0; phase ^= 1u; }
+                        continue;
+                    }
                     mbar_arrive_expect_tx(&full[stage], Cfg::STAGE_BYTES);
 #pragma unroll
                     for (int op = 0; op < Cfg::NOPS; ++op) {
@@ -297,24 +331,25 @@ __global__ void __launch_bounds__(192, 1)
                 }
                 if (!ok) break;
             }
-            // drain: every issued copy must have landed before the CTA may exit
+            // drain: every issued copy must have landed before the CTA may exit (a pair: the
+            // leader's MMAs have consumed it, which the stage's empty barrier reports in both CTAs)
             int s = stage;
             uint32_t ph = phase;
             for (int i = 0; i < min(issued, Cfg::STAGES); ++i) {
                 if (--s < 0) { s = Cfg::STAGES - 1; ph ^= 1u; }
-                mbar_wait(&full[s], ph, err, ERR_WAIT_DRAIN);
+                mbar_wait(PAIR ? &empty[s] : &full[s], ph, err, ERR_WAIT_DRAIN);
             }
         }
     } else if (warp == 1) {
         // ------------------------------------------------------------ MMA issuer
-        if (lane == 0) {
+        if (lane == 0 && leader) {
             int stage = 0;
             uint32_t phase = 0;
             int local = 0;
             bool ok = true;
             int rslot = 0;
             uint32_t rph = 0;
-            for (int item = RES ? -1 : (int)blockIdx.x;; item += RES ? 0 : gridDim.x, ++local) {
+            for (int item = RES ? -1 : unit;; item += RES ? 0 : nunits, ++local) {
                 if (RES) {
                     if (!mbar_wait(&ring_full[rslot], rph, err, ERR_WAIT_FULL)) break;
                     item = ring[rslot];
@@ -325,7 +360,7 @@ __global__ void __launch_bounds__(192, 1)
                     break;
                 }
                 const ItemPos ip = RES ? decode_in_leaf(leaves, __ldcg(&ctl.item_leaf[item]), item)
-                                       : decode_item(leaves, nleaves, item, BN);
+                                       : decode_item<Cfg::TM>(leaves, nleaves, item);
                 const int kb_n = __ldg(&leaves[ip.leaf].kblocks);
                 const int acc = local & 1;
                 const uint32_t acc_phase = (local >> 1) & 1;
@@ -342,7 +377,8 @@ __global__ void __launch_bounds__(192, 1)
                         for (int kk = 0; kk < TF_BK / 8; ++kk) {  // K = 8 per MMA, 32 bytes
                             const uint64_t ad = make_sdesc(a_addr + kk * 32, 16, 1024, SWZ_128B);
                             const uint64_t bd = make_sdesc(b_addr + kk * 32, 16, 1024, SWZ_128B);
-                            mma_tf32(d_tmem, ad, bd, Cfg::IDESC, (kb | kk) != 0 ? 1u : 0u);
+                            if (PAIR) mma_tf32_pair(d_tmem, ad, bd, Cfg::IDESC, (kb | kk) != 0 ? 1u : 0u);
+                            else mma_tf32(d_tmem, ad, bd, Cfg::IDESC, (kb | kk) != 0 ? 1u : 0u);
                         }
                     } else {
                         const uint32_t ah = smem_u32(stage_a(stage, 0)), al = smem_u32(stage_a(stage, 1));
@@ -360,15 +396,24 @@ __global__ void __launch_bounds__(192, 1)
                             mma_f16(d_tmem, dah, dbh, Cfg::IDESC, 1u);                           // hi * hi
                         }
                     }
-                    mma_commit(&empty[stage]);  // stage is free once these MMAs have read it
+                    // stage is free once these MMAs have read it (in both CTAs of a pair)
+                    if (PAIR) mma_commit_pair(&empty[stage], 3);
+                    else mma_commit(&empty[stage]);
                     if (++stage == Cfg::STAGES) { stage = 0; phase ^= 1u; }
                 }
                 if (!ok) break;
-                mma_commit(&tfull[acc]);  // accumulator ready for the epilogue
+                // accumulator ready for the epilogue
+                if (PAIR) mma_commit_pair(&tfull[acc], 3);
+                else mma_commit(&tfull[acc]);
             }
-            // drain: all MMAs issued by this thread must finish before TMEM is released
-            mma_commit(done);
-            mbar_wait(done, 0, err, ERR_WAIT_DRAIN);
+            // drain: all MMAs issued by this thread must finish before TMEM is released (a pair
+            // waits for this in both CTAs at the end)
+            if (PAIR) {
+                mma_commit_pair(done, 3);
+            } else {
+                mma_commit(done);
+                mbar_wait(done, 0, err, ERR_WAIT_DRAIN);
+            }
         }
     } else {
         // ------------------------------------------------------------ epilogue (warps 2..5)
@@ -378,7 +423,7 @@ __global__ void __launch_bounds__(192, 1)
         bool issued_bulk = false;
         int rslot = 0;
         uint32_t rph = 0;
-        for (int item = RES ? -1 : (int)blockIdx.x;; item += RES ? 0 : gridDim.x, ++local) {
+        for (int item = RES ? -1 : unit;; item += RES ? 0 : nunits, ++local) {
             if (RES) {
                 int it = -1;
                 if (lane == 0) {
@@ -392,7 +437,7 @@ __global__ void __launch_bounds__(192, 1)
                 break;
             }
             const ItemPos ip = RES ? decode_in_leaf(leaves, __ldcg(&ctl.item_leaf[item]), item)
-                                   : decode_item(leaves, nleaves, item, BN);
+                                   : decode_item<Cfg::TM>(leaves, nleaves, item);
             const Leaf* L = &leaves[ip.leaf];
             const int acc = local & 1;
             const uint32_t acc_phase = (local >> 1) & 1;
@@ -406,7 +451,8 @@ __global__ void __launch_bounds__(192, 1)
                 has_neg |= sg < 0.f;
                 all_tma &= __ldg(&targets[tb + t].map) >= 0;
             }
-            const int row_t = __ldg(&L->c_row0) + ip.tm * TF_BM;   // the tile's first row in its blocks
+            // this CTA's first row of the tile in its blocks (a pair: rank 1 holds rows 128..255)
+            const int row_t = __ldg(&L->c_row0) + ip.tm * Cfg::TM + (int)rank * TF_BM;
             const int col_t = __ldg(&L->c_col0) + ip.tn * BN;      // the tile's first column
             const int row_w = row_t + q * 32;                        // this warp's first row
             const uint32_t t_base = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN);
@@ -484,7 +530,10 @@ __global__ void __launch_bounds__(192, 1)
             }
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&tempty[acc]);
+            if (lane == 0) {
+                if (PAIR) mbar_arrive_cluster(mapa_shared(smem_u32(&tempty[acc]), 0u));
+                else mbar_arrive(&tempty[acc]);
+            }
             // first writes done: publish them tile by tile (one count per epilogue warp)
             if (flags && has_first) {
                 if (lane == 0 && issued_bulk) bulk_wait<0>();  // this warp's TMA stores are complete
@@ -522,24 +571,53 @@ __global__ void __launch_bounds__(192, 1)
 
     tc_fence_before();
     __syncthreads();
+    if (PAIR) {
+        // no MMA of the pair may still read this CTA's shared memory or write its tensor memory,
+        // and neither CTA leaves while the other may still arrive on its barriers
+        if (warp == 1 && lane == 0) mbar_wait(done, 0, err, ERR_WAIT_DRAIN);
+        __syncwarp();
+        tc_fence_before();
+        cluster_sync_all();
+        tc_fence_after();
+        if (warp == 1) tmem_dealloc_pair(tmem_base, Cfg::TMEM_COLS);
+        return;
+    }
     if (warp == 1) {
         tc_fence_after();
         tmem_dealloc(tmem_base, Cfg::TMEM_COLS);
     }
 }
 
-template <int MODE, int BN, bool RES = false>
+template <int MODE, int BN, bool RES = false, bool PAIR = false>
 static cudaError_t launch_tc_impl(const MapSet& maps, const CUtensorMap* gmaps, const Leaf* leaves, int nleaves,
                                   const Target* targets, const CUtensorMap* tmaps, unsigned* flags, unsigned epoch,
                                   int total_items, int* err, int grid, cudaStream_t stream,
                                   const ResidentCtl* ctl = nullptr) {
-    using Cfg = TfCfg<MODE, BN>;
+    using Cfg = TfCfg<MODE, BN, PAIR>;
     static_assert(Cfg::SMEM_BYTES <= 232448, "shared memory budget");
+    auto kern = gemm_tc_kernel<MODE, BN, RES, PAIR>;
     static bool attr_set = false;
+    static int max_pairs = 0;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<MODE, BN, RES>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM_BYTES);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM_BYTES);
         if (e != cudaSuccess) return e;
+        if (PAIR) {
+            // clusters of two that fit at once (one CTA per SM)
+            cudaLaunchConfig_t q = {};
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = 2;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            q.gridDim = dim3(2 * 1024, 1, 1);
+            q.blockDim = dim3(192, 1, 1);
+            q.dynamicSmemBytes = Cfg::SMEM_BYTES;
+            q.attrs = at;
+            q.numAttrs = 1;
+            e = cudaOccupancyMaxActiveClusters(&max_pairs, (void*)kern, &q);
+            if (e != cudaSuccess) return e;
+            if (max_pairs <= 0) return cudaErrorLaunchOutOfResources;
+        }
         attr_set = true;
     }
     ResidentCtl c;
@@ -549,10 +627,30 @@ static cudaError_t launch_tc_impl(const MapSet& maps, const CUtensorMap* gmaps, 
         c = *ctl;
     } else {
         if (total_items <= 0) return cudaSuccess;
+        if (PAIR) grid = std::min(grid / 2, max_pairs);
         if (grid > total_items) grid = total_items;
+        if (grid < 1) grid = 1;
     }
-    gemm_tc_kernel<MODE, BN, RES><<<grid, 192, Cfg::SMEM_BYTES, stream>>>(maps, gmaps, leaves, nleaves, targets,
-                                                                           tmaps, flags, epoch, total_items, err, c);
+    if (PAIR) {
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 2;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(2 * grid, 1, 1);
+        cfg.blockDim = dim3(192, 1, 1);
+        cfg.dynamicSmemBytes = Cfg::SMEM_BYTES;
+        cfg.stream = stream;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        cudaError_t e = cudaLaunchKernelEx(&cfg, kern, maps, gmaps, leaves, nleaves, targets, tmaps, flags, epoch,
+                                           total_items, err, c);
+        if (e != cudaSuccess) return e;
+        return cudaGetLastError();
+    }
+    kern<<<grid, 192, Cfg::SMEM_BYTES, stream>>>(maps, gmaps, leaves, nleaves, targets, tmaps, flags, epoch,
+                                                 total_items, err, c);
     return cudaGetLastError();
 }
 
@@ -567,7 +665,10 @@ cudaError_t launch_gemm_tf32_resident(const CUtensorMap* gmaps, const Leaf* leav
 
 cudaError_t launch_gemm_tf32(int bn, const MapSet& maps, const CUtensorMap* gmaps, const Leaf* leaves, int nleaves,
                              const Target* targets, const CUtensorMap* tmaps, unsigned* flags, unsigned epoch,
-                             int total_items, int* err, int grid, cudaStream_t stream) {
+                             int total_items, int* err, int grid, cudaStream_t stream, bool pair) {
+    if (pair)
+        return launch_tc_impl<MODE_TF32, 256, false, true>(maps, gmaps, leaves, nleaves, targets, tmaps, flags, epoch,
+                                                           total_items, err, grid, stream);
     if (bn == 256)
         return launch_tc_impl<MODE_TF32, 256>(maps, gmaps, leaves, nleaves, targets, tmaps, flags, epoch, total_items,
                                               err, grid, stream);

@@ -25,9 +25,12 @@ struct MatRef {
 // tmaps: tensor maps of the target blocks (Target::map indexes it), or nullptr for the
 // per-thread epilogue only.  flags / epoch: the ordering counters of the targets (Target::flag_base)
 // and this launch's epoch (1, 2, ... per counter array), or nullptr.
+// pair: the CTA-pair form (cta_group::2, 256 x 256 tiles, bn must be 256): work items count
+// 256-row tiles (Leaf::tile_begin in those units), B maps have 128-row boxes, `grid` is the number
+// of SMs to use (rounded down to whole pairs).
 cudaError_t launch_gemm_tf32(int bn, const MapSet& maps, const CUtensorMap* gmaps, const Leaf* leaves, int nleaves,
                              const Target* targets, const CUtensorMap* tmaps, unsigned* flags, unsigned epoch,
-                             int total_items, int* err, int grid, cudaStream_t stream);
+                             int total_items, int* err, int grid, cudaStream_t stream, bool pair = false);
 // Resident (serving) form of the TF32 grouped GEMM, BN = 256: runs until ctl.stop, an error, or
 // ctl.idle_ns without newly published items.
 cudaError_t launch_gemm_tf32_resident(const CUtensorMap* gmaps, const Leaf* leaves, const Target* targets,
