@@ -215,9 +215,9 @@ sw_status sw_error_norms(sw_handle h, int elem_bytes, int m, int n, int k, const
  * kernel kind, the number of launches and the summed device time in milliseconds since the last
  * read (then resets).  Kinds: 0 tensor-core leaf GEMM (TF32), 1 SIMT leaf GEMM, 2 block addition,
  * 3 padded copy, 4 operand-sum pass, 5 memset, 6 transpose, 7 in-place transpose, 8 bf16 split,
- * 9 tensor-core leaf GEMM (split BF16).
- * `nkinds` is the length of both output arrays (entries beyond 10 are set to 0). */
-#define SW_PROFILE_KINDS 10
+ * 9 tensor-core leaf GEMM (split BF16), 10 batched copy / transpose (sw_mm_batched staging).
+ * `nkinds` is the length of both output arrays (entries beyond 11 are set to 0). */
+#define SW_PROFILE_KINDS 11
 sw_status sw_profile(sw_handle h, int enable);
 sw_status sw_profile_read(sw_handle h, int nkinds, int *launches, double *ms);
 

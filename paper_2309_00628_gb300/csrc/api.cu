@@ -111,6 +111,8 @@ struct Op {
     MapSet maps;
     int bn = 256, nleaves = 0, items = 0, ntmaps = 0, nflags = 0;
     bool pair = false;   // TF32: the CTA-pair form (256 x 256 tiles; items count 256-row tiles)
+    bool has_item_leaf = false;  // tensor-core GEMM: item -> leaf table at item_leaf_off
+    size_t item_leaf_off = 0;
     size_t leaves_off = 0, targets_off = 0, refs_off = 0, tmaps_off = 0, flags_off = 0;
     unsigned epoch = 0;  // launches of this op so far (its ordering counters grow by 4 per launch)
     int ngmaps = 0, njobs = 0, tiles = 0, transpose = 0;
@@ -404,6 +406,18 @@ struct Planner {
         o.nleaves = (int)leaves.size();
         o.leaves_off = put_blob(leaves.data(), leaves.size() * sizeof(Leaf));
         o.targets_off = put_blob(tg.data(), tg.size() * sizeof(Target));
+        // many leaves: a table of every item's leaf replaces the kernel's per-tile binary search
+        if ((o.kind == OP_GEMM_TF32 || o.kind == OP_GEMM_BF16X3) && leaves.size() > 4 && o.items > 0) {
+            const long long tm = o.pair ? 2 * tf32_tile_m() : tf32_tile_m();
+            std::vector<int> il(o.items, 0);
+            for (size_t i = 0; i < leaves.size(); ++i) {
+                const Leaf& lf = leaves[i];
+                const long long cnt = ceil_div(lf.m, tm) * lf.tiles_n;
+                for (long long t = 0; t < cnt && lf.tile_begin + t < o.items; ++t) il[lf.tile_begin + t] = (int)i;
+            }
+            o.has_item_leaf = true;
+            o.item_leaf_off = put_blob(il.data(), il.size() * sizeof(int));
+        }
         flush_tmaps(o);
         if (nflags > 0) {
             std::vector<unsigned> zeros(nflags, 0u);
@@ -955,7 +969,7 @@ struct Planner {
             j.src_rows = src.rows; j.src_cols = src.cols; j.out_rows = dst.rows; j.out_cols = dst.cols;
             j.tile_begin = tiles;
             j.pad_ = 0;
-            tiles += (int)(ceil_div(dst.rows, 32) * ceil_div(dst.cols, 32));
+            tiles += (int)(ceil_div(dst.rows, BCOPY_TILE) * ceil_div(dst.cols, BCOPY_TILE));
             return j;
         };
         for (int i : order) {
@@ -1234,7 +1248,8 @@ static sw_status run_ops(sw_handle h, Plan* plan, cudaStream_t s, size_t first, 
                                      o.nleaves, reinterpret_cast<const Target*>(blob + o.targets_off),
                                      o.ntmaps ? reinterpret_cast<const CUtensorMap*>(blob + o.tmaps_off) : nullptr,
                                      o.nflags ? reinterpret_cast<unsigned*>(blob + o.flags_off) : nullptr,
-                                     o.nflags ? ++o.epoch : 0u, o.items, h->d_err, h->sms, s, o.pair);
+                                     o.nflags ? ++o.epoch : 0u, o.items, h->d_err, h->sms, s, o.pair,
+                                     o.has_item_leaf ? reinterpret_cast<const int*>(blob + o.item_leaf_off) : nullptr);
                 break;
             case OP_GEMM_SIMT:
                 e = launch_gemm_simt(o.eb, reinterpret_cast<const MatRef*>(blob + o.refs_off),
@@ -1261,7 +1276,9 @@ static sw_status run_ops(sw_handle h, Plan* plan, cudaStream_t s, size_t first, 
                                        o.nleaves, reinterpret_cast<const Target*>(blob + o.targets_off),
                                        o.ntmaps ? reinterpret_cast<const CUtensorMap*>(blob + o.tmaps_off) : nullptr,
                                        o.nflags ? reinterpret_cast<unsigned*>(blob + o.flags_off) : nullptr,
-                                       o.nflags ? ++o.epoch : 0u, o.items, h->d_err, h->sms, s);
+                                       o.nflags ? ++o.epoch : 0u, o.items, h->d_err, h->sms, s,
+                                       o.has_item_leaf ? reinterpret_cast<const int*>(blob + o.item_leaf_off)
+                                                       : nullptr);
                 break;
             case OP_ADDSUB:
                 e = launch_addsub(o.eb, o.rows, o.cols, o.z, o.ldz, o.x, o.ldx, o.y, o.ldy, o.sy, s);

@@ -20,7 +20,8 @@
 //   warps 2..5  epilogue: tcgen05.ld 32 columns at a time; each warp stages its 32 x 32 chunk
 //               (with the target's sign) in 128-byte-swizzled shared memory and one lane issues a
 //               TMA store (first writer) or TMA reduce-add (further contributions) per target;
-//               targets without a tensor map fall back to per-thread stores / atomics.
+//               targets without a tensor map take coalesced row stores / atomics from the same
+//               staging (one 128-byte row run per warp step).
 // Two TMEM accumulators (2 x BN columns) let the epilogue of tile i overlap the MMAs of i+1.
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -96,16 +97,19 @@ __device__ __forceinline__ ItemPos decode_item(const Leaf* __restrict__ leaves, 
     return p;
 }
 
-// Tile position of an item whose leaf is known (resident mode: leaf index from item_leaf).
+// Tile position of an item whose leaf is known (from an item -> leaf table: the resident mode's,
+// or the one the planner writes for launches with many leaves); same order as decode_item.
+template <int TM>
 __device__ __forceinline__ ItemPos decode_in_leaf(const Leaf* __restrict__ leaves, int leaf, int item) {
+    constexpr int GROUP = TF_GROUP_M * TF_BM / TM;
     const Leaf* L = &leaves[leaf];
     int local = item - __ldg(&L->tile_begin);
-    int tiles_m = (__ldg(&L->m) + TF_BM - 1) / TF_BM;
+    int tiles_m = (__ldg(&L->m) + TM - 1) / TM;
     int tiles_n = __ldg(&L->tiles_n);
-    int per_group = TF_GROUP_M * tiles_n;
+    int per_group = GROUP * tiles_n;
     int g = local / per_group;
-    int first_m = g * TF_GROUP_M;
-    int gsz = min(tiles_m - first_m, TF_GROUP_M);
+    int first_m = g * GROUP;
+    int gsz = min(tiles_m - first_m, GROUP);
     int r = local - g * per_group;
     ItemPos p;
     p.leaf = leaf;
@@ -150,38 +154,21 @@ __device__ __forceinline__ const CUtensorMap* pick_map(const MapSet& maps, const
     return gmaps ? gmaps + idx : &maps.m[idx];
 }
 
-// Epilogue store of 32 consecutive columns of one row into one target.
-__device__ __forceinline__ void store_row32(const Target& t, int row, int col0, const uint32_t (&r)[32]) {
-    if (row >= t.rows || col0 >= t.cols) return;
-    float* c = reinterpret_cast<float*>(t.c) + (long long)row * t.ldc + col0;
+// Epilogue store of one 32 x 32 chunk (rows row_w.., columns col0..) into one target without a
+// tensor map: the chunk sits row-major in shared memory (row stride 33 floats) and the warp writes
+// it one row per step, lane j on column col0 + j, so every step is one contiguous 128-byte run.
+__device__ __forceinline__ void store_chunk32(const Target& t, int row_w, int col0, const float* sf, int lane) {
+    const int c = col0 + lane;
+    if (c >= t.cols) return;
+    const int nrow = min(32, t.rows - row_w);
+    float* base = reinterpret_cast<float*>(t.c) + (long long)row_w * t.ldc + c;
     const float s = t.sign;
-    const int ncol = min(32, t.cols - col0);
-    if (t.vec_ok && ncol == 32) {
-        float4* c4 = reinterpret_cast<float4*>(c);
-#pragma unroll
-        for (int g = 0; g < 8; ++g) {
-            float4 v = make_float4(s * __uint_as_float(r[4 * g + 0]), s * __uint_as_float(r[4 * g + 1]),
-                                   s * __uint_as_float(r[4 * g + 2]), s * __uint_as_float(r[4 * g + 3]));
-            if (t.mode == TGT_STORE) {
-                c4[g] = v;
-            } else if (t.mode == TGT_ATOMIC) {
-                atomicAdd(&c4[g], v);
-            } else {
-                float4 o = c4[g];
-                o.x += v.x; o.y += v.y; o.z += v.z; o.w += v.w;
-                c4[g] = o;
-            }
-        }
-    } else {
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-            if (j < ncol) {
-                float v = s * __uint_as_float(r[j]);
-                if (t.mode == TGT_STORE) c[j] = v;
-                else if (t.mode == TGT_ATOMIC) atomicAdd(&c[j], v);
-                else c[j] += v;
-            }
-        }
+    for (int i = 0; i < nrow; ++i) {
+        const float v = s * sf[i * 33 + lane];
+        float* q = base + (long long)i * t.ldc;
+        if (t.mode == TGT_STORE) *q = v;
+        else if (t.mode == TGT_ATOMIC) atomicAdd(q, v);
+        else *q += v;
     }
 }
 
@@ -274,8 +261,9 @@ __global__ void __launch_bounds__(192, 1)
                 } else if (item >= total_items || !ok) {
                     break;
                 }
-                const ItemPos ip = RES ? decode_in_leaf(leaves, __ldcg(&ctl.item_leaf[item]), item)
-                                       : decode_item<Cfg::TM>(leaves, nleaves, item);
+                const ItemPos ip = RES ? decode_in_leaf<Cfg::TM>(leaves, __ldcg(&ctl.item_leaf[item]), item)
+                                   : ctl.item_leaf ? decode_in_leaf<Cfg::TM>(leaves, __ldg(&ctl.item_leaf[item]), item)
+                                                   : decode_item<Cfg::TM>(leaves, nleaves, item);
                 const Leaf* L = &leaves[ip.leaf];
                 const int am = __ldg(&L->a_map), bm = __ldg(&L->b_map);
                 const int a_row = __ldg(&L->a_row) + ip.tm * Cfg::TM + (int)rank * TF_BM;
@@ -359,8 +347,9 @@ __global__ void __launch_bounds__(192, 1)
                 } else if (item >= total_items || !ok) {
                     break;
                 }
-                const ItemPos ip = RES ? decode_in_leaf(leaves, __ldcg(&ctl.item_leaf[item]), item)
-                                       : decode_item<Cfg::TM>(leaves, nleaves, item);
+                const ItemPos ip = RES ? decode_in_leaf<Cfg::TM>(leaves, __ldcg(&ctl.item_leaf[item]), item)
+                                   : ctl.item_leaf ? decode_in_leaf<Cfg::TM>(leaves, __ldg(&ctl.item_leaf[item]), item)
+                                                   : decode_item<Cfg::TM>(leaves, nleaves, item);
                 const int kb_n = __ldg(&leaves[ip.leaf].kblocks);
                 const int acc = local & 1;
                 const uint32_t acc_phase = (local >> 1) & 1;
@@ -436,8 +425,9 @@ __global__ void __launch_bounds__(192, 1)
             } else if (item >= total_items) {
                 break;
             }
-            const ItemPos ip = RES ? decode_in_leaf(leaves, __ldcg(&ctl.item_leaf[item]), item)
-                                   : decode_item<Cfg::TM>(leaves, nleaves, item);
+            const ItemPos ip = RES ? decode_in_leaf<Cfg::TM>(leaves, __ldcg(&ctl.item_leaf[item]), item)
+                               : ctl.item_leaf ? decode_in_leaf<Cfg::TM>(leaves, __ldg(&ctl.item_leaf[item]), item)
+                                               : decode_item<Cfg::TM>(leaves, nleaves, item);
             const Leaf* L = &leaves[ip.leaf];
             const int acc = local & 1;
             const uint32_t acc_phase = (local >> 1) & 1;
@@ -473,13 +463,10 @@ __global__ void __launch_bounds__(192, 1)
                 if (lane == 0) fence_async_global();
                 ordered_ok = __shfl_sync(0xffffffffu, ordered_ok ? 1 : 0, 0) != 0;
             }
-#pragma unroll 1
-            for (int chunk = 0; chunk < BN / 32; ++chunk) {
-                uint32_t r[32];
-                tmem_ld32(t_base + chunk * 32, r);
-                tmem_ld_wait();
+            // one 32-column chunk: staged and stored into every target
+            auto emit_chunk = [&](int chunk, const uint32_t (&r)[32]) {
                 const int col0 = col_t + chunk * 32;
-                if (!ordered_ok) continue;  // an expired wait: the device error word reports it
+                if (!ordered_ok) return;  // an expired wait: the device error word reports it
                 if (all_tma) {
                     const bool mixed = has_pos && has_neg;
                     uint8_t* bpos;
@@ -522,11 +509,32 @@ __global__ void __launch_bounds__(192, 1)
                     __syncwarp();
                     ++chunk_ctr;
                 } else {
+                    // no tensor map: stage the chunk row-major (lane = row), then coalesced rows
+                    if (lane == 0 && issued_bulk) bulk_wait_read<0>();
+                    __syncwarp();
+                    float* sf = reinterpret_cast<float*>(stg);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) sf[lane * 33 + j] = __uint_as_float(r[j]);
+                    __syncwarp();
                     for (int t = 0; t < tc; ++t) {
-                        Target tg = targets[tb + t];
-                        store_row32(tg, row_w + lane, col0, r);
+                        const Target tg = targets[tb + t];
+                        if (row_w < tg.rows && col0 < tg.cols) store_chunk32(tg, row_w, col0, sf, lane);
                     }
+                    __syncwarp();
                 }
+            };
+            // TMEM loads double-buffered: chunk c + 1 is in flight while chunk c is stored
+            constexpr int NCH = BN / 32;  // even
+            uint32_t ra[32], rb[32];
+            tmem_ld32(t_base, ra);
+#pragma unroll 1
+            for (int chunk = 0; chunk < NCH; chunk += 2) {
+                tmem_ld_wait();
+                tmem_ld32(t_base + (chunk + 1) * 32, rb);
+                emit_chunk(chunk, ra);
+                tmem_ld_wait();
+                if (chunk + 2 < NCH) tmem_ld32(t_base + (chunk + 2) * 32, ra);
+                emit_chunk(chunk + 1, rb);
             }
             tc_fence_before();
             __syncwarp();
@@ -592,7 +600,7 @@ template <int MODE, int BN, bool RES = false, bool PAIR = false>
 static cudaError_t launch_tc_impl(const MapSet& maps, const CUtensorMap* gmaps, const Leaf* leaves, int nleaves,
                                   const Target* targets, const CUtensorMap* tmaps, unsigned* flags, unsigned epoch,
                                   int total_items, int* err, int grid, cudaStream_t stream,
-                                  const ResidentCtl* ctl = nullptr) {
+                                  const ResidentCtl* ctl = nullptr, const int* item_leaf = nullptr) {
     using Cfg = TfCfg<MODE, BN, PAIR>;
     static_assert(Cfg::SMEM_BYTES <= 232448, "shared memory budget");
     auto kern = gemm_tc_kernel<MODE, BN, RES, PAIR>;
@@ -627,6 +635,7 @@ static cudaError_t launch_tc_impl(const MapSet& maps, const CUtensorMap* gmaps, 
         c = *ctl;
     } else {
         if (total_items <= 0) return cudaSuccess;
+        c.item_leaf = item_leaf;  // optional item -> leaf table (nullptr: binary search)
         if (PAIR) grid = std::min(grid / 2, max_pairs);
         if (grid > total_items) grid = total_items;
         if (grid < 1) grid = 1;
@@ -665,25 +674,26 @@ cudaError_t launch_gemm_tf32_resident(const CUtensorMap* gmaps, const Leaf* leav
 
 cudaError_t launch_gemm_tf32(int bn, const MapSet& maps, const CUtensorMap* gmaps, const Leaf* leaves, int nleaves,
                              const Target* targets, const CUtensorMap* tmaps, unsigned* flags, unsigned epoch,
-                             int total_items, int* err, int grid, cudaStream_t stream, bool pair) {
+                             int total_items, int* err, int grid, cudaStream_t stream, bool pair,
+                             const int* item_leaf) {
     if (pair)
         return launch_tc_impl<MODE_TF32, 256, false, true>(maps, gmaps, leaves, nleaves, targets, tmaps, flags, epoch,
-                                                           total_items, err, grid, stream);
+                                                           total_items, err, grid, stream, nullptr, item_leaf);
     if (bn == 256)
         return launch_tc_impl<MODE_TF32, 256>(maps, gmaps, leaves, nleaves, targets, tmaps, flags, epoch, total_items,
-                                              err, grid, stream);
+                                              err, grid, stream, nullptr, item_leaf);
     return launch_tc_impl<MODE_TF32, 128>(maps, gmaps, leaves, nleaves, targets, tmaps, flags, epoch, total_items, err,
-                                          grid, stream);
+                                          grid, stream, nullptr, item_leaf);
 }
 
 cudaError_t launch_gemm_bf16x3(int bn, const MapSet& maps, const CUtensorMap* gmaps, const Leaf* leaves, int nleaves,
                                const Target* targets, const CUtensorMap* tmaps, unsigned* flags, unsigned epoch,
-                               int total_items, int* err, int grid, cudaStream_t stream) {
+                               int total_items, int* err, int grid, cudaStream_t stream, const int* item_leaf) {
     if (bn == 256)
         return launch_tc_impl<MODE_BF16X3, 256>(maps, gmaps, leaves, nleaves, targets, tmaps, flags, epoch,
-                                                total_items, err, grid, stream);
+                                                total_items, err, grid, stream, nullptr, item_leaf);
     return launch_tc_impl<MODE_BF16X3, 128>(maps, gmaps, leaves, nleaves, targets, tmaps, flags, epoch, total_items,
-                                            err, grid, stream);
+                                            err, grid, stream, nullptr, item_leaf);
 }
 
 int tf32_tile_m() { return TF_BM; }

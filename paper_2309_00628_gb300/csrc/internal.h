@@ -27,10 +27,12 @@ struct MatRef {
 // and this launch's epoch (1, 2, ... per counter array), or nullptr.
 // pair: the CTA-pair form (cta_group::2, 256 x 256 tiles, bn must be 256): work items count
 // 256-row tiles (Leaf::tile_begin in those units), B maps have 128-row boxes, `grid` is the number
-// of SMs to use (rounded down to whole pairs).
+// of SMs to use (rounded down to whole pairs).  item_leaf: optional device table of the leaf of
+// every work item (saves the per-tile binary search over the leaves; nullptr: search).
 cudaError_t launch_gemm_tf32(int bn, const MapSet& maps, const CUtensorMap* gmaps, const Leaf* leaves, int nleaves,
                              const Target* targets, const CUtensorMap* tmaps, unsigned* flags, unsigned epoch,
-                             int total_items, int* err, int grid, cudaStream_t stream, bool pair = false);
+                             int total_items, int* err, int grid, cudaStream_t stream, bool pair = false,
+                             const int* item_leaf = nullptr);
 // Resident (serving) form of the TF32 grouped GEMM, BN = 256: runs until ctl.stop, an error, or
 // ctl.idle_ns without newly published items.
 cudaError_t launch_gemm_tf32_resident(const CUtensorMap* gmaps, const Leaf* leaves, const Target* targets,
@@ -44,7 +46,8 @@ int bf16x3_tile_k();
 // (k x n as stored); Leaf::kblocks counts 64-deep k blocks.
 cudaError_t launch_gemm_bf16x3(int bn, const MapSet& maps, const CUtensorMap* gmaps, const Leaf* leaves, int nleaves,
                                const Target* targets, const CUtensorMap* tmaps, unsigned* flags, unsigned epoch,
-                               int total_items, int* err, int grid, cudaStream_t stream);
+                               int total_items, int* err, int grid, cudaStream_t stream,
+                               const int* item_leaf = nullptr);
 
 // hi = bf16(x), lo = bf16(x - hi), elementwise on a rows x cols FP32 view; outputs share ldo.
 cudaError_t launch_split_bf16(int rows, int cols, const float* x, long long ldx, void* hi, void* lo, long long ldo,
@@ -86,7 +89,9 @@ struct PreaddArgs {
 cudaError_t launch_preadd(int elem_bytes, const PreaddArgs& a, cudaStream_t stream);
 
 // One FP32 copy (or transpose) job of a batched launch: out (out_rows x out_cols) <- x or x^T,
-// zero outside the source extent; tile_begin is the job's first 32 x 32 tile (prefix sum).
+// zero outside the source extent; tile_begin is the job's first BCOPY_TILE x BCOPY_TILE output
+// tile (prefix sum).
+constexpr int BCOPY_TILE = 64;
 struct CopyJob {
     const void* x;
     long long ldx;

@@ -525,8 +525,12 @@ cudaError_t launch_transpose_inplace(int n, float* x, long long ld, cudaStream_t
 
 // ============================================================== batched copies / transposes
 // One launch over many independent FP32 copies: job j covers tiles [tile_begin, tile_begin + tiles)
-// of 32 x 32; a block finds its job by binary search.  `transpose` selects out = x^T.
-__global__ void batched_copy_kernel(const CopyJob* __restrict__ jobs, int njobs, int transpose) {
+// of BCOPY_TILE x BCOPY_TILE; a block finds its job by binary search.  `transpose` selects
+// out = x^T.  256 threads per block: a warp covers half of one 64-wide tile row, so reads and
+// writes are 128-byte runs; transposes go through a padded shared tile (conflict-free).
+__global__ void __launch_bounds__(256) batched_copy_kernel(const CopyJob* __restrict__ jobs, int njobs,
+                                                           int transpose) {
+    constexpr int T = BCOPY_TILE;
     int lo = 0, hi = njobs - 1;
     const int b = blockIdx.x;
     while (lo < hi) {
@@ -535,33 +539,47 @@ __global__ void batched_copy_kernel(const CopyJob* __restrict__ jobs, int njobs,
     }
     const CopyJob J = jobs[lo];
     const int t = b - J.tile_begin;
-    const int tiles_c = (J.out_cols + 31) / 32;
-    const int r0 = (t / tiles_c) * 32, c0 = (t % tiles_c) * 32;
+    const int tiles_c = (J.out_cols + T - 1) / T;
+    const int r0 = (t / tiles_c) * T, c0 = (t % tiles_c) * T;
     const float* x = static_cast<const float*>(J.x);
     float* out = static_cast<float*>(J.out);
+    const int tx = threadIdx.x % T, ty = threadIdx.x / T;
+    constexpr int RS = 256 / T;  // rows per pass
+    constexpr int NP = T / RS;   // passes: all loads of a thread are issued before its stores
+    float v[NP];
     if (!transpose) {
-        for (int i = threadIdx.y; i < 32; i += 8) {
-            const int r = r0 + i, c = c0 + threadIdx.x;
-            if (r < J.out_rows && c < J.out_cols)
-                out[r * J.ldo + c] = (r < J.src_rows && c < J.src_cols) ? x[r * J.ldx + c] : 0.f;
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            const int r = r0 + ty + p * RS, c = c0 + tx;
+            v[p] = (r < J.src_rows && c < J.src_cols) ? x[(long long)r * J.ldx + c] : 0.f;
+        }
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            const int r = r0 + ty + p * RS, c = c0 + tx;
+            if (r < J.out_rows && c < J.out_cols) out[(long long)r * J.ldo + c] = v[p];
         }
         return;
     }
-    __shared__ float tt[32][33];
-    for (int i = threadIdx.y; i < 32; i += 8) {
-        const int c = c0 + i, r = r0 + threadIdx.x;  // x row c, column r
-        tt[i][threadIdx.x] = (c < J.src_rows && r < J.src_cols) ? x[c * J.ldx + r] : 0.f;
+    __shared__ float tt[T][T + 1];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        const int c = c0 + ty + p * RS, r = r0 + tx;  // x row c, column r
+        v[p] = (c < J.src_rows && r < J.src_cols) ? x[(long long)c * J.ldx + r] : 0.f;
     }
+#pragma unroll
+    for (int p = 0; p < NP; ++p) tt[ty + p * RS][tx] = v[p];
     __syncthreads();
-    for (int i = threadIdx.y; i < 32; i += 8) {
-        const int r = r0 + i, c = c0 + threadIdx.x;
-        if (r < J.out_rows && c < J.out_cols) out[r * J.ldo + c] = tt[threadIdx.x][i];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        const int i = ty + p * RS;
+        const int r = r0 + i, c = c0 + tx;
+        if (r < J.out_rows && c < J.out_cols) out[(long long)r * J.ldo + c] = tt[tx][i];
     }
 }
 
 cudaError_t launch_batched_copy(const CopyJob* jobs, int njobs, int total_tiles, int transpose, cudaStream_t s) {
     if (njobs <= 0 || total_tiles <= 0) return cudaSuccess;
-    batched_copy_kernel<<<total_tiles, dim3(32, 8), 0, s>>>(jobs, njobs, transpose);
+    batched_copy_kernel<<<total_tiles, 256, 0, s>>>(jobs, njobs, transpose);
     return cudaGetLastError();
 }
 

@@ -154,7 +154,7 @@ def sw_error_norms(h, elem_bytes, m, n, k, A, lda, B, ldb, C, ldc, R, ldr, strea
 
 
 PROFILE_KINDS = ["gemm_tf32", "gemm_simt", "addsub", "copy_pad", "preadd", "memset", "transpose", "transpose_sq",
-                 "split_bf16", "gemm_bf16x3"]
+                 "split_bf16", "gemm_bf16x3", "batch_copy"]
 
 
 def sw_profile(h, enable: bool) -> int:
