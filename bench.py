@@ -4,8 +4,8 @@ plain tensor-core GEMM of the same library and the FP64 CPU oracle.
 
 Workload (default): one FP32 product C = A B, square n = 8192, A and B i.i.d. uniform[-1, 1]
 (PCG64 seeds 0 and 1), TF32 leaves with FP32 accumulation.  A step is one whole product
-through the C ABI (sw_smm): B -> B^T, the operand-sum pass, the grouped leaf GEMM with the
-post-additions in its epilogue.  Inputs (256 MiB each) exceed the 129 MB L2, so no flush is
+through the C ABI (sw_smm): the operand-sum pass and the grouped leaf GEMM (CTA pairs, B read
+N-major as stored) with the post-additions in its epilogue.  Inputs (256 MiB each) exceed the 129 MB L2, so no flush is
 needed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]

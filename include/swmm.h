@@ -137,7 +137,8 @@ typedef struct {
 
 /* `count` independent FP32 products (different shapes allowed, any alignment), asynchronous on
  * `stream`.  The tensor-core work of all products runs as ONE persistent grouped launch; the
- * per-product staging (packing unaligned A, writing B^T) runs as one batched launch each, and
+ * per-product staging (packing operands whose rows are not 16-byte aligned) runs as one batched
+ * launch, and
  * depth >= 1 products add their operand-sum passes.  The whole batch is captured once into a CUDA
  * graph and replayed on later calls with the same problem list (same pointers and shapes).
  * Variant: SW_SCHED_FUSED with SW_LEAF_TF32 (other schedules / leaves: SW_EUNSUPPORTED); each

@@ -70,6 +70,22 @@ bool make_map_f32(CUtensorMap* m, const void* base, int rows, int cols, long lon
     return r == CUDA_SUCCESS;
 }
 
+// FP32 row-major k x n view of an N-major B operand (ld elements) -> 2-D tensor map with a box of
+// 32 columns (128 bytes) x 32 rows, 128-byte swizzle with 32-byte atoms (the layout the tensor core
+// reads an MN-major TF32 operand from), zero fill out of bounds.
+bool make_map_f32_n(CUtensorMap* m, const void* base, int rows, int cols, long long ld) {
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)std::max(cols, 1), (cuuint64_t)std::max(rows, 1)};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
+    cuuint32_t box[2] = {32, 32};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B_ATOM_32B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
 // BF16 row-major view rows x cols (ld elements, a multiple of 8) -> 2-D tensor map with a box of
 // 64 columns (128 bytes) x box_rows, 128-byte swizzle, zero fill out of bounds.
 bool make_map_bf16(CUtensorMap* m, const void* base, int rows, int cols, long long ld, int box_rows) {
@@ -112,6 +128,7 @@ struct Op {
     int bn = 256, nleaves = 0, items = 0, ntmaps = 0, nflags = 0;
     bool pair = false;   // TF32: the CTA-pair form (256 x 256 tiles; items count 256-row tiles)
     bool has_item_leaf = false;  // tensor-core GEMM: item -> leaf table at item_leaf_off
+    bool nmaj = false;           // TF32 GEMM reading B N-major (launch_gemm_tf32n)
     size_t item_leaf_off = 0;
     size_t leaves_off = 0, targets_off = 0, refs_off = 0, tmaps_off = 0, flags_off = 0;
     unsigned epoch = 0;  // launches of this op so far (its ordering counters grow by 4 per launch)
@@ -149,15 +166,17 @@ struct View {
     int rows, cols;
 };
 
-// Lowers one product to ops.  On the FP32 path the tensor cores take B as B^T (K-major), so
-// every B-side value -- B itself, its quadrants, the T sums and the B-side temporaries -- is
-// held transposed ("bt" storage): a logical B quadrant Bij lives at position ji of the stored
+// Lowers one product to ops.  The TF32 leaves read B N-major, as stored (nmaj).  In the B^T
+// form (serving plans, SWMM_TF32_BT=1) the tensor cores take B as B^T (K-major), so every
+// B-side value -- B itself, its quadrants, the T sums and the B-side temporaries -- is held
+// transposed ("bt" storage): a logical B quadrant Bij lives at position ji of the stored
 // matrix, and a k x n block is stored n x k.  Elementwise steps are orientation-free as long
 // as all their operands share it, which the schedules below guarantee.
 struct Planner {
     int eb;                 // 4 = FP32 (TF32 or split-BF16 leaves), 8 = FP64
     bool bf;                // FP32 with split-BF16 leaves
-    bool bt;                // B side stored transposed (TF32 leaves only)
+    bool bt;                // B side stored transposed (TF32 leaves read through B^T)
+    bool nmaj = false;      // TF32 leaves read B N-major, as stored (bt is then false)
     uint32_t variant;
     bool dry;               // size only: no pointers, no maps
     char* ws_base;
@@ -427,7 +446,8 @@ struct Planner {
         push(o);
     }
 
-    // One leaf product c (=|+=) a b on the tensor cores (FP32: b is held as B^T) or, for FP64,
+    // One leaf product c (=|+=) a b on the tensor cores (FP32: b as stored, or as B^T in bt
+    // storage) or, for FP64,
     // on the SIMT kernel.
     bool gemm(View a, View b, View c, int mode) {
         if (c.rows <= 0 || c.cols <= 0) return true;
@@ -457,8 +477,10 @@ struct Planner {
         o.bn = force_bn ? force_bn : bn_override() ? bn_override() : (c.cols <= 128 ? 128 : 256);
         lf.kblocks = (int)ceil_div(a.cols, tf32_tile_k());
         lf.tiles_n = (int)ceil_div(c.cols, o.bn);
+        o.nmaj = nmaj;
         if (!make_map_f32(&o.maps.m[0], a.p, a.rows, a.cols, a.ld, 32, tf32_tile_m()) ||
-            !make_map_f32(&o.maps.m[1], b.p, b.rows, b.cols, b.ld, 32, b_box(o.bn))) {
+            !(nmaj ? make_map_f32_n(&o.maps.m[1], b.p, b.rows, b.cols, b.ld)
+                   : make_map_f32(&o.maps.m[1], b.p, b.rows, b.cols, b.ld, 32, b_box(o.bn)))) {
             err = "tensor map encoding failed (alignment?)";
             return false;
         }
@@ -929,10 +951,14 @@ struct Planner {
         } else if (eb == 4) {
             o.kind = OP_GEMM_TF32;
             o.bn = bn;
-            if (!make_map_f32(&o.maps.m[0], A.p, m, k, A.ld, 32, tf32_tile_m()) ||
-                !make_map_f32(&o.maps.m[1], B.p, n, k, B.ld, 32, b_box(bn)) ||
-                !make_map_f32(&o.maps.m[2], SA.p, std::max(SA.rows, 1), kb, SA.ld, 32, tf32_tile_m()) ||
-                !make_map_f32(&o.maps.m[3], SB.p, std::max(SB.rows, 1), kb, SB.ld, 32, b_box(bn))) {
+            o.nmaj = nmaj;
+            const bool mok =
+                nmaj ? make_map_f32_n(&o.maps.m[1], B.p, k, n, B.ld) &&
+                           make_map_f32_n(&o.maps.m[3], SB.p, std::max(SB.rows, 1), nb, SB.ld)
+                     : make_map_f32(&o.maps.m[1], B.p, n, k, B.ld, 32, b_box(bn)) &&
+                           make_map_f32(&o.maps.m[3], SB.p, std::max(SB.rows, 1), kb, SB.ld, 32, b_box(bn));
+            if (!make_map_f32(&o.maps.m[0], A.p, m, k, A.ld, 32, tf32_tile_m()) || !mok ||
+                !make_map_f32(&o.maps.m[2], SA.p, std::max(SA.rows, 1), kb, SA.ld, 32, tf32_tile_m())) {
                 err = "tensor map encoding failed";
                 return false;
             }
@@ -949,11 +975,11 @@ struct Planner {
     }
 
     // ---------------------------------------------------------- batched (TF32 leaves)
-    // Many independent products in one grouped launch: one batched copy launch packs the A
-    // operands that are not 16-byte aligned, one batched transpose launch writes every B^T, the
-    // depth >= 1 products add their operand-sum passes, and all leaves of all products go into a
-    // single persistent GEMM launch (longest k first).  C needs no staging: unaligned or ragged
-    // C blocks take the per-thread epilogue.
+    // Many independent products in one grouped launch: one batched copy launch packs the A and B
+    // operands whose rows are not 16-byte aligned (bt storage: a batched transpose launch writes
+    // every B^T instead), the depth >= 1 products add their operand-sum passes, and all leaves of
+    // all products go into a single persistent GEMM launch (longest k first).  C needs no
+    // staging: unaligned or ragged C blocks take the per-thread epilogue.
     bool batched(const sw_problem* probs, int count, const std::vector<int>& depth) {
         batch = true;
         force_bn = 256;
@@ -981,10 +1007,19 @@ struct Planner {
                 packs.push_back(job(a, a2, pack_tiles));
                 a = a2;
             }
-            View bt = talloc(q.n, q.k);
-            trans.push_back(job(b, bt, trans_tiles));
+            if (nmaj) {  // B read as stored: packed only when its rows are not 16-byte aligned
+                if (!vec_ok(b)) {
+                    View b2 = talloc(q.k, q.n);
+                    packs.push_back(job(b, b2, pack_tiles));
+                    b = b2;
+                }
+            } else {
+                View bt = talloc(q.n, q.k);
+                trans.push_back(job(b, bt, trans_tiles));
+                b = bt;
+            }
             As[i] = a;
-            Bs[i] = bt;
+            Bs[i] = b;
             Cs[i] = c;
         }
         if (!dry) {
@@ -1011,6 +1046,7 @@ struct Planner {
         if (dry || bleaves.empty()) return true;
         Op o;
         o.kind = OP_GEMM_TF32;
+        o.nmaj = nmaj;
         o.bn = force_bn;
         o.items = bitems;
         o.ngmaps = (int)bmaps.size();
@@ -1127,7 +1163,11 @@ static sw_status build_plan(sw_handle h, int eb, const void* A, int lda, const v
     Planner P;
     P.eb = eb;
     P.bf = bf;
-    P.bt = eb == 4 && !bf;
+    // TF32 leaves read B N-major, as stored (no B^T staging), except in serving plans, whose
+    // resident GEMM reads B^T; SWMM_TF32_BT=1 selects the B^T form everywhere (diagnostics)
+    static const bool bt_env = getenv("SWMM_TF32_BT") != nullptr;
+    P.nmaj = eb == 4 && !bf && !server && !bt_env;
+    P.bt = eb == 4 && !bf && !P.nmaj;
     P.variant = variant;
     P.dry = dry;
     P.ws_base = ws_base ? ws_base : h->ws;
@@ -1145,10 +1185,12 @@ static sw_status build_plan(sw_handle h, int eb, const void* A, int lda, const v
     const bool direct = L == 0 || algo == SW_ALGO_NAIVE || sched == SW_SCHED_FUSED;  // C is only a target
     const bool a_ok = eb == 8 || bf || Planner::vec_ok(Av),
                c_ok = eb == 8 || bf || (server && direct) || Planner::vec_ok(Cv);
-    // B in the storage the leaves want: B^T in workspace (FP32), B itself (FP64)
+    // B in the storage the leaves want: B itself (FP64, split-BF16, N-major TF32; copied when a
+    // TMA read needs aligned rows), B^T in workspace (bt storage)
     auto stage_b = [&](View b, int rows_pad, int cols_pad) -> View {  // logical k x n -> storage
         if (!P.bt) {
-            if (rows_pad == b.rows && cols_pad == b.cols) return b;
+            // N-major TF32 leaves read B through TMA: 16-byte aligned rows
+            if (rows_pad == b.rows && cols_pad == b.cols && (!P.nmaj || Planner::vec_ok(b))) return b;
             View b2 = P.talloc(rows_pad, cols_pad);
             P.copy_pad(b2, b);
             return b2;
@@ -1242,7 +1284,7 @@ static sw_status run_ops(sw_handle h, Plan* plan, cudaStream_t s, size_t first, 
         }
         switch (o.kind) {
             case OP_GEMM_TF32:
-                e = launch_gemm_tf32(o.bn, o.maps,
+                e = (o.nmaj ? launch_gemm_tf32n : launch_gemm_tf32)(o.bn, o.maps,
                                      o.ngmaps ? reinterpret_cast<const CUtensorMap*>(blob + o.gmaps_off) : nullptr,
                                      reinterpret_cast<const Leaf*>(blob + o.leaves_off),
                                      o.nleaves, reinterpret_cast<const Target*>(blob + o.targets_off),
@@ -1334,7 +1376,9 @@ static sw_status build_batched_plan(sw_handle h, int count, const sw_problem* pr
     Planner P;
     P.eb = 4;
     P.bf = false;
-    P.bt = true;
+    static const bool bt_env = getenv("SWMM_TF32_BT") != nullptr;  // diagnostics: B^T staging
+    P.nmaj = !bt_env;
+    P.bt = !P.nmaj;
     P.variant = variant;
     P.dry = dry;
     P.ws_base = h->ws;

@@ -4,11 +4,13 @@
 // leaf and a single STORE target it is the plain product of Alg. 1) and adds sign * P into
 // each of the leaf's target blocks of C -- the post-additions folded into the epilogue.
 //
-// Two operand modes:
-//  * TF32: FP32 operands staged by TMA into 128-byte-swizzled shared memory and consumed by
+// Operand modes:
+//  * TF32N (the default TF32 form): FP32 operands staged by TMA and consumed by
 //    tcgen05.mma.kind::tf32 (the tensor core reads each FP32 operand as TF32: its 10 leading
-//    mantissa bits).  Both operands K-major: A as stored (m x k) and B as B^T (n x k) --
-//    kind::tf32 does not take an N-major B, so the planner hands this mode B^T views.
+//    mantissa bits).  A K-major as stored (m x k, 128-byte swizzle); B N-major as stored (k x n):
+//    32-column boxes with the 128-byte swizzle of 32-byte atoms, read by a layout-type-1
+//    descriptor whose K direction comes in 4-row groups (stride 512 bytes).
+//  * TF32: the same with B given as B^T (n x k), K-major (serving loop, diagnostics).
 //  * BF16X3: each FP32 operand arrives split into bf16 halves hi = bf16(x), lo = bf16(x - hi);
 //    per k-step the kernel issues kind::f16 MMAs hi*hi + hi*lo + lo*hi into one FP32
 //    accumulator.  A K-major, B N-major (as stored, k x n).
@@ -38,19 +40,23 @@ namespace swk {
 constexpr int TF_BM = 128;
 constexpr int TF_BK = 32;  // TF32 k-block: 32 FP32 = 128 bytes, one swizzle row
 constexpr int TF_GROUP_M = 8;
-constexpr int MODE_TF32 = 0, MODE_BF16X3 = 1;
+// MODE_TF32N: TF32 with B N-major (k x n as stored): B staged in 32-column (128-byte) boxes
+// with the 32-byte-atom 128-byte swizzle, read by the MMA through a layout-type-1 descriptor.
+constexpr int MODE_TF32 = 0, MODE_BF16X3 = 1, MODE_TF32N = 2;
+constexpr uint32_t SWZ_128B_BASE32B = 1;  // descriptor layout: 128-byte swizzle, 32-byte atoms
 
 // PAIR: the TF32 form for a CTA pair (cta_group::2): one 256 x BN tile per pair, each CTA holding
 // 128 rows of A and BN / 2 rows of B^T; the even CTA issues M = 256 MMAs that read both CTAs'
 // shared memory and write 128 accumulator rows into each CTA's tensor memory.
 template <int MODE, int BN, bool PAIR = false>
 struct TfCfg {
-    static constexpr int BK = MODE == MODE_TF32 ? 32 : 64;           // elements per 128-byte row
+    static constexpr bool TF = MODE != MODE_BF16X3;                  // a TF32 form
+    static constexpr int BK = TF ? 32 : 64;                          // elements per 128-byte row
     static constexpr int TM = PAIR ? 2 * TF_BM : TF_BM;              // tile rows per work item
     static constexpr int B_ROWS = PAIR ? BN / 2 : BN;                // B rows held by one CTA
     static constexpr int A_BYTES = TF_BM * 128;                      // one A tile (16 KB)
     static constexpr int B_BYTES = B_ROWS * 128;                     // one B tile
-    static constexpr int NOPS = MODE == MODE_TF32 ? 1 : 2;           // tiles per operand (hi, lo)
+    static constexpr int NOPS = TF ? 1 : 2;                          // tiles per operand (hi, lo)
     static constexpr int STAGE_BYTES = NOPS * (A_BYTES + B_BYTES);
     static constexpr int STAGES = (4 * 49152) / STAGE_BYTES;         // 192 KB of operand stages
     static constexpr int TMEM_COLS = 2 * BN;
@@ -61,8 +67,8 @@ struct TfCfg {
     // instruction descriptor: D F32; TF32: A/B TF32, both K-major; BF16X3: A/B BF16, A K-major,
     // B MN-major; N = BN, M = 128
     static constexpr uint32_t IDESC =
-        MODE == MODE_TF32
-            ? ((1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24))
+        TF ? ((1u << 4) | (2u << 7) | (2u << 10) | (MODE == MODE_TF32N ? (1u << 16) : 0u) |
+              ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24))
             : ((1u << 4) | (1u << 7) | (1u << 10) | (1u << 16) | ((uint32_t)(BN >> 3) << 17) |
                ((uint32_t)(TF_BM >> 4) << 24));
 };
@@ -178,7 +184,7 @@ __global__ void __launch_bounds__(192, 1)
                      const Leaf* __restrict__ leaves, int nleaves, const Target* __restrict__ targets,
                      const CUtensorMap* __restrict__ tmaps, unsigned* __restrict__ flags, unsigned epoch,
                      int total_items, int* err, const ResidentCtl ctl) {
-    static_assert(!PAIR || (MODE == MODE_TF32 && !RES), "CTA pairs: TF32, non-resident only");
+    static_assert(!PAIR || (MODE != MODE_BF16X3 && !RES), "CTA pairs: TF32, non-resident only");
     using Cfg = TfCfg<MODE, BN, PAIR>;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw_addr = smem_u32(smem_raw);
@@ -268,12 +274,12 @@ __global__ void __launch_bounds__(192, 1)
                 const int am = __ldg(&L->a_map), bm = __ldg(&L->b_map);
                 const int a_row = __ldg(&L->a_row) + ip.tm * Cfg::TM + (int)rank * TF_BM;
                 const int a_col = __ldg(&L->a_col);
-                // TF32: B^T, rows are N, columns K.  BF16X3: B as stored, rows K, columns N.
+                // TF32: B^T, rows are N, columns K.  BF16X3 / TF32N: B as stored, rows K, columns N.
                 const int b_row = __ldg(&L->b_row) + (MODE == MODE_TF32 ? ip.tn * BN + (int)rank * Cfg::B_ROWS : 0);
-                const int b_col = __ldg(&L->b_col) + (MODE == MODE_TF32 ? 0 : ip.tn * BN);
+                const int b_col = __ldg(&L->b_col) + (MODE == MODE_TF32 ? 0 : ip.tn * BN + (int)rank * Cfg::B_ROWS);
                 const int kb_n = __ldg(&L->kblocks);
                 // TMA x coordinates must be 16-byte aligned (4 FP32 / 8 BF16 elements)
-                if (((a_col | b_col) & (MODE == MODE_TF32 ? 3 : 7)) != 0) {
+                if (((a_col | b_col) & (Cfg::TF ? 3 : 7)) != 0) {
                     set_error(err, ERR_ALIGN);
                     ok = false;
                     break;
@@ -293,8 +299,15 @@ __global__ void __launch_bounds__(192, 1)
                         const uint32_t fb = mapa_shared(smem_u32(&full[stage]), 0u);
                         tma_load_2d_pair(stage_a(stage, 0), pick_map(maps, gmaps, am), fb, a_col + kb * Cfg::BK,
                                          a_row);
-                        tma_load_2d_pair(stage_b(stage, 0), pick_map(maps, gmaps, bm), fb, b_col + kb * Cfg::BK,
-                                         b_row);
+                        if (MODE == MODE_TF32N) {
+#pragma unroll
+                            for (int c = 0; c < Cfg::B_ROWS / 32; ++c)  // 32 N-columns x 32 K-rows per box
+                                tma_load_2d_pair(stage_b(stage, 0) + c * 4096, pick_map(maps, gmaps, bm), fb,
+                                                 b_col + c * 32, b_row + kb * Cfg::BK);
+                        } else {
+                            tma_load_2d_pair(stage_b(stage, 0), pick_map(maps, gmaps, bm), fb, b_col + kb * Cfg::BK,
+                                             b_row);
+                        }
                         ++issued;
                         if (++stage == Cfg::STAGES) { stage = 0; phase ^= 1u; }
                         continue;
@@ -307,6 +320,11 @@ __global__ void __launch_bounds__(192, 1)
                         tma_load_2d(stage_a(stage, op), ma, &full[stage], a_col + kb * Cfg::BK, a_row);
                         if (MODE == MODE_TF32) {
                             tma_load_2d(stage_b(stage, op), mb, &full[stage], b_col + kb * Cfg::BK, b_row);
+                        } else if (MODE == MODE_TF32N) {
+#pragma unroll
+                            for (int c = 0; c < BN / 32; ++c)  // 32 N-columns (128 B) x 32 K-rows per box
+                                tma_load_2d(stage_b(stage, op) + c * 4096, mb, &full[stage], b_col + c * 32,
+                                            b_row + kb * Cfg::BK);
                         } else {
 #pragma unroll
                             for (int c = 0; c < BN / 64; ++c)  // 64 N-columns (128 B) x 64 K-rows per box
@@ -359,13 +377,17 @@ __global__ void __launch_bounds__(192, 1)
                 for (int kb = 0; kb < kb_n; ++kb) {
                     if (!mbar_wait(&full[stage], phase, err, ERR_WAIT_FULL)) { ok = false; break; }
                     tc_fence_after();
-                    if (MODE == MODE_TF32) {
+                    if (Cfg::TF) {
                         const uint32_t a_addr = smem_u32(stage_a(stage, 0));
                         const uint32_t b_addr = smem_u32(stage_b(stage, 0));
 #pragma unroll
                         for (int kk = 0; kk < TF_BK / 8; ++kk) {  // K = 8 per MMA, 32 bytes
                             const uint64_t ad = make_sdesc(a_addr + kk * 32, 16, 1024, SWZ_128B);
-                            const uint64_t bd = make_sdesc(b_addr + kk * 32, 16, 1024, SWZ_128B);
+                            // TF32N: 8 K-rows of 128 bytes per step, read as two 4-row groups
+                            // 512 bytes apart; 32-column chunks 4 KB apart
+                            const uint64_t bd = MODE == MODE_TF32N
+                                                    ? make_sdesc(b_addr + kk * 1024, 4096, 512, SWZ_128B_BASE32B)
+                                                    : make_sdesc(b_addr + kk * 32, 16, 1024, SWZ_128B);
                             if (PAIR) mma_tf32_pair(d_tmem, ad, bd, Cfg::IDESC, (kb | kk) != 0 ? 1u : 0u);
                             else mma_tf32(d_tmem, ad, bd, Cfg::IDESC, (kb | kk) != 0 ? 1u : 0u);
                         }
@@ -684,6 +706,20 @@ cudaError_t launch_gemm_tf32(int bn, const MapSet& maps, const CUtensorMap* gmap
                                               err, grid, stream, nullptr, item_leaf);
     return launch_tc_impl<MODE_TF32, 128>(maps, gmaps, leaves, nleaves, targets, tmaps, flags, epoch, total_items, err,
                                           grid, stream, nullptr, item_leaf);
+}
+
+cudaError_t launch_gemm_tf32n(int bn, const MapSet& maps, const CUtensorMap* gmaps, const Leaf* leaves, int nleaves,
+                              const Target* targets, const CUtensorMap* tmaps, unsigned* flags, unsigned epoch,
+                              int total_items, int* err, int grid, cudaStream_t stream, bool pair,
+                              const int* item_leaf) {
+    if (pair)
+        return launch_tc_impl<MODE_TF32N, 256, false, true>(maps, gmaps, leaves, nleaves, targets, tmaps, flags,
+                                                            epoch, total_items, err, grid, stream, nullptr, item_leaf);
+    if (bn == 256)
+        return launch_tc_impl<MODE_TF32N, 256>(maps, gmaps, leaves, nleaves, targets, tmaps, flags, epoch,
+                                               total_items, err, grid, stream, nullptr, item_leaf);
+    return launch_tc_impl<MODE_TF32N, 128>(maps, gmaps, leaves, nleaves, targets, tmaps, flags, epoch, total_items,
+                                           err, grid, stream, nullptr, item_leaf);
 }
 
 cudaError_t launch_gemm_bf16x3(int bn, const MapSet& maps, const CUtensorMap* gmaps, const Leaf* leaves, int nleaves,

@@ -33,6 +33,12 @@ cudaError_t launch_gemm_tf32(int bn, const MapSet& maps, const CUtensorMap* gmap
                              const Target* targets, const CUtensorMap* tmaps, unsigned* flags, unsigned epoch,
                              int total_items, int* err, int grid, cudaStream_t stream, bool pair = false,
                              const int* item_leaf = nullptr);
+// TF32 leaves with B N-major (k x n as stored; maps from make_map_f32_n, Leaf::b_row = K,
+// Leaf::b_col = N); otherwise as launch_gemm_tf32.
+cudaError_t launch_gemm_tf32n(int bn, const MapSet& maps, const CUtensorMap* gmaps, const Leaf* leaves, int nleaves,
+                              const Target* targets, const CUtensorMap* tmaps, unsigned* flags, unsigned epoch,
+                              int total_items, int* err, int grid, cudaStream_t stream, bool pair = false,
+                              const int* item_leaf = nullptr);
 // Resident (serving) form of the TF32 grouped GEMM, BN = 256: runs until ctl.stop, an error, or
 // ctl.idle_ns without newly published items.
 cudaError_t launch_gemm_tf32_resident(const CUtensorMap* gmaps, const Leaf* leaves, const Target* targets,

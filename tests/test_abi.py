@@ -62,11 +62,11 @@ def test_workspace_matches_schedule_counts(lib, L):
         st, b = swmm.sw_mm_workspace_size(n, n, n, cutoff, swmm.SW_ALGO_WINOGRAD | sched, 8)
         assert st == swmm.SW_OK
         assert b == pytest.approx(oracle.workspace_elems(which, n, n, n, L) * 8, rel=1e-3)
-        # FP32: the same temporaries plus the B^T copy the TF32 tensor cores read
+        # FP32: the same temporaries (the TF32 tensor cores read B as stored: no B^T copy)
         st, b = swmm.sw_mm_workspace_size(n, n, n, cutoff, swmm.SW_ALGO_WINOGRAD | sched, 4)
         assert st == swmm.SW_OK
-        assert b == pytest.approx((oracle.workspace_elems(which, n, n, n, L) + n * n) * 4, rel=1e-3)
-    for eb in (4, 8):  # in place: B is transposed in place, temporaries live in A, B, C
+        assert b == pytest.approx(oracle.workspace_elems(which, n, n, n, L) * 4, rel=1e-3)
+    for eb in (4, 8):  # in place: temporaries live in A, B, C
         st, b = swmm.sw_mm_workspace_size(n, n, n, cutoff, swmm.SW_ALGO_WINOGRAD | swmm.SW_SCHED_IN_PLACE, eb)
         assert st == swmm.SW_OK and b == 0
 
@@ -78,7 +78,7 @@ def test_fused_workspace_counts_materialised_sums(lib):
         st, b = swmm.sw_mm_workspace_size(n, n, n, n >> L, swmm.SW_ALGO_WINOGRAD | swmm.SW_SCHED_FUSED, 4)
         blk = (n >> L) ** 2 * 4
         assert st == swmm.SW_OK
-        assert b == pytest.approx(2 * (7 ** L - 3 ** L) * blk + n * n * 4, rel=1e-3)  # + B^T
+        assert b == pytest.approx(2 * (7 ** L - 3 ** L) * blk, rel=1e-3)
 
 
 def test_argument_errors_without_gpu(lib):
