@@ -49,6 +49,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-batched", action="store_true")
     p.add_argument("--no-serving", action="store_true")
+    p.add_argument("--no-extra", action="store_true",
+                   help="skip the depth sweep, the split-BF16 line and the n = 16384 comparison")
     p.add_argument("--serve-rates", default="2,4,8", help="Poisson arrival rates (requests/s) of the serving sweep")
     p.add_argument("--serve-requests", type=int, default=40, help="requests per rate")
     p.add_argument("--serve-share", type=int, default=16, help="SMs of the resident leaf-GEMM loop")
@@ -379,9 +381,15 @@ def main():
 
     K, W = args.steps, max(args.warmup, 3)
     clocks = ClockSampler(local)
-    total, per, clk, prof = timed(variant, args.cutoff, K, W, clocks=clocks, profile=True)
+    # the headline: K whole products, nothing but the product in the timed region
+    total, per, clk, _ = timed(variant, args.cutoff, K, W, clocks=clocks)
     # plain tensor-core GEMM of the same library, same size, same timing
-    total0, per0, _, prof0 = timed(swmm.SW_ALGO_NAIVE, 0, K, W, profile=True)
+    total0, per0, _, _ = timed(swmm.SW_ALGO_NAIVE, 0, K, W)
+    # per-kernel durations (roofline, launch counts): the same step again with every launch of the
+    # library bracketed by CUDA events on its own stream (the events cost some time per launch,
+    # so this pass is kept out of the headline)
+    Kp = max(K // 4, 10)
+    _, _, _, prof = timed(variant, args.cutoff, Kp, W, profile=True)
     if dist:
         t = torch.tensor([total, total0], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -392,7 +400,7 @@ def main():
 
     # dominant kernel: the grouped TF32 leaf GEMM
     gl, gms = prof["gemm_tf32"]
-    launches = sum(v[0] for k, v in prof.items() if k != "memset")
+    launches = int(round(sum(v[0] for k, v in prof.items()) * K / Kp))
     achieved = leaf_flops(n, L) / (gms / gl / 1e3) / 1e12 if gl else None
     pk = peaks()
     peak, peak_src = (pk["bf16_tflops"] * TF32_OVER_BF16, "of measured (bf16 burst x nominal TF32/BF16)") \
@@ -470,11 +478,68 @@ def main():
                "sample": f"{rows} random rows of the n={n} product (Alg. 1, FP64, OpenMP over rows), {tc:.1f} s"}
         amax, bmax = float(np.max(np.abs(A))), float(np.max(np.abs(B)))
         idx = torch.from_numpy(sel).cuda()
-        for name, v, c in (("winograd", variant, args.cutoff), ("plain", swmm.SW_ALGO_NAIVE, 0)):
+
+        def row_err(v, c):
             product(v, c)
             swmm.check(h, swmm.sw_sync(h, sp))
             Cr = dC[idx].double().cpu().numpy()
-            err[name] = float(np.max(np.abs(Cr - R)) / (n * amax * bmax))
+            return float(np.max(np.abs(Cr - R)) / (n * amax * bmax))
+
+        for name, v, c in (("winograd", variant, args.cutoff), ("plain", swmm.SW_ALGO_NAIVE, 0)):
+            err[name] = row_err(v, c)
+
+    # error and time against recursion depth (same inputs, same oracle rows), the FP32-accuracy
+    # split-BF16 leaves, and the n = 16384 comparison of plain and Winograd
+    extra = None
+    if rank == 0 and not args.no_extra:
+        ks = max(K // 8, 10)
+        BF = swmm.SW_LEAF_BF16X3
+        depth_rows = []
+        for lab, v, c in [("plain L0", swmm.SW_ALGO_NAIVE, 0)] + [
+                (f"winograd L{l}", swmm.SW_ALGO_WINOGRAD | swmm.SW_SCHED_FUSED, n >> l) for l in (1, 2, 3)] + [
+                (f"strassen L{l}", swmm.SW_ALGO_STRASSEN | swmm.SW_SCHED_FUSED, n >> l) for l in (1, 2)]:
+            tot, _, _, _ = timed(v, c, ks, W)
+            depth_rows.append({"variant": lab, "ms": tot / ks, "eff_tflops": flop / (tot / ks / 1e3) / 1e12,
+                               "err": row_err(v, c)})
+        bf_rows = []
+        for lab, v, c in (("plain L0", swmm.SW_ALGO_NAIVE | BF, 0),
+                          ("winograd L1", swmm.SW_ALGO_WINOGRAD | swmm.SW_SCHED_FUSED | BF, n >> 1)):
+            tot, _, _, _ = timed(v, c, ks, W)
+            bf_rows.append({"variant": lab, "ms": tot / ks, "eff_tflops": flop / (tot / ks / 1e3) / 1e12,
+                            "err": row_err(v, c)})
+        # n = 16384: device-generated uniform[-1, 1] operands (seeded), 1 GiB each
+        n2 = 2 * n
+        g2 = torch.Generator(device="cuda")
+        g2.manual_seed(11)
+        A2 = torch.rand((n2, n2), generator=g2, device="cuda") * 2 - 1
+        B2 = torch.rand((n2, n2), generator=g2, device="cuda") * 2 - 1
+        C2 = torch.empty((n2, n2), device="cuda")
+        big = []
+        for lab, v, c in (("plain L0", swmm.SW_ALGO_NAIVE, 0),
+                          ("winograd L1", swmm.SW_ALGO_WINOGRAD | swmm.SW_SCHED_FUSED, n2 >> 1),
+                          ("winograd L2", swmm.SW_ALGO_WINOGRAD | swmm.SW_SCHED_FUSED, n2 >> 2)):
+            for _ in range(W):
+                swmm.check(h, swmm.sw_smm(h, p(A2), n2, p(B2), n2, p(C2), n2, n2, n2, n2, c, v, sp))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            kb2 = 10
+            e0.record(stream)
+            for _ in range(kb2):
+                swmm.check(h, swmm.sw_smm(h, p(A2), n2, p(B2), n2, p(C2), n2, n2, n2, n2, c, v, sp))
+            e1.record(stream)
+            swmm.check(h, swmm.sw_sync(h, sp))
+            ms2 = e0.elapsed_time(e1) / kb2
+            big.append({"variant": lab, "ms": ms2, "eff_tflops": 2.0 * n2 ** 3 / (ms2 / 1e3) / 1e12})
+        del A2, B2, C2
+        # peak workspace of each schedule for the n = 16384 split-BF16 configuration (depth 2)
+        ws = {}
+        for lab, sc in (("alloc", swmm.SW_SCHED_ALLOC), ("two_temp", swmm.SW_SCHED_TWO_TEMP),
+                        ("in_place", swmm.SW_SCHED_IN_PLACE), ("fused", swmm.SW_SCHED_FUSED)):
+            st_, b_ = swmm.sw_mm_workspace_size(16384, 16384, 16384, 4096, swmm.SW_ALGO_WINOGRAD | sc | BF, 4)
+            ws[lab] = b_ if st_ == swmm.SW_OK else None
+        extra = {"depth_sweep_n8192_tf32": depth_rows, "split_bf16_n8192": bf_rows,
+                 "n16384_tf32": big,
+                 "workspace_bytes_n16384_L2_bf16x3": ws,
+                 "err_metric": "max|C - C_oracle| / (n max|A| max|B|) on the sampled oracle rows"}
 
     if rank == 0:
         traffic = traffic_from_profiles("gemm_tc.cu", f"gemm_tf32_winograd_n{n}_L{L}")
@@ -499,13 +564,15 @@ def main():
                          "kernel": "gemm_tf32_kernel (grouped leaf GEMM)", "peak_source": peak_src,
                          "algorithmic_flops_per_launch": leaf_flops(n, L),
                          "avg_launch_ms": gms / gl if gl else None},
-            "kernels_in_step": {k: {"launches_per_step": v[0] / K, "ms_per_step": v[1] / K}
+            "kernels_in_step": {k: {"launches_per_step": v[0] / Kp, "ms_per_step": v[1] / Kp}
                                 for k, v in prof.items() if v[0]},
+            "profiled_steps": Kp,
             "gpu_launches": launches,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "batched": batched,
             "serving": serving,
+            "extra": extra,
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)
