@@ -41,7 +41,13 @@
  *   The FP64 entry points ignore the leaf group and always use FP64 leaves.
  *
  * Recursion depth L (Sec. 3.4 cutoff): halve while min(ceil(m/2^l), ceil(n/2^l), ceil(k/2^l))
- * > cutoff.  cutoff <= 0 asks the library's tuned choice.  SW_ALGO_NAIVE ignores the cutoff.
+ * > cutoff.  SW_ALGO_NAIVE ignores the cutoff.  cutoff <= 0 asks the library's autotuner: the
+ * first call for a shape (a problem list for sw_mm_batched) and variant times the candidate depths
+ * (batched: also the grouped GEMM's tile shape) on the caller's operands, keeps the fastest and
+ * runs it once more, so C holds exactly its result; later calls reuse the decision (per handle).
+ * That first call therefore runs the product several times and waits for the stream.  Under stream
+ * capture, and for SW_SCHED_IN_PLACE (whose runs overwrite A and B), a static default applies
+ * instead (FP32: cutoff 8192; FP64: 64), which is also what sw_mm_depth reports for cutoff <= 0.
  */
 #ifndef SWMM_H
 #define SWMM_H
@@ -142,10 +148,16 @@ typedef struct {
  * depth >= 1 products add their operand-sum passes.  The whole batch is captured once into a CUDA
  * graph and replayed on later calls with the same problem list (same pointers and shapes).
  * Variant: SW_SCHED_FUSED with SW_LEAF_TF32 (other schedules / leaves: SW_EUNSUPPORTED); each
- * product's depth follows `cutoff` as for sw_smm (<= 0: the tuned choice).  Odd sizes are padded
- * virtually (TMA out-of-bounds fill). */
+ * product's depth follows `cutoff` as for sw_smm (<= 0: the autotuner picks one cutoff and the tile
+ * shape for the whole list).  Odd sizes are padded virtually (TMA out-of-bounds fill). */
 sw_status sw_mm_batched(sw_handle h, int count, const sw_problem *probs, int cutoff, uint32_t variant,
                         void *stream);
+
+/* The autotuner's last decision on this handle (a call with cutoff <= 0 that had to tune): the
+ * chosen cutoff (1 << 30: no recursion), the grouped GEMM's tile width and CTA-pair flag (batched
+ * calls; 0 for single products), the winner's device time in ms and the number of candidates timed.
+ * Any pointer may be NULL.  SW_EINVAL if nothing has been tuned on the handle. */
+sw_status sw_last_tuning(sw_handle h, int *cutoff, int *tile_n, int *cta_pair, double *ms, int *candidates);
 
 /* ---------------------------------------------------------------------------------------------
  * Serving: a request loop with continuous batching.  Requests (FP32 or FP64 products of any

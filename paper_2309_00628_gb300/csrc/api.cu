@@ -25,6 +25,7 @@
 #include <mutex>
 #include <string>
 #include <thread>
+#include <functional>
 #include <unordered_map>
 #include <vector>
 
@@ -190,6 +191,8 @@ struct Planner {
     bool batch = false;
     bool server = false;  // plan for the serving loop (no ordering counters)
     int force_bn = 0;
+    int batch_bn = 256;       // batched launch: tile width of the grouped GEMM (128 or 256)
+    bool batch_pair = false;  // batched launch: CTA-pair form (256 x 256 tiles; N-major B only)
     // The CTA-pair TF32 GEMM (cta_group::2) serves single products with 256-wide tiles; batched
     // and serving launches keep the one-CTA form.  SWMM_NO_PAIR=1 disables it (diagnostics).
     bool pair_ok(int bn) const {
@@ -982,7 +985,7 @@ struct Planner {
     // staging: unaligned or ragged C blocks take the per-thread epilogue.
     bool batched(const sw_problem* probs, int count, const std::vector<int>& depth) {
         batch = true;
-        force_bn = 256;
+        force_bn = batch_bn == 128 ? 128 : 256;
         std::vector<int> order(count);
         for (int i = 0; i < count; ++i) order[i] = i;
         std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return probs[x].k > probs[y].k; });
@@ -1051,6 +1054,7 @@ struct Planner {
         o.items = bitems;
         o.ngmaps = (int)bmaps.size();
         o.gmaps_off = put_blob(bmaps.data(), bmaps.size() * sizeof(CUtensorMap));
+        if (batch_pair && nmaj && o.bn == 256) to_pair(o, bleaves);  // B maps do not depend on the width
         batch = false;  // the combined op itself is emitted normally
         emit_grouped(o, bleaves, btargets, 0);
         return true;
@@ -1082,6 +1086,11 @@ struct sw_handle_s {
     std::vector<ProfRec> prof_live;
     std::vector<cudaEvent_t> prof_free;
     cudaStream_t capture_stream = nullptr;  // private stream for CUDA-graph capture
+    // autotuner (cutoff <= 0): decisions per problem signature, and the last one made
+    struct Tune { int cutoff = 0, bn = 0, pair = 0, candidates = 0; double ms = 0.0; };
+    std::unordered_map<std::string, Tune> tuned;
+    Tune last_tune;
+    bool has_tune = false;
     std::mutex mu;
 };
 
@@ -1132,7 +1141,10 @@ static sw_status ensure_ws(sw_handle h, size_t need) {
 
 static int resolve_depth(int m, int n, int k, int cutoff, uint32_t variant, int eb) {
     if ((variant & SW_ALGO_MASK) == SW_ALGO_NAIVE) return 0;
-    if (cutoff <= 0) cutoff = eb == 4 ? 4096 : 64;  // tuned default: see the bench's sweep
+    // static default where the autotuner does not run (stream capture, IN_PLACE, sw_mm_depth):
+    // from the bench's sweeps, one TF32 Winograd level pays from n = 16384 on; FP64 leaves are
+    // ALU-bound and gain from depth early
+    if (cutoff <= 0) cutoff = eb == 4 ? 8192 : 64;
     int L = 0;
     while (L < 20) {
         const long long s = 1LL << L;
@@ -1372,8 +1384,10 @@ static sw_status execute(sw_handle h, Plan* plan, cudaStream_t s) {
 }
 
 static sw_status build_batched_plan(sw_handle h, int count, const sw_problem* probs, int cutoff, uint32_t variant,
-                                    bool dry, Plan* plan) {
+                                    bool dry, Plan* plan, int bn = 256, bool pair = false) {
     Planner P;
+    P.batch_bn = bn;
+    P.batch_pair = pair;
     P.eb = 4;
     P.bf = false;
     static const bool bt_env = getenv("SWMM_TF32_BT") != nullptr;  // diagnostics: B^T staging
@@ -1398,6 +1412,125 @@ static sw_status build_batched_plan(sw_handle h, int count, const sw_problem* pr
     return SW_OK;
 }
 
+// Plan construction: a dry run sizes the workspace, the real run fills the plan, whose descriptors
+// are uploaded once.  Growing the workspace flushes cached plans, so callers size every plan they
+// will hold before building any of them.
+using PlanBuilder = std::function<sw_status(bool dry, Plan* plan)>;
+
+static sw_status plan_need(const PlanBuilder& build, size_t* need) {
+    Plan d;
+    sw_status st = build(true, &d);
+    if (st == SW_OK) *need = d.ws_need;
+    return st;
+}
+
+static sw_status plan_make(sw_handle h, const PlanBuilder& build, Plan** out) {
+    Plan* plan = new Plan();
+    sw_status st = build(false, plan);
+    if (st != SW_OK) { delete plan; return st; }
+    if (!plan->blob.empty()) {
+        if (cudaMalloc(&plan->d_blob, plan->blob.size()) != cudaSuccess) {
+            cudaGetLastError();
+            delete plan;
+            return fail(h, SW_ENOMEM, "descriptor allocation failed");
+        }
+        cudaMemcpy(plan->d_blob, plan->blob.data(), plan->blob.size(), cudaMemcpyHostToDevice);
+    }
+    *out = plan;
+    return SW_OK;
+}
+
+static void plan_cache(sw_handle h, const std::string& key, Plan* plan) {
+    if (h->plans.size() >= 256) flush_plans(h);
+    h->plans[key] = plan;
+}
+
+static sw_status cached_plan(sw_handle h, const std::string& key, const PlanBuilder& build, Plan** out) {
+    auto it = h->plans.find(key);
+    if (it != h->plans.end()) { *out = it->second; return SW_OK; }
+    size_t need = 0;
+    sw_status st = plan_need(build, &need);
+    if (st != SW_OK) return st;
+    st = ensure_ws(h, need);
+    if (st != SW_OK) return st;
+    st = plan_make(h, build, out);
+    if (st != SW_OK) return st;
+    plan_cache(h, key, *out);
+    return SW_OK;
+}
+
+// Device time of one run of a plan on `s` (after one untimed run), with the error word checked.
+static sw_status time_plan(sw_handle h, Plan* plan, cudaStream_t s, double* ms) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return cuda_fail(h, cudaGetLastError(), "tuning events");
+    }
+    sw_status st = run_plan(h, plan, s);
+    if (st == SW_OK) {
+        cudaEventRecord(e0, s);
+        st = run_plan(h, plan, s);
+        cudaEventRecord(e1, s);
+    }
+    cudaError_t e = cudaEventSynchronize(e1);
+    float t = 0.f;
+    if (st == SW_OK && e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != SW_OK) return st;
+    if (e != cudaSuccess) return cuda_fail(h, e, "tuning run");
+    int code = 0;
+    e = cudaMemcpy(&code, h->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(h, e, "error word read");
+    if (code != 0) {
+        cudaMemset(h->d_err, 0, sizeof(int));
+        flush_plans(h);
+        return fail(h, SW_ETIMEOUT, "bounded device wait expired while tuning (code " + std::to_string(code) + ")");
+    }
+    *ms = t;
+    return SW_OK;
+}
+
+// Autotuner: time every candidate (each a builder for one configuration) on the caller's operands,
+// keep the fastest plan under `key`, forget the others.  Returns the winner's index.
+static sw_status tune(sw_handle h, const std::string& key, const std::vector<PlanBuilder>& cands, cudaStream_t s,
+                      int* best, double* best_ms) {
+    size_t need = 0;
+    std::vector<char> ok(cands.size(), 0);
+    for (size_t i = 0; i < cands.size(); ++i) {
+        size_t b = 0;
+        if (plan_need(cands[i], &b) == SW_OK) { ok[i] = 1; need = std::max(need, b); }
+    }
+    sw_status st = ensure_ws(h, need);  // sized for every candidate: no flush while tuning
+    if (st != SW_OK) return st;
+    Plan* keep = nullptr;
+    *best = -1;
+    for (size_t i = 0; i < cands.size(); ++i) {
+        if (!ok[i]) continue;
+        Plan* p = nullptr;
+        if (plan_make(h, cands[i], &p) != SW_OK) continue;
+        double t = 0.0;
+        st = time_plan(h, p, s, &t);
+        if (st != SW_OK) { delete p; delete keep; return st; }
+        if (*best < 0 || t < *best_ms) {
+            delete keep;
+            keep = p;
+            *best = (int)i;
+            *best_ms = t;
+        } else {
+            delete p;
+        }
+    }
+    if (!keep) return fail(h, SW_EUNSUPPORTED, "no tuning candidate could be planned");
+    plan_cache(h, key, keep);
+    return SW_OK;
+}
+
+static bool capturing(cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    return cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone;
+}
+
 static sw_status do_mm(sw_handle h, int eb, const void* A, int lda, const void* B, int ldb, void* C, int ldc, int m,
                        int n, int k, int cutoff, uint32_t variant, void* stream) {
     if (!h) return SW_EINVAL;
@@ -1407,34 +1540,63 @@ static sw_status do_mm(sw_handle h, int eb, const void* A, int lda, const void* 
         return fail(h, SW_EINVAL, "leading dimension smaller than the row length");
     std::lock_guard<std::mutex> lock(h->mu);
     cudaSetDevice(h->device);
-    char key[256];
-    snprintf(key, sizeof(key), "%d|%p|%d|%p|%d|%p|%d|%d|%d|%d|%d|%u", eb, A, lda, B, ldb, C, ldc, m, n, k, cutoff,
-             variant);
-    auto it = h->plans.find(key);
-    Plan* plan = nullptr;
-    if (it != h->plans.end()) {
-        plan = it->second;
-    } else {
-        Plan dryp;
-        sw_status st = build_plan(h, eb, A, lda, B, ldb, C, ldc, m, n, k, cutoff, variant, true, &dryp);
-        if (st != SW_OK) return st;
-        st = ensure_ws(h, dryp.ws_need);
-        if (st != SW_OK) return st;
-        plan = new Plan();
-        st = build_plan(h, eb, A, lda, B, ldb, C, ldc, m, n, k, cutoff, variant, false, plan);
-        if (st != SW_OK) { delete plan; return st; }
-        if (!plan->blob.empty()) {
-            if (cudaMalloc(&plan->d_blob, plan->blob.size()) != cudaSuccess) {
-                cudaGetLastError();
-                delete plan;
-                return fail(h, SW_ENOMEM, "descriptor allocation failed");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    auto builder = [=](int c) {
+        return PlanBuilder([=](bool dry, Plan* p) {
+            return build_plan(h, eb, A, lda, B, ldb, C, ldc, m, n, k, c, variant, dry, p);
+        });
+    };
+    auto key_of = [&](int c) {
+        char key[256];
+        snprintf(key, sizeof(key), "%d|%p|%d|%p|%d|%p|%d|%d|%d|%d|%d|%u", eb, A, lda, B, ldb, C, ldc, m, n, k, c,
+                 variant);
+        return std::string(key);
+    };
+    // cutoff <= 0: the autotuner picks the depth on the first call for this shape and variant (not
+    // under stream capture, and not for IN_PLACE, whose runs overwrite A and B)
+    const uint32_t algo = variant & SW_ALGO_MASK, sched = variant & SW_SCHED_MASK;
+    if (cutoff <= 0 && algo != SW_ALGO_NAIVE && sched != SW_SCHED_IN_PLACE && !capturing(s) && m && n && k) {
+        char sig[160];
+        const int align = (int)((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B) |
+                                 reinterpret_cast<uintptr_t>(C)) & 15) | (((lda | ldb | ldc) & 3) << 4);
+        snprintf(sig, sizeof(sig), "M|%d|%d|%d|%d|%u|%d", eb, m, n, k, variant, align);
+        auto t = h->tuned.find(sig);
+        if (t != h->tuned.end()) {
+            cutoff = t->second.cutoff;
+        } else {
+            // depths whose leaves stay large enough to keep the leaf kernels efficient
+            const bool tc = eb == 4;
+            const int leaf_min = tc ? 1024 : 128, lmax = sched == SW_SCHED_FUSED ? (tc ? 2 : 3) : 2;
+            const int dmin = std::min(m, std::min(n, k));
+            std::vector<int> cuts;
+            for (int L = 0; L <= lmax && (dmin >> L) >= leaf_min; ++L) cuts.push_back((int)ceil_div(dmin, 1LL << L));
+            if (cuts.size() >= 2) {
+                std::vector<PlanBuilder> cands;
+                for (int c : cuts) cands.push_back(builder(c));
+                int best = -1;
+                double ms = 0.0;
+                sw_status st = tune(h, key_of(cuts[0]) + "|tuning", cands, s, &best, &ms);
+                if (st != SW_OK) return st;
+                // the winner's plan goes under its own key; it runs once more below, so C holds
+                // exactly its result
+                Plan* p = h->plans[key_of(cuts[0]) + "|tuning"];
+                h->plans.erase(key_of(cuts[0]) + "|tuning");
+                cutoff = cuts[best];
+                plan_cache(h, key_of(cutoff), p);
+                sw_handle_s::Tune tr;
+                tr.cutoff = cutoff;
+                tr.candidates = (int)cuts.size();
+                tr.ms = ms;
+                h->tuned[sig] = tr;
+                h->last_tune = tr;
+                h->has_tune = true;
             }
-            cudaMemcpy(plan->d_blob, plan->blob.data(), plan->blob.size(), cudaMemcpyHostToDevice);
         }
-        if (h->plans.size() >= 256) flush_plans(h);
-        h->plans[key] = plan;
     }
-    return execute(h, plan, static_cast<cudaStream_t>(stream));
+    Plan* plan = nullptr;
+    sw_status st = cached_plan(h, key_of(cutoff), builder(cutoff), &plan);
+    if (st != SW_OK) return st;
+    return execute(h, plan, s);
 }
 
 // ====================================================================== serving loop
@@ -2052,34 +2214,68 @@ sw_status sw_mm_batched(sw_handle h, int count, const sw_problem* probs, int cut
     if (count == 0) return SW_OK;
     std::lock_guard<std::mutex> lock(h->mu);
     cudaSetDevice(h->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
     // plan key: the problem list's bytes
     std::string key = "B|" + std::to_string(count) + "|" + std::to_string(cutoff) + "|" + std::to_string(variant) + "|";
     key.append(reinterpret_cast<const char*>(probs), sizeof(sw_problem) * (size_t)count);
-    auto it = h->plans.find(key);
-    Plan* plan = nullptr;
-    if (it != h->plans.end()) {
-        plan = it->second;
-    } else {
-        Plan dryp;
-        sw_status st = build_batched_plan(h, count, probs, cutoff, variant, true, &dryp);
-        if (st != SW_OK) return st;
-        st = ensure_ws(h, dryp.ws_need);
-        if (st != SW_OK) return st;
-        plan = new Plan();
-        st = build_batched_plan(h, count, probs, cutoff, variant, false, plan);
-        if (st != SW_OK) { delete plan; return st; }
-        if (!plan->blob.empty()) {
-            if (cudaMalloc(&plan->d_blob, plan->blob.size()) != cudaSuccess) {
-                cudaGetLastError();
-                delete plan;
-                return fail(h, SW_ENOMEM, "descriptor allocation failed");
-            }
-            cudaMemcpy(plan->d_blob, plan->blob.data(), plan->blob.size(), cudaMemcpyHostToDevice);
+    struct Cfg { int bn, pair, cutoff; };
+    auto builder = [=](Cfg c) {
+        return PlanBuilder([=](bool dry, Plan* p) {
+            return build_batched_plan(h, count, probs, c.cutoff, variant, dry, p, c.bn, c.pair != 0);
+        });
+    };
+    auto key_of = [&](Cfg c) {
+        return key + "|" + std::to_string(c.bn) + "|" + std::to_string(c.pair) + "|" + std::to_string(c.cutoff);
+    };
+    Cfg cfg = {256, 0, cutoff};
+    // cutoff <= 0: the autotuner times the grouped launch's tile shape (128- or 256-wide tiles on one
+    // CTA, 256 x 256 tiles on CTA pairs) and the recursion cutoff on this problem list, once
+    if (cutoff <= 0 && !capturing(s)) {
+        auto t = h->tuned.find(key);
+        if (t != h->tuned.end()) {
+            cfg = {t->second.bn, t->second.pair, t->second.cutoff};
+        } else {
+            static const bool bt_env = getenv("SWMM_TF32_BT") != nullptr;  // pairs need N-major B
+            const int none = 1 << 30;                                       // no recursion
+            std::vector<Cfg> cs = {{256, 0, none}, {128, 0, none}};
+            if (!bt_env) { cs.push_back({256, 1, none}); cs.push_back({256, 1, 2048}); }
+            std::vector<PlanBuilder> cands;
+            for (const Cfg& c : cs) cands.push_back(builder(c));
+            int best = -1;
+            double ms = 0.0;
+            sw_status st = tune(h, key + "|tuning", cands, s, &best, &ms);
+            if (st != SW_OK) return st;
+            cfg = cs[best];
+            Plan* p = h->plans[key + "|tuning"];
+            h->plans.erase(key + "|tuning");
+            plan_cache(h, key_of(cfg), p);
+            sw_handle_s::Tune tr;
+            tr.cutoff = cfg.cutoff;
+            tr.bn = cfg.bn;
+            tr.pair = cfg.pair;
+            tr.candidates = (int)cs.size();
+            tr.ms = ms;
+            h->tuned[key] = tr;
+            h->last_tune = tr;
+            h->has_tune = true;
         }
-        if (h->plans.size() >= 256) flush_plans(h);
-        h->plans[key] = plan;
     }
-    return execute(h, plan, static_cast<cudaStream_t>(stream));
+    Plan* plan = nullptr;
+    sw_status st = cached_plan(h, key_of(cfg), builder(cfg), &plan);
+    if (st != SW_OK) return st;
+    return execute(h, plan, s);
+}
+
+sw_status sw_last_tuning(sw_handle h, int* cutoff, int* tile_n, int* cta_pair, double* ms, int* candidates) {
+    if (!h) return SW_EINVAL;
+    std::lock_guard<std::mutex> lock(h->mu);
+    if (!h->has_tune) return fail(h, SW_EINVAL, "nothing tuned on this handle yet");
+    if (cutoff) *cutoff = h->last_tune.cutoff;
+    if (tile_n) *tile_n = h->last_tune.bn;
+    if (cta_pair) *cta_pair = h->last_tune.pair;
+    if (ms) *ms = h->last_tune.ms;
+    if (candidates) *candidates = h->last_tune.candidates;
+    return SW_OK;
 }
 
 sw_status sw_smm_host(sw_handle h, const float* A, int lda, const float* B, int ldb, float* C, int ldc, int m, int n,

@@ -82,6 +82,7 @@ def load(build_if_missing: bool = False):
     lib.sw_mm_batched.restype = _I
     lib.sw_profile.argtypes = [_V, _I]
     lib.sw_profile_read.argtypes = [_V, _I, _P(_I), _P(ctypes.c_double)]
+    lib.sw_last_tuning.argtypes = [_V, _P(_I), _P(_I), _P(_I), _P(ctypes.c_double), _P(_I)]
     lib.sw_server_start.argtypes = [_V, _P(sw_server_cfg)]
     lib.sw_server_submit.argtypes = [_V, _P(sw_request), _P(ctypes.c_uint64)]
     lib.sw_server_wait.argtypes = [_V, ctypes.c_uint64, ctypes.c_int64]
@@ -168,6 +169,15 @@ def sw_profile_read(h):
     ms = (ctypes.c_double * n)()
     st = load().sw_profile_read(h, n, launches, ms)
     return st, {PROFILE_KINDS[i]: (launches[i], ms[i]) for i in range(n)}
+
+
+def sw_last_tuning(h):
+    """(status, {"cutoff", "tile_n", "cta_pair", "ms", "candidates"}) of the autotuner's last decision."""
+    c, t, pr, nc = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    ms = ctypes.c_double()
+    st = load().sw_last_tuning(h, ctypes.byref(c), ctypes.byref(t), ctypes.byref(pr), ctypes.byref(ms),
+                               ctypes.byref(nc))
+    return st, {"cutoff": c.value, "tile_n": t.value, "cta_pair": pr.value, "ms": ms.value, "candidates": nc.value}
 
 
 def sw_server_start(h, cfg: sw_server_cfg | None = None) -> int:

@@ -95,6 +95,10 @@ def test_batched_512_uneven_products(h):
         keep.append((dA, dB, dC))
     arr = (swmm.sw_problem * len(probs))(*probs)
     run_batch(h, arr, 0)
+    # the first call with cutoff 0 timed the grouped launch's shapes and cutoffs on this list
+    st, t = swmm.sw_last_tuning(h)
+    assert st == swmm.SW_OK
+    assert t["candidates"] == 4 and t["tile_n"] in (128, 256) and t["cta_pair"] in (0, 1) and t["ms"] > 0, t
     rng = np.random.Generator(np.random.PCG64(3))
     worst = 0.0
     for i, ((dA, dB, dC), (m, n, k)) in enumerate(zip(keep, shapes)):

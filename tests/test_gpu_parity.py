@@ -344,3 +344,24 @@ def test_ragged_leaf_widths_do_not_spill_into_neighbours(h, sched):
         A, B = inputs.pair(n, n, n, "int", seed=75, dtype=np.float64, lim=2)
         C = run(h, A, B, cutoff, W | sched | BF)
         assert np.array_equal(C, oracle.naive(A, B)), (n, sched)
+
+
+# ------------------------------------------------------------------ autotuner (cutoff <= 0)
+def test_autotuned_depth_is_timed_exact_and_reused(h):
+    # n = 4096: depths 0, 1, 2 keep TF32 leaves of >= 1024, so the first call times three plans;
+    # integers in [-1, 1] keep every partial sum an exact integer at all three depths
+    n = 4096
+    assert exact_int_safe(1, n, 2)
+    A, B = inputs.pair(n, n, n, "int", seed=5, dtype=np.float32, lim=1)
+    R = A.astype(np.float64) @ B.astype(np.float64)  # integer sums below 2^53: exact in FP64
+    v = W | FUSED
+    C = run(h, A, B, 0, v)
+    assert np.array_equal(C, R)
+    st, t = swmm.sw_last_tuning(h)
+    assert st == swmm.SW_OK
+    assert t["candidates"] == 3 and t["cutoff"] in (4096, 2048, 1024) and t["ms"] > 0, t
+    # the decision is kept: a second call plans nothing new and gives the same bits
+    C2 = run(h, A, B, 0, v)
+    assert np.array_equal(C2, R)
+    st, t2 = swmm.sw_last_tuning(h)
+    assert st == swmm.SW_OK and t2 == t
