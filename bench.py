@@ -44,7 +44,8 @@ def parse():
     p.add_argument("--n", type=int, default=8192)
     p.add_argument("--algo", choices=["winograd", "strassen", "naive"], default="winograd")
     p.add_argument("--sched", choices=["fused", "two_temp", "in_place", "alloc"], default="fused")
-    p.add_argument("--cutoff", type=int, default=0, help="recursion cutoff; 0 = the library's choice")
+    p.add_argument("--cutoff", type=int, default=None,
+                   help="recursion cutoff (default n / 2: one level); 0 = the library's autotuner")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-oracle sample budget")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-batched", action="store_true")
@@ -130,6 +131,20 @@ def traffic_from_profiles(kernel_file: str, workload: str):
     if not m or not t or m.group(1) != sha:
         return None
     return float(t.group(1))
+
+
+def replica_throughput(times_ms, units_per_rank: float, dist=None, device=None):
+    """Whole-job throughput of independent replicas: every rank's timed region is reduced to the
+    slowest rank's (max over ranks), and the units all ranks processed are divided by that time.
+    Returns (max times in ms, units per second for each time)."""
+    import torch
+    t = torch.tensor([float(x) for x in times_ms], dtype=torch.float64, device=device)
+    world = 1
+    if dist is not None and dist.is_initialized():
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        world = dist.get_world_size()
+    mx = [float(x) for x in t.cpu()]
+    return mx, [units_per_rank * world / (x / 1e3) for x in mx]
 
 
 def leaf_flops(n: int, L: int) -> float:
@@ -307,6 +322,8 @@ def main():
     sched = {"fused": swmm.SW_SCHED_FUSED, "two_temp": swmm.SW_SCHED_TWO_TEMP, "in_place": swmm.SW_SCHED_IN_PLACE,
              "alloc": swmm.SW_SCHED_ALLOC}[args.sched]
     variant = algo | sched | swmm.SW_LEAF_TF32
+    if args.cutoff is None:
+        args.cutoff = n // 2
     st, L = swmm.sw_mm_depth(n, n, n, args.cutoff, variant, 4)
     swmm.check(h, st)
 
@@ -390,13 +407,9 @@ def main():
     # so this pass is kept out of the headline)
     Kp = max(K // 4, 10)
     _, _, _, prof = timed(variant, args.cutoff, Kp, W, profile=True)
-    if dist:
-        t = torch.tensor([total, total0], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total, total0 = float(t[0]), float(t[1])
     flop = 2.0 * n ** 3
-    value = flop * K * world / (total / 1e3) / 1e12
-    value0 = flop * K * world / (total0 / 1e3) / 1e12
+    (total, total0), (rate, rate0) = replica_throughput([total, total0], flop * K, dist, device="cuda")
+    value, value0 = rate / 1e12, rate0 / 1e12
 
     # dominant kernel: the grouped TF32 leaf GEMM
     gl, gms = prof["gemm_tf32"]
@@ -449,9 +462,11 @@ def main():
         swmm.check(h, swmm.sw_sync(h, sp))
         tb = e0.elapsed_time(e1) / kb
         fl = sum(2.0 * m * nn * k for (m, nn, k) in shapes)
+        _, btune = swmm.sw_last_tuning(h)
         batched = {"value": fl / (tb / 1e3) / 1e12, "unit": "TFLOP/s", "ms_per_step": tb, "problems": len(shapes),
                    "workload": "512 FP32 products, m,n,k log-uniform [96,3000], uniform[-1,1], one grouped "
-                               "launch (CUDA graph replay), depth by the tuned cutoff"}
+                               "launch (CUDA graph replay), tile shape and cutoff chosen by the autotuner",
+                   "autotuner": btune}
         del keep
 
     serving = None
@@ -536,7 +551,15 @@ def main():
                         ("in_place", swmm.SW_SCHED_IN_PLACE), ("fused", swmm.SW_SCHED_FUSED)):
             st_, b_ = swmm.sw_mm_workspace_size(16384, 16384, 16384, 4096, swmm.SW_ALGO_WINOGRAD | sc | BF, 4)
             ws[lab] = b_ if st_ == swmm.SW_OK else None
-        extra = {"depth_sweep_n8192_tf32": depth_rows, "split_bf16_n8192": bf_rows,
+        # the autotuner's own pick for this product (cutoff 0: candidate depths timed on first use)
+        product(swmm.SW_ALGO_WINOGRAD | swmm.SW_SCHED_FUSED, 0)
+        swmm.check(h, swmm.sw_sync(h, sp))
+        _, tune = swmm.sw_last_tuning(h)
+        tot, _, _, _ = timed(swmm.SW_ALGO_WINOGRAD | swmm.SW_SCHED_FUSED, 0, ks, W)
+        tuned = {"cutoff": tune["cutoff"], "depth": swmm.sw_mm_depth(n, n, n, tune["cutoff"], variant, 4)[1],
+                 "candidates": tune["candidates"], "ms": tot / ks, "eff_tflops": flop / (tot / ks / 1e3) / 1e12}
+        extra = {"autotuned_winograd_n8192": tuned,
+                 "depth_sweep_n8192_tf32": depth_rows, "split_bf16_n8192": bf_rows,
                  "n16384_tf32": big,
                  "workspace_bytes_n16384_L2_bf16x3": ws,
                  "err_metric": "max|C - C_oracle| / (n max|A| max|B|) on the sampled oracle rows"}
