@@ -42,7 +42,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--n", type=int, default=8192)
-    p.add_argument("--algo", choices=["winograd", "strassen", "naive"], default="winograd")
+    p.add_argument("--algo", choices=["winograd", "knuth", "strassen", "naive"], default="winograd")
     p.add_argument("--sched", choices=["fused", "two_temp", "in_place", "alloc"], default="fused")
     p.add_argument("--cutoff", type=int, default=None,
                    help="recursion cutoff (default n / 2: one level); 0 = the library's autotuner")
@@ -318,7 +318,8 @@ def main():
     stream = torch.cuda.current_stream()
     sp = swmm._stream_ptr(stream)
     n = args.n
-    algo = {"winograd": swmm.SW_ALGO_WINOGRAD, "strassen": swmm.SW_ALGO_STRASSEN, "naive": swmm.SW_ALGO_NAIVE}[args.algo]
+    algo = {"winograd": swmm.SW_ALGO_WINOGRAD, "knuth": swmm.SW_ALGO_WINOGRAD_KNUTH, "strassen": swmm.SW_ALGO_STRASSEN,
+            "naive": swmm.SW_ALGO_NAIVE}[args.algo]
     sched = {"fused": swmm.SW_SCHED_FUSED, "two_temp": swmm.SW_SCHED_TWO_TEMP, "in_place": swmm.SW_SCHED_IN_PLACE,
              "alloc": swmm.SW_SCHED_ALLOC}[args.sched]
     variant = algo | sched | swmm.SW_LEAF_TF32
@@ -512,7 +513,8 @@ def main():
         depth_rows = []
         for lab, v, c in [("plain L0", swmm.SW_ALGO_NAIVE, 0)] + [
                 (f"winograd L{l}", swmm.SW_ALGO_WINOGRAD | swmm.SW_SCHED_FUSED, n >> l) for l in (1, 2, 3)] + [
-                (f"strassen L{l}", swmm.SW_ALGO_STRASSEN | swmm.SW_SCHED_FUSED, n >> l) for l in (1, 2)]:
+                (f"strassen L{l}", swmm.SW_ALGO_STRASSEN | swmm.SW_SCHED_FUSED, n >> l) for l in (1, 2)] + [
+                (f"winograd-knuth L{l}", swmm.SW_ALGO_WINOGRAD_KNUTH | swmm.SW_SCHED_FUSED, n >> l) for l in (1, 2)]:
             tot, _, _, _ = timed(v, c, ks, W)
             depth_rows.append({"variant": lab, "ms": tot / ks, "eff_tflops": flop / (tot / ks / 1e3) / 1e12,
                                "err": row_err(v, c)})

@@ -20,6 +20,10 @@
  *   algorithm   SW_ALGO_NAIVE     plain product (Alg. 1) as one tiled tensor-core GEMM
  *               SW_ALGO_STRASSEN  Strassen's 7 products and 18 additions (Sec. 2.2, Alg. 2)
  *               SW_ALGO_WINOGRAD  Strassen-Winograd, the 22-operation BDPZ form (Sec. 2.3, Alg. 3)
+ *               SW_ALGO_WINOGRAD_KNUTH  Strassen-Winograd in Knuth's form (Sec. 2.3: u, v, w with
+ *                                 aA, bB, (a+b-c-d)D, d(B+C-A-D)), the form the paper implemented;
+ *                                 the same seven products, operand sums grouped as Knuth writes
+ *                                 them (FUSED schedule only)
  *   schedule    SW_SCHED_FUSED    all levels' operand sums in one pass; the 7^L leaf products in
  *                                 one grouped launch whose epilogue adds +-P into the C blocks
  *               SW_SCHED_TWO_TEMP Table 2 ("Two Temp Winograd", Sec. 3.3): two temporaries X, Y
@@ -72,6 +76,7 @@ typedef enum {
 #define SW_ALGO_NAIVE 0x0u
 #define SW_ALGO_STRASSEN 0x1u
 #define SW_ALGO_WINOGRAD 0x2u
+#define SW_ALGO_WINOGRAD_KNUTH 0x3u
 #define SW_ALGO_MASK 0xFu
 #define SW_SCHED_FUSED 0x00u
 #define SW_SCHED_TWO_TEMP 0x10u

@@ -750,7 +750,23 @@ struct Planner {
              {{0, -1}, {1, 1}},
              {{3, 1}},
              {{0, 1}}}};
-        return algo == SW_ALGO_STRASSEN ? str : win;
+        // Winograd in Knuth's form (Sec. 2.3), a, b, c, d = A11, A12, A21, A22 and A, C, B, D =
+        // B11, B12, B21, B22: products aA, bB, (a+b-c-d)D, d(B+C-A-D), v = (c+d)(C-A),
+        // (c+d-a)(A+D-C) (w = aA + this), u = (c-a)(C-D); C11 = aA+bB, C12 = w+v+(a+b-c-d)D,
+        // C21 = w+u+d(B+C-A-D), C22 = w+u+v.  The same seven products as BDPZ up to the sign of the
+        // fourth; its operand sums are grouped as Knuth writes them.
+        static const ProdTab knuth = {
+            {0, 1, -1, 3, -1, -1, -1},
+            {0, 2, 3, -1, -1, -1, -1},
+            {4, 1, 1, 1, 2, 3, 2},
+            {{{0, 1}, {1, 1}, {2, 1}, {3, 1}},
+             {{0, 1}},
+             {{1, 1}},
+             {{2, 1}},
+             {{1, 1}, {3, 1}},
+             {{1, 1}, {2, 1}, {3, 1}},
+             {{2, 1}, {3, 1}}}};
+        return algo == SW_ALGO_STRASSEN ? str : algo == SW_ALGO_WINOGRAD_KNUTH ? knuth : win;
     }
 
     // FUSED plan for C (m x n) <- A (m x k) B (k x n) at depth L (1..3).  `B` is in bt storage
@@ -813,7 +829,7 @@ struct Planner {
             PreaddArgs& p = o.pre;
             memset(&p, 0, sizeof(p));
             p.x = A.p; p.ldx = A.ld; p.rows = m; p.cols = k; p.brows = mb; p.bcols = kb;
-            p.out = SA.p; p.L = L; p.alg = algo == SW_ALGO_STRASSEN ? 1 : 2; p.bside = 0; p.bt = 0;
+            p.out = SA.p; p.L = L; p.alg = algo == SW_ALGO_STRASSEN ? 1 : algo == SW_ALGO_WINOGRAD_KNUTH ? 3 : 2; p.bside = 0; p.bt = 0;
             for (int w = 0; w < 343; ++w) p.slot_of[w] = w < nleaf ? slot_a[w] : (short)-1;
             push(o);
         }
@@ -826,7 +842,7 @@ struct Planner {
             p.x = B.p; p.ldx = B.ld;
             if (bt) { p.rows = n; p.cols = k; p.brows = nb; p.bcols = kb; }
             else { p.rows = k; p.cols = n; p.brows = kb; p.bcols = nb; }
-            p.out = SB.p; p.L = L; p.alg = algo == SW_ALGO_STRASSEN ? 1 : 2; p.bside = 1; p.bt = bt ? 1 : 0;
+            p.out = SB.p; p.L = L; p.alg = algo == SW_ALGO_STRASSEN ? 1 : algo == SW_ALGO_WINOGRAD_KNUTH ? 3 : 2; p.bside = 1; p.bt = bt ? 1 : 0;
             for (int w = 0; w < 343; ++w) p.slot_of[w] = w < nleaf ? slot_b[w] : (short)-1;
             push(o);
         }
@@ -1163,8 +1179,10 @@ static sw_status build_plan(sw_handle h, int eb, const void* A, int lda, const v
                             int m, int n, int k, int cutoff, uint32_t variant, bool dry, Plan* plan,
                             char* ws_base = nullptr, bool server = false) {
     const uint32_t algo = variant & SW_ALGO_MASK, sched = variant & SW_SCHED_MASK, odd = variant & SW_ODD_MASK;
-    if (algo > SW_ALGO_WINOGRAD) return fail(h, SW_EINVAL, "unknown algorithm bits");
+    if (algo > SW_ALGO_WINOGRAD_KNUTH) return fail(h, SW_EINVAL, "unknown algorithm bits");
     if (sched > SW_SCHED_ALLOC) return fail(h, SW_EINVAL, "unknown schedule bits");
+    if (algo == SW_ALGO_WINOGRAD_KNUTH && sched != SW_SCHED_FUSED)
+        return fail(h, SW_EUNSUPPORTED, "Knuth's form runs in the FUSED schedule");
     if ((variant & SW_LEAF_MASK) > SW_LEAF_BF16X3) return fail(h, SW_EINVAL, "unknown leaf bits");
     if (algo == SW_ALGO_STRASSEN && (sched == SW_SCHED_TWO_TEMP || sched == SW_SCHED_IN_PLACE))
         return fail(h, SW_EUNSUPPORTED, "Tables 2 and 3 are Winograd schedules");
@@ -2203,7 +2221,7 @@ sw_status sw_mm_batched(sw_handle h, int count, const sw_problem* probs, int cut
     if (count < 0 || (count > 0 && !probs)) return fail(h, SW_EINVAL, "bad problem list");
     if ((variant & SW_SCHED_MASK) != SW_SCHED_FUSED || (variant & SW_LEAF_MASK) != SW_LEAF_TF32)
         return fail(h, SW_EUNSUPPORTED, "batched products take the FUSED schedule with TF32 leaves");
-    if ((variant & SW_ALGO_MASK) > SW_ALGO_WINOGRAD) return fail(h, SW_EINVAL, "unknown algorithm bits");
+    if ((variant & SW_ALGO_MASK) > SW_ALGO_WINOGRAD_KNUTH) return fail(h, SW_EINVAL, "unknown algorithm bits");
     for (int i = 0; i < count; ++i) {
         const sw_problem& q = probs[i];
         if (q.m < 0 || q.n < 0 || q.k < 0) return fail(h, SW_EINVAL, "negative dimension in problem " + std::to_string(i));

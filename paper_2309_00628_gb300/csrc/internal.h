@@ -81,14 +81,14 @@ cudaError_t launch_copy_pad(int elem_bytes, int rows, int cols, void* z, long lo
 
 // One pass over a 2^L x 2^L grid of blocks of X that writes every non-pure leaf operand sum
 // (all recursion levels at once) into `out` (slot s occupies rows [s*brows, (s+1)*brows),
-// leading dimension bcols).  alg: 1 Strassen, 2 Winograd.  bside: B-side coefficients.
+// leading dimension bcols).  bside: B-side coefficients.
 struct PreaddArgs {
     const void* x;
     long long ldx;
     int rows, cols;      // real extent of X
     int brows, bcols;    // leaf block extent
     void* out;
-    int L, alg, bside;
+    int L, alg, bside;   // alg: 1 Strassen, 2 Winograd (BDPZ), 3 Winograd (Knuth form)
     int bt;              // B side stored as B^T (quadrants 12 and 21 swap roles)
     short slot_of[343];  // leaf word -> output slot, -1 = pure (not written)
 };

@@ -117,9 +117,33 @@ struct Vec {
 // Operand of product p (0..6 = P1..P7) from the four quadrant values of one level.
 // ALG 1: Strassen (Sec. 2.2).  ALG 2: Winograd, BDPZ chains (Sec. 2.3), evaluated in the
 // chain order S1 -> S2 -> S4 and T1 -> T2 -> T4 so the rounding matches the 22-step form.
+// ALG 3: Winograd in Knuth's form (Sec. 2.3), a, b, c, d = X11, X12, X21, X22 on the A side and
+// A, C, B, D = X11, X12, X21, X22 on the B side, each sum grouped left to right as Knuth writes it.
 template <int ALG, bool BSIDE, typename V>
 __device__ __forceinline__ V form(int p, const V& x11, const V& x12, const V& x21, const V& x22) {
-    if (ALG == 2) {
+    if (ALG == 3) {
+        if (!BSIDE) {
+            switch (p) {
+                case 0: return x11;                                    // a
+                case 1: return x12;                                    // b
+                case 2: { V t = x11 + x12; t = t - x21; return t - x22; }  // a + b - c - d
+                case 3: return x22;                                    // d
+                case 4: return x21 + x22;                              // c + d
+                case 5: { V t = x21 + x22; return t - x11; }           // c + d - a
+                default: return x21 - x11;                             // c - a
+            }
+        } else {
+            switch (p) {
+                case 0: return x11;                                    // A
+                case 1: return x21;                                    // B
+                case 2: return x22;                                    // D
+                case 3: { V t = x21 + x12; t = t - x11; return t - x22; }  // B + C - A - D
+                case 4: return x12 - x11;                              // C - A
+                case 5: { V t = x11 + x22; return t - x12; }           // A + D - C
+                default: return x12 - x22;                             // C - D
+            }
+        }
+    } else if (ALG == 2) {
         if (!BSIDE) {
             switch (p) {
                 case 0: return x11;                                    // A11
@@ -256,7 +280,11 @@ __global__ void __launch_bounds__(256) preadd_kernel(const PreaddArgs a) {
 
 template <typename T, int VEC, int L>
 static void preadd_dispatch_alg(const PreaddArgs& a, int grid, cudaStream_t s) {
-    if (a.alg == 2) {
+    if (a.alg == 3) {
+        if (a.bside && a.bt) preadd_kernel<T, VEC, L, 3, true, true><<<grid, 256, 0, s>>>(a);
+        else if (a.bside) preadd_kernel<T, VEC, L, 3, true, false><<<grid, 256, 0, s>>>(a);
+        else preadd_kernel<T, VEC, L, 3, false, false><<<grid, 256, 0, s>>>(a);
+    } else if (a.alg == 2) {
         if (a.bside && a.bt) preadd_kernel<T, VEC, L, 2, true, true><<<grid, 256, 0, s>>>(a);
         else if (a.bside) preadd_kernel<T, VEC, L, 2, true, false><<<grid, 256, 0, s>>>(a);
         else preadd_kernel<T, VEC, L, 2, false, false><<<grid, 256, 0, s>>>(a);

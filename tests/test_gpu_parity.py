@@ -23,7 +23,7 @@ from paper_2309_00628_gb300 import inputs, swmm
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
-W, S = swmm.SW_ALGO_WINOGRAD, swmm.SW_ALGO_STRASSEN
+W, S, K = swmm.SW_ALGO_WINOGRAD, swmm.SW_ALGO_STRASSEN, swmm.SW_ALGO_WINOGRAD_KNUTH
 FUSED, TWO, INPL, ALLOC = swmm.SW_SCHED_FUSED, swmm.SW_SCHED_TWO_TEMP, swmm.SW_SCHED_IN_PLACE, swmm.SW_SCHED_ALLOC
 
 
@@ -119,7 +119,7 @@ def test_degenerate_sizes(h):
 
 
 # ------------------------------------------------------------------ FUSED recursion
-@pytest.mark.parametrize("algo", [W, S])
+@pytest.mark.parametrize("algo", [W, S, K])
 @pytest.mark.parametrize("m,n,k,cutoff", [(256, 256, 256, 128), (256, 256, 256, 64), (384, 384, 384, 32),
                                           (300, 260, 200, 64), (97, 131, 203, 40), (512, 128, 1024, 32),
                                           (1024, 1024, 1024, 256)])
@@ -134,7 +134,7 @@ def test_fused_integers_bit_exact(h, algo, m, n, k, cutoff):
     assert np.array_equal(C, oracle.naive(A, B)), (algo, L)
 
 
-@pytest.mark.parametrize("algo", [W, S])
+@pytest.mark.parametrize("algo", [W, S, K])
 @pytest.mark.parametrize("L", [1, 2, 3])
 def test_fused_float_within_bound(h, algo, L):
     n = 1024
@@ -186,7 +186,8 @@ def test_schedules_float_within_bound(h):
 
 
 # ------------------------------------------------------------------ FP64 path (n = 256, cutoff 32, L = 3)
-CONFIG1 = [(swmm.SW_ALGO_NAIVE, FUSED), (S, FUSED), (S, ALLOC), (W, FUSED), (W, TWO), (W, INPL), (W, ALLOC)]
+CONFIG1 = [(swmm.SW_ALGO_NAIVE, FUSED), (S, FUSED), (S, ALLOC), (W, FUSED), (W, TWO), (W, INPL), (W, ALLOC),
+           (K, FUSED)]
 
 
 @pytest.mark.parametrize("algo,sched", CONFIG1)
@@ -365,3 +366,36 @@ def test_autotuned_depth_is_timed_exact_and_reused(h):
     assert np.array_equal(C2, R)
     st, t2 = swmm.sw_last_tuning(h)
     assert st == swmm.SW_OK and t2 == t
+
+
+# ------------------------------------------------------------------ Knuth's form of Winograd
+def test_knuth_and_bdpz_errors_agree_by_depth(h):
+    # the same seven products with differently grouped operand sums: at every depth both forms
+    # stay within the TF32 bound and within a factor 2 of each other
+    n = 1024
+    A, B = inputs.pair(n, n, n, "uniform", seed=60, dtype=np.float32)
+    R = oracle.naive_mt(A.astype(np.float64), B.astype(np.float64))
+    for L in (1, 2, 3):
+        ew = check_close(run(h, A, B, n >> L, W | FUSED), R, A, B, tol_tf32(n, L))
+        ek = check_close(run(h, A, B, n >> L, K | FUSED), R, A, B, tol_tf32(n, L))
+        assert 0.5 <= ek / ew <= 2.0, (L, ek, ew)
+
+
+def test_knuth_fp64_matches_oracle_knuth_recursion(h):
+    # FP64, n = 256, cutoff 32 (depth 3): the GPU's Knuth form against the oracle's own Knuth
+    # recursion (Sec. 2.3 as written) and the plain product
+    n = 256
+    A, B = inputs.pair(n, n, n, "uniform", seed=61, dtype=np.float64)
+    C = run(h, A, B, 32, K | FUSED, dtype=np.float64)
+    assert oracle.err_norm(C, oracle.recursive(oracle.KNUTH, A, B, 32), A, B) <= 1e-13
+    assert oracle.err_norm(C, oracle.naive(A, B), A, B) <= 1e-13
+
+
+def test_knuth_only_in_fused_schedule(h):
+    A, B = inputs.pair(64, 64, 64, "int", seed=62, dtype=np.float32, lim=2)
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    dC = torch.empty(64, 64, device="cuda")
+    p = lambda t: ctypes.c_void_p(t.data_ptr())
+    for sched in (TWO, INPL, ALLOC):
+        st = swmm.sw_smm(h, p(dA), 64, p(dB), 64, p(dC), 64, 64, 64, 64, 16, K | sched, None)
+        assert st == swmm.SW_EUNSUPPORTED, sched
