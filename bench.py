@@ -543,8 +543,11 @@ def main():
             depth_rows.append({"variant": lab, "ms": tot / ks, "eff_tflops": flop / (tot / ks / 1e3) / 1e12,
                                "err": row_err(v, c)})
         bf_rows = []
+        X3 = swmm.SW_LEAF_TF32X3
         for lab, v, c in (("plain L0", swmm.SW_ALGO_NAIVE | BF, 0),
-                          ("winograd L1", swmm.SW_ALGO_WINOGRAD | swmm.SW_SCHED_FUSED | BF, n >> 1)):
+                          ("winograd L1", swmm.SW_ALGO_WINOGRAD | swmm.SW_SCHED_FUSED | BF, n >> 1),
+                          ("tf32x3 plain L0", swmm.SW_ALGO_NAIVE | X3, 0),
+                          ("tf32x3 winograd L1", swmm.SW_ALGO_WINOGRAD | swmm.SW_SCHED_FUSED | X3, n >> 1)):
             tot, _, _, _ = timed(v, c, ks, W)
             bf_rows.append({"variant": lab, "ms": tot / ks, "eff_tflops": flop / (tot / ks / 1e3) / 1e12,
                             "err": row_err(v, c)})
@@ -585,7 +588,9 @@ def main():
         for lab, v, c in (("plain", swmm.SW_ALGO_NAIVE | BF, 0),
                           ("two_temp L1", swmm.SW_ALGO_WINOGRAD | swmm.SW_SCHED_TWO_TEMP | BF, n2 >> 1),
                           ("two_temp L2", swmm.SW_ALGO_WINOGRAD | swmm.SW_SCHED_TWO_TEMP | BF, n2 >> 2),
-                          ("fused L1", swmm.SW_ALGO_WINOGRAD | swmm.SW_SCHED_FUSED | BF, n2 >> 1)):
+                          ("fused L1", swmm.SW_ALGO_WINOGRAD | swmm.SW_SCHED_FUSED | BF, n2 >> 1),
+                          ("tf32x3 plain", swmm.SW_ALGO_NAIVE | X3, 0),
+                          ("tf32x3 two_temp L1", swmm.SW_ALGO_WINOGRAD | swmm.SW_SCHED_TWO_TEMP | X3, n2 >> 1)):
             for _ in range(2):
                 swmm.check(h, swmm.sw_smm(h, p(A2), n2, p(B2), n2, p(C2), n2, n2, n2, n2, c, v, sp))
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -614,7 +619,7 @@ def main():
         tuned = {"cutoff": tune["cutoff"], "depth": swmm.sw_mm_depth(n, n, n, tune["cutoff"], variant, 4)[1],
                  "candidates": tune["candidates"], "ms": tot / ks, "eff_tflops": flop / (tot / ks / 1e3) / 1e12}
         extra = {"autotuned_winograd_n8192": tuned,
-                 "depth_sweep_n8192_tf32": depth_rows, "split_bf16_n8192": bf_rows,
+                 "depth_sweep_n8192_tf32": depth_rows, "fp32_accuracy_leaves_n8192": bf_rows,
                  "n16384_tf32": big,
                  "fp32_accuracy_n16384_normal_bf16x3": cfg3,
                  "workspace_bytes_n16384_L2_bf16x3": ws,

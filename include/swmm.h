@@ -42,6 +42,11 @@
  *                                 bits), FP32 accumulation
  *               SW_LEAF_BF16X3    FP32 inputs split as hi = bf16(x), lo = bf16(x - hi); products
  *                                 hi*hi + hi*lo + lo*hi with FP32 accumulation (FP32-level accuracy)
+ *               SW_LEAF_TF32X3    FP32 inputs split as hi = tf32(x) (nearest, ties away), lo = x - hi
+ *                                 (FP32, read by the tensor core as TF32); TF32 products
+ *                                 lo*hi + hi*lo + hi*hi with FP32 accumulation: a finer operand
+ *                                 split than SW_LEAF_BF16X3 at half its tensor rate (on uniform
+ *                                 data both reach the FP32-accumulation floor)
  *   The FP64 entry points ignore the leaf group and always use FP64 leaves.
  *
  * Recursion depth L (Sec. 3.4 cutoff): halve while min(ceil(m/2^l), ceil(n/2^l), ceil(k/2^l))
@@ -88,6 +93,7 @@ typedef enum {
 #define SW_ODD_MASK 0xF00u
 #define SW_LEAF_TF32 0x0000u
 #define SW_LEAF_BF16X3 0x1000u
+#define SW_LEAF_TF32X3 0x2000u
 #define SW_LEAF_MASK 0xF000u
 
 typedef struct sw_handle_s *sw_handle;
@@ -233,9 +239,10 @@ sw_status sw_error_norms(sw_handle h, int elem_bytes, int m, int n, int k, const
  * kernel kind, the number of launches and the summed device time in milliseconds since the last
  * read (then resets).  Kinds: 0 tensor-core leaf GEMM (TF32), 1 SIMT leaf GEMM, 2 block addition,
  * 3 padded copy, 4 operand-sum pass, 5 memset, 6 transpose, 7 in-place transpose, 8 bf16 split,
- * 9 tensor-core leaf GEMM (split BF16), 10 batched copy / transpose (sw_mm_batched staging).
- * `nkinds` is the length of both output arrays (entries beyond 11 are set to 0). */
-#define SW_PROFILE_KINDS 11
+ * 9 tensor-core leaf GEMM (split BF16), 10 batched copy / transpose (sw_mm_batched staging),
+ * 11 tf32 split, 12 tensor-core leaf GEMM (compensated TF32).
+ * `nkinds` is the length of both output arrays (entries beyond 13 are set to 0). */
+#define SW_PROFILE_KINDS 13
 sw_status sw_profile(sw_handle h, int enable);
 sw_status sw_profile_read(sw_handle h, int nkinds, int *launches, double *ms);
 

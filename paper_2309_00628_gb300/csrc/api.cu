@@ -119,7 +119,7 @@ inline long long ceil_div(long long x, long long a) { return (x + a - 1) / a; }
 // ------------------------------------------------------------------ plan
 enum OpKind {
     OP_GEMM_TF32, OP_GEMM_SIMT, OP_ADDSUB, OP_COPY_PAD, OP_PREADD, OP_MEMSET, OP_TRANSPOSE, OP_TRANSPOSE_SQ,
-    OP_SPLIT, OP_GEMM_BF16X3, OP_BATCH_COPY
+    OP_SPLIT, OP_GEMM_BF16X3, OP_BATCH_COPY, OP_SPLIT_TF32, OP_GEMM_TF32X3
 };
 
 struct Op {
@@ -176,6 +176,7 @@ struct View {
 struct Planner {
     int eb;                 // 4 = FP32 (TF32 or split-BF16 leaves), 8 = FP64
     bool bf;                // FP32 with split-BF16 leaves
+    bool x3 = false;        // FP32 with compensated-TF32 leaves (FP32 hi / lo halves)
     bool bt;                // B side stored transposed (TF32 leaves read through B^T)
     bool nmaj = false;      // TF32 leaves read B N-major, as stored (bt is then false)
     uint32_t variant;
@@ -197,7 +198,7 @@ struct Planner {
     // and serving launches keep the one-CTA form.  SWMM_NO_PAIR=1 disables it (diagnostics).
     bool pair_ok(int bn) const {
         static const bool off = getenv("SWMM_NO_PAIR") != nullptr;
-        return !off && bn == 256 && !batch && !server && !bf && eb == 4;
+        return !off && bn == 256 && !batch && !server && !bf && !x3 && eb == 4;
     }
     // rows of one B-side TMA box: half the tile width for a CTA pair
     int b_box(int bn) const { return pair_ok(bn) ? bn / 2 : bn; }
@@ -265,15 +266,18 @@ struct Planner {
         return v;
     }
 
-    // FP32 view -> (hi, lo) bf16 halves in workspace
+    // one half of a split operand: bf16 (split-BF16 leaves) or FP32 (compensated TF32)
+    View talloc_half(int rows, int cols) { return x3 ? talloc(rows, cols) : talloc_bf16(rows, cols); }
+
+    // FP32 view -> (hi, lo) halves in workspace
     void split(View x, View& hi, View& lo) {
-        hi = talloc_bf16(x.rows, x.cols);
-        lo = talloc_bf16(x.rows, x.cols);
+        hi = talloc_half(x.rows, x.cols);
+        lo = talloc_half(x.rows, x.cols);
         split_into(x, hi, lo);
     }
     void split_into(View x, const View& hi, const View& lo) {
         Op o;
-        o.kind = OP_SPLIT;
+        o.kind = x3 ? OP_SPLIT_TF32 : OP_SPLIT;
         o.rows = x.rows;
         o.cols = x.cols;
         o.x = x.p;
@@ -429,7 +433,8 @@ struct Planner {
         o.leaves_off = put_blob(leaves.data(), leaves.size() * sizeof(Leaf));
         o.targets_off = put_blob(tg.data(), tg.size() * sizeof(Target));
         // many leaves: a table of every item's leaf replaces the kernel's per-tile binary search
-        if ((o.kind == OP_GEMM_TF32 || o.kind == OP_GEMM_BF16X3) && leaves.size() > 4 && o.items > 0) {
+        if ((o.kind == OP_GEMM_TF32 || o.kind == OP_GEMM_BF16X3 || o.kind == OP_GEMM_TF32X3) && leaves.size() > 4 &&
+            o.items > 0) {
             const long long tm = o.pair ? 2 * tf32_tile_m() : tf32_tile_m();
             std::vector<int> il(o.items, 0);
             for (size_t i = 0; i < leaves.size(); ++i) {
@@ -462,7 +467,7 @@ struct Planner {
             if (dry) return true;
             return simt(a, b, c, mode);
         }
-        if (bf) return gemm_bf16x3(a, b, c, mode);
+        if (bf || x3) return gemm_split(a, b, c, mode);
         if (dry) return true;
         Target t = make_target(c, 1.f, mode, target_map(c));
         Leaf lf;
@@ -495,9 +500,10 @@ struct Planner {
         return true;
     }
 
-    // Split-BF16 leaf: both operands split into (hi, lo) bf16 halves in workspace (released once
-    // the launch is queued: later ops run after it on the same stream), then one launch.
-    bool gemm_bf16x3(View a, View b, View c, int mode) {
+    // Split leaf (split-BF16 or compensated TF32): both operands split into (hi, lo) halves in
+    // workspace (released once the launch is queued: later ops run after it on the same stream),
+    // then one launch.
+    bool gemm_split(View a, View b, View c, int mode) {
         const size_t mark = ws_top;
         View ah, al, bh, bl;
         split(a, ah, al);
@@ -514,15 +520,21 @@ struct Planner {
             lf.n = c.cols;
             lf.tgt_count = 1;
             Op o;
-            o.kind = OP_GEMM_BF16X3;
+            o.kind = x3 ? OP_GEMM_TF32X3 : OP_GEMM_BF16X3;
             o.bn = bn_override() ? bn_override() : 128;
-            lf.kblocks = (int)ceil_div(a.cols, bf16x3_tile_k());
+            lf.kblocks = (int)ceil_div(a.cols, x3 ? tf32_tile_k() : bf16x3_tile_k());
             lf.tiles_n = (int)ceil_div(c.cols, o.bn);
-            ok = make_map_bf16(&o.maps.m[0], ah.p, ah.rows, ah.cols, ah.ld, tf32_tile_m()) &&
-                 make_map_bf16(&o.maps.m[1], al.p, al.rows, al.cols, al.ld, tf32_tile_m()) &&
-                 make_map_bf16(&o.maps.m[2], bh.p, bh.rows, bh.cols, bh.ld, 64) &&
-                 make_map_bf16(&o.maps.m[3], bl.p, bl.rows, bl.cols, bl.ld, 64);
-            if (!ok) err = "bf16 tensor map encoding failed";
+            if (x3)
+                ok = make_map_f32(&o.maps.m[0], ah.p, ah.rows, ah.cols, ah.ld, 32, tf32_tile_m()) &&
+                     make_map_f32(&o.maps.m[1], al.p, al.rows, al.cols, al.ld, 32, tf32_tile_m()) &&
+                     make_map_f32_n(&o.maps.m[2], bh.p, bh.rows, bh.cols, bh.ld) &&
+                     make_map_f32_n(&o.maps.m[3], bl.p, bl.rows, bl.cols, bl.ld);
+            else
+                ok = make_map_bf16(&o.maps.m[0], ah.p, ah.rows, ah.cols, ah.ld, tf32_tile_m()) &&
+                     make_map_bf16(&o.maps.m[1], al.p, al.rows, al.cols, al.ld, tf32_tile_m()) &&
+                     make_map_bf16(&o.maps.m[2], bh.p, bh.rows, bh.cols, bh.ld, 64) &&
+                     make_map_bf16(&o.maps.m[3], bl.p, bl.rows, bl.cols, bl.ld, 64);
+            if (!ok) err = "split-leaf tensor map encoding failed";
             o.items = (int)(ceil_div(c.rows, tf32_tile_m()) * lf.tiles_n);
             o.nleaves = 1;
             o.leaves_off = put_blob(&lf, sizeof(lf));
@@ -815,11 +827,11 @@ struct Planner {
         (void)mark;
         // split-BF16 leaves: (hi, lo) halves of A, B and the S / T sums (sized in the dry run too)
         View halves[4][2];
-        if (bf) {
+        if (bf || x3) {
             const int hr[4] = {m, k, std::max(SA.rows, 1), std::max(SB.rows, 1)};
             const int hc[4] = {k, n, kb, nb};
             for (int i = 0; i < 4; ++i)
-                for (int j = 0; j < 2; ++j) halves[i][j] = talloc_bf16(hr[i], hc[i]);
+                for (int j = 0; j < 2; ++j) halves[i][j] = talloc_half(hr[i], hc[i]);
         }
         if (dry) return true;
         if (na > 0) {
@@ -855,7 +867,7 @@ struct Planner {
         if (!ordered) memset0(C);
         const int bn_o = eb == 8 ? F64_BN
                                  : force_bn ? force_bn
-                                            : (bn_override() ? bn_override() : (bf || nb <= 128 ? 128 : 256));
+                                            : (bn_override() ? bn_override() : (bf || x3 || nb <= 128 ? 128 : 256));
         std::vector<int> first_writer(1 << (2 * L), -1), flag_base(1 << (2 * L), -1), flag_cols(1 << (2 * L), 0);
         int nflags = 0;
         // leaves and their Kronecker-product targets
@@ -947,9 +959,9 @@ struct Planner {
                 }
         Op o;
         o.items = items;
-        if (bf) {
+        if (bf || x3) {
             // split every operand source once: A, B, and the S / T sums
-            o.kind = OP_GEMM_BF16X3;
+            o.kind = x3 ? OP_GEMM_TF32X3 : OP_GEMM_BF16X3;
             o.bn = bn;
             View srcs[4] = {A, B, SA, SB};
             srcs[0].rows = m; srcs[0].cols = k;
@@ -961,9 +973,18 @@ struct Planner {
                 const View& hi = halves[i][0];
                 const View& lo = halves[i][1];
                 if (srcs[i].rows > 0) split_into(srcs[i], hi, lo);
-                if (!make_map_bf16(&o.maps.m[2 * i], hi.p, hi.rows, hi.cols, hi.ld, box[i]) ||
-                    !make_map_bf16(&o.maps.m[2 * i + 1], lo.p, lo.rows, lo.cols, lo.ld, box[i])) {
-                    err = "bf16 tensor map encoding failed";
+                bool mok;
+                if (x3)  // A side K-major, B side N-major (i odd: B and the T sums)
+                    mok = (i & 1) ? make_map_f32_n(&o.maps.m[2 * i], hi.p, hi.rows, hi.cols, hi.ld) &&
+                                        make_map_f32_n(&o.maps.m[2 * i + 1], lo.p, lo.rows, lo.cols, lo.ld)
+                                  : make_map_f32(&o.maps.m[2 * i], hi.p, hi.rows, hi.cols, hi.ld, 32, tf32_tile_m()) &&
+                                        make_map_f32(&o.maps.m[2 * i + 1], lo.p, lo.rows, lo.cols, lo.ld, 32,
+                                                     tf32_tile_m());
+                else
+                    mok = make_map_bf16(&o.maps.m[2 * i], hi.p, hi.rows, hi.cols, hi.ld, box[i]) &&
+                          make_map_bf16(&o.maps.m[2 * i + 1], lo.p, lo.rows, lo.cols, lo.ld, box[i]);
+                if (!mok) {
+                    err = "split-leaf tensor map encoding failed";
                     return false;
                 }
             }
@@ -1183,16 +1204,20 @@ static sw_status build_plan(sw_handle h, int eb, const void* A, int lda, const v
     if (sched > SW_SCHED_ALLOC) return fail(h, SW_EINVAL, "unknown schedule bits");
     if (algo == SW_ALGO_WINOGRAD_KNUTH && sched != SW_SCHED_FUSED)
         return fail(h, SW_EUNSUPPORTED, "Knuth's form runs in the FUSED schedule");
-    if ((variant & SW_LEAF_MASK) > SW_LEAF_BF16X3) return fail(h, SW_EINVAL, "unknown leaf bits");
+    if ((variant & SW_LEAF_MASK) > SW_LEAF_TF32X3) return fail(h, SW_EINVAL, "unknown leaf bits");
     if (algo == SW_ALGO_STRASSEN && (sched == SW_SCHED_TWO_TEMP || sched == SW_SCHED_IN_PLACE))
         return fail(h, SW_EUNSUPPORTED, "Tables 2 and 3 are Winograd schedules");
     if (sched == SW_SCHED_IN_PLACE && algo != SW_ALGO_NAIVE && !(m == n && n == k))
         return fail(h, SW_EUNSUPPORTED, "in-place schedule needs m == n == k");
 
-    const bool bf = eb == 4 && (variant & SW_LEAF_MASK) == SW_LEAF_BF16X3;
+    // split leaves (split-BF16 or compensated TF32): the split pass reads any layout
+    const bool x3 = eb == 4 && (variant & SW_LEAF_MASK) == SW_LEAF_TF32X3;
+    const bool bf_only = eb == 4 && (variant & SW_LEAF_MASK) == SW_LEAF_BF16X3;
+    const bool bf = bf_only || x3;
     Planner P;
     P.eb = eb;
-    P.bf = bf;
+    P.bf = bf_only;
+    P.x3 = x3;
     // TF32 leaves read B N-major, as stored (no B^T staging), except in serving plans, whose
     // resident GEMM reads B^T; SWMM_TF32_BT=1 selects the B^T form everywhere (diagnostics)
     static const bool bt_env = getenv("SWMM_TF32_BT") != nullptr;
@@ -1342,6 +1367,19 @@ static sw_status run_ops(sw_handle h, Plan* plan, cudaStream_t s, size_t first, 
             case OP_SPLIT:
                 e = launch_split_bf16(o.rows, o.cols, static_cast<const float*>(o.x), o.ldx, o.z,
                                       const_cast<void*>(o.y), o.ldz, s);
+                break;
+            case OP_SPLIT_TF32:
+                e = launch_split_tf32(o.rows, o.cols, static_cast<const float*>(o.x), o.ldx, static_cast<float*>(o.z),
+                                      static_cast<float*>(const_cast<void*>(o.y)), o.ldz, s);
+                break;
+            case OP_GEMM_TF32X3:
+                e = launch_gemm_tf32x3(o.bn, o.maps, nullptr, reinterpret_cast<const Leaf*>(blob + o.leaves_off),
+                                       o.nleaves, reinterpret_cast<const Target*>(blob + o.targets_off),
+                                       o.ntmaps ? reinterpret_cast<const CUtensorMap*>(blob + o.tmaps_off) : nullptr,
+                                       o.nflags ? reinterpret_cast<unsigned*>(blob + o.flags_off) : nullptr,
+                                       o.nflags ? ++o.epoch : 0u, o.items, h->d_err, h->sms, s,
+                                       o.has_item_leaf ? reinterpret_cast<const int*>(blob + o.item_leaf_off)
+                                                       : nullptr);
                 break;
             case OP_GEMM_BF16X3:
                 e = launch_gemm_bf16x3(o.bn, o.maps, nullptr, reinterpret_cast<const Leaf*>(blob + o.leaves_off),

@@ -42,7 +42,9 @@ constexpr int TF_BK = 32;  // TF32 k-block: 32 FP32 = 128 bytes, one swizzle row
 constexpr int TF_GROUP_M = 8;
 // MODE_TF32N: TF32 with B N-major (k x n as stored): B staged in 32-column (128-byte) boxes
 // with the 32-byte-atom 128-byte swizzle, read by the MMA through a layout-type-1 descriptor.
-constexpr int MODE_TF32 = 0, MODE_BF16X3 = 1, MODE_TF32N = 2;
+// MODE_TF32X3: compensated TF32 -- each FP32 operand arrives as (hi, lo) FP32 halves, hi = tf32(x),
+// lo = x - hi; per k-step three MMAs lo*hi + hi*lo + hi*hi (A K-major, B N-major as in TF32N).
+constexpr int MODE_TF32 = 0, MODE_BF16X3 = 1, MODE_TF32N = 2, MODE_TF32X3 = 3;
 constexpr uint32_t SWZ_128B_BASE32B = 1;  // descriptor layout: 128-byte swizzle, 32-byte atoms
 
 // PAIR: the TF32 form for a CTA pair (cta_group::2): one 256 x BN tile per pair, each CTA holding
@@ -51,12 +53,13 @@ constexpr uint32_t SWZ_128B_BASE32B = 1;  // descriptor layout: 128-byte swizzle
 template <int MODE, int BN, bool PAIR = false>
 struct TfCfg {
     static constexpr bool TF = MODE != MODE_BF16X3;                  // a TF32 form
+    static constexpr bool BN_MAJOR32 = MODE == MODE_TF32N || MODE == MODE_TF32X3;  // B N-major, 32-bit
     static constexpr int BK = TF ? 32 : 64;                          // elements per 128-byte row
     static constexpr int TM = PAIR ? 2 * TF_BM : TF_BM;              // tile rows per work item
     static constexpr int B_ROWS = PAIR ? BN / 2 : BN;                // B rows held by one CTA
     static constexpr int A_BYTES = TF_BM * 128;                      // one A tile (16 KB)
     static constexpr int B_BYTES = B_ROWS * 128;                     // one B tile
-    static constexpr int NOPS = TF ? 1 : 2;                          // tiles per operand (hi, lo)
+    static constexpr int NOPS = (MODE == MODE_TF32 || MODE == MODE_TF32N) ? 1 : 2;  // tiles per operand (hi, lo)
     static constexpr int STAGE_BYTES = NOPS * (A_BYTES + B_BYTES);
     static constexpr int STAGES = (4 * 49152) / STAGE_BYTES;         // 192 KB of operand stages
     static constexpr int TMEM_COLS = 2 * BN;
@@ -67,7 +70,7 @@ struct TfCfg {
     // instruction descriptor: D F32; TF32: A/B TF32, both K-major; BF16X3: A/B BF16, A K-major,
     // B MN-major; N = BN, M = 128
     static constexpr uint32_t IDESC =
-        TF ? ((1u << 4) | (2u << 7) | (2u << 10) | (MODE == MODE_TF32N ? (1u << 16) : 0u) |
+        TF ? ((1u << 4) | (2u << 7) | (2u << 10) | (BN_MAJOR32 ? (1u << 16) : 0u) |
               ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24))
             : ((1u << 4) | (1u << 7) | (1u << 10) | (1u << 16) | ((uint32_t)(BN >> 3) << 17) |
                ((uint32_t)(TF_BM >> 4) << 24));
@@ -184,7 +187,7 @@ __global__ void __launch_bounds__(192, 1)
                      const Leaf* __restrict__ leaves, int nleaves, const Target* __restrict__ targets,
                      const CUtensorMap* __restrict__ tmaps, unsigned* __restrict__ flags, unsigned epoch,
                      int total_items, int* err, const ResidentCtl ctl) {
-    static_assert(!PAIR || (MODE != MODE_BF16X3 && !RES), "CTA pairs: TF32, non-resident only");
+    static_assert(!PAIR || ((MODE == MODE_TF32 || MODE == MODE_TF32N) && !RES), "CTA pairs: TF32, non-resident only");
     using Cfg = TfCfg<MODE, BN, PAIR>;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw_addr = smem_u32(smem_raw);
@@ -320,7 +323,7 @@ __global__ void __launch_bounds__(192, 1)
                         tma_load_2d(stage_a(stage, op), ma, &full[stage], a_col + kb * Cfg::BK, a_row);
                         if (MODE == MODE_TF32) {
                             tma_load_2d(stage_b(stage, op), mb, &full[stage], b_col + kb * Cfg::BK, b_row);
-                        } else if (MODE == MODE_TF32N) {
+                        } else if (Cfg::BN_MAJOR32) {
 #pragma unroll
                             for (int c = 0; c < BN / 32; ++c)  // 32 N-columns (128 B) x 32 K-rows per box
                                 tma_load_2d(stage_b(stage, op) + c * 4096, mb, &full[stage], b_col + c * 32,
@@ -377,7 +380,20 @@ __global__ void __launch_bounds__(192, 1)
                 for (int kb = 0; kb < kb_n; ++kb) {
                     if (!mbar_wait(&full[stage], phase, err, ERR_WAIT_FULL)) { ok = false; break; }
                     tc_fence_after();
-                    if (Cfg::TF) {
+                    if (MODE == MODE_TF32X3) {
+                        const uint32_t ah = smem_u32(stage_a(stage, 0)), al = smem_u32(stage_a(stage, 1));
+                        const uint32_t bh = smem_u32(stage_b(stage, 0)), bl = smem_u32(stage_b(stage, 1));
+#pragma unroll
+                        for (int kk = 0; kk < TF_BK / 8; ++kk) {  // K = 8 per MMA
+                            const uint64_t dah = make_sdesc(ah + kk * 32, 16, 1024, SWZ_128B);
+                            const uint64_t dal = make_sdesc(al + kk * 32, 16, 1024, SWZ_128B);
+                            const uint64_t dbh = make_sdesc(bh + kk * 1024, 4096, 512, SWZ_128B_BASE32B);
+                            const uint64_t dbl = make_sdesc(bl + kk * 1024, 4096, 512, SWZ_128B_BASE32B);
+                            mma_tf32(d_tmem, dal, dbh, Cfg::IDESC, (kb | kk) != 0 ? 1u : 0u);  // lo * hi
+                            mma_tf32(d_tmem, dah, dbl, Cfg::IDESC, 1u);                           // hi * lo
+                            mma_tf32(d_tmem, dah, dbh, Cfg::IDESC, 1u);                           // hi * hi
+                        }
+                    } else if (Cfg::TF) {
                         const uint32_t a_addr = smem_u32(stage_a(stage, 0));
                         const uint32_t b_addr = smem_u32(stage_b(stage, 0));
 #pragma unroll
@@ -720,6 +736,16 @@ cudaError_t launch_gemm_tf32n(int bn, const MapSet& maps, const CUtensorMap* gma
                                                total_items, err, grid, stream, nullptr, item_leaf);
     return launch_tc_impl<MODE_TF32N, 128>(maps, gmaps, leaves, nleaves, targets, tmaps, flags, epoch, total_items,
                                            err, grid, stream, nullptr, item_leaf);
+}
+
+cudaError_t launch_gemm_tf32x3(int bn, const MapSet& maps, const CUtensorMap* gmaps, const Leaf* leaves, int nleaves,
+                               const Target* targets, const CUtensorMap* tmaps, unsigned* flags, unsigned epoch,
+                               int total_items, int* err, int grid, cudaStream_t stream, const int* item_leaf) {
+    if (bn == 256)
+        return launch_tc_impl<MODE_TF32X3, 256>(maps, gmaps, leaves, nleaves, targets, tmaps, flags, epoch,
+                                                total_items, err, grid, stream, nullptr, item_leaf);
+    return launch_tc_impl<MODE_TF32X3, 128>(maps, gmaps, leaves, nleaves, targets, tmaps, flags, epoch, total_items,
+                                            err, grid, stream, nullptr, item_leaf);
 }
 
 cudaError_t launch_gemm_bf16x3(int bn, const MapSet& maps, const CUtensorMap* gmaps, const Leaf* leaves, int nleaves,

@@ -55,6 +55,18 @@ cudaError_t launch_gemm_bf16x3(int bn, const MapSet& maps, const CUtensorMap* gm
                                int total_items, int* err, int grid, cudaStream_t stream,
                                const int* item_leaf = nullptr);
 
+// Compensated-TF32 leaves: operand map index i refers to maps 2i (hi) and 2i+1 (lo), FP32 halves
+// with hi = tf32(x), lo = x - hi; A K-major (make_map_f32, 128-row boxes), B N-major
+// (make_map_f32_n); Leaf::kblocks counts 32-deep k blocks.
+cudaError_t launch_gemm_tf32x3(int bn, const MapSet& maps, const CUtensorMap* gmaps, const Leaf* leaves, int nleaves,
+                               const Target* targets, const CUtensorMap* tmaps, unsigned* flags, unsigned epoch,
+                               int total_items, int* err, int grid, cudaStream_t stream,
+                               const int* item_leaf = nullptr);
+// hi = tf32(x) (round to nearest, ties away), lo = x - hi (exact), elementwise on a rows x cols
+// FP32 view; both outputs FP32 with leading dimension ldo.
+cudaError_t launch_split_tf32(int rows, int cols, const float* x, long long ldx, float* hi, float* lo, long long ldo,
+                              cudaStream_t stream);
+
 // hi = bf16(x), lo = bf16(x - hi), elementwise on a rows x cols FP32 view; outputs share ldo.
 cudaError_t launch_split_bf16(int rows, int cols, const float* x, long long ldx, void* hi, void* lo, long long ldo,
                               cudaStream_t stream);

@@ -448,6 +448,56 @@ __global__ void split_bf16x4_kernel(int rows, int cols4, const float4* __restric
     }
 }
 
+// Compensated-TF32 split: hi = tf32(x) rounded to nearest (ties away), lo = x - hi (exact in FP32:
+// the difference has at most 13 significant bits).  Four elements per thread when rows are 16-byte
+// aligned, else one.
+__device__ __forceinline__ float tf32_rna(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+__global__ void split_tf32_kernel(int rows, int cols, const float* __restrict__ x, long long ldx,
+                                  float* __restrict__ hi, float* __restrict__ lo, long long ldo) {
+    const long long total = (long long)rows * cols;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / cols), j = (int)(e - (long long)i * cols);
+        const float v = x[i * ldx + j];
+        const float h = tf32_rna(v);
+        hi[i * ldo + j] = h;
+        lo[i * ldo + j] = v - h;
+    }
+}
+
+__global__ void split_tf32x4_kernel(int rows, int cols4, const float4* __restrict__ x, long long ldx4,
+                                    float4* __restrict__ hi, float4* __restrict__ lo, long long ldo4) {
+    const long long total = (long long)rows * cols4;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / cols4), j = (int)(e - (long long)i * cols4);
+        const float4 v = x[i * ldx4 + j];
+        const float4 h = make_float4(tf32_rna(v.x), tf32_rna(v.y), tf32_rna(v.z), tf32_rna(v.w));
+        hi[i * ldo4 + j] = h;
+        lo[i * ldo4 + j] = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+    }
+}
+
+cudaError_t launch_split_tf32(int rows, int cols, const float* x, long long ldx, float* hi, float* lo, long long ldo,
+                              cudaStream_t s) {
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    if (((cols | ldx | ldo) & 3) == 0 &&
+        ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(hi) | reinterpret_cast<uintptr_t>(lo)) & 15) ==
+            0) {
+        split_tf32x4_kernel<<<grid_for((long long)rows * cols / 4, 256), 256, 0, s>>>(
+            rows, cols / 4, reinterpret_cast<const float4*>(x), ldx / 4, reinterpret_cast<float4*>(hi),
+            reinterpret_cast<float4*>(lo), ldo / 4);
+        return cudaGetLastError();
+    }
+    split_tf32_kernel<<<grid_for((long long)rows * cols, 256), 256, 0, s>>>(rows, cols, x, ldx, hi, lo, ldo);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_split_bf16(int rows, int cols, const float* x, long long ldx, void* hi, void* lo, long long ldo,
                               cudaStream_t s) {
     if (rows <= 0 || cols <= 0) return cudaSuccess;

@@ -399,3 +399,55 @@ def test_knuth_only_in_fused_schedule(h):
     for sched in (TWO, INPL, ALLOC):
         st = swmm.sw_smm(h, p(dA), 64, p(dB), 64, p(dC), 64, 64, 64, 64, 16, K | sched, None)
         assert st == swmm.SW_EUNSUPPORTED, sched
+
+
+# ------------------------------------------------------------------ compensated TF32 leaves (3 TF32 products)
+# hi = tf32(x) (nearest) leaves |x - hi| <= 2^-11 |x|; lo = x - hi is read by the tensor core as
+# TF32 (10 mantissa bits), so hi + lo carries x to 2^-21 relative; the dropped lo*lo term is below
+# 2^-22 |a b|.  Each product term errs by < 2^-19 |a||b|: the Hoeffding argument gives
+# 8 * 2^-19 * 3^L / sqrt(k), plus the same FP32-accumulation floor 2^-20 as the split-BF16 bound.
+X3 = swmm.SW_LEAF_TF32X3
+
+
+def tol_tf32x3(k, L):
+    return 8.0 * 2.0 ** -19 * 3.0 ** L / np.sqrt(k) + 2.0 ** -20
+
+
+@pytest.mark.parametrize("m,n,k", [(128, 128, 64), (300, 500, 200), (1000, 1000, 1000), (129, 257, 33)])
+def test_tf32x3_plain_integers_bit_exact(h, m, n, k):
+    A, B = inputs.pair(m, n, k, "int", seed=80, dtype=np.float64)
+    assert np.array_equal(run(h, A, B, 0, swmm.SW_ALGO_NAIVE | X3), oracle.naive(A, B))
+
+
+def test_tf32x3_plain_float_far_tighter_than_tf32(h):
+    # both compensated forms end at the FP32-accumulation floor of the tensor core (the operand
+    # split of TF32X3 is finer, but it issues two accumulator updates per 16-deep k-step where
+    # split-BF16 issues one): within a factor 4 of each other, and 16x tighter than plain TF32
+    m, n, k = 777, 640, 1500
+    A, B = inputs.pair(m, n, k, "uniform", seed=81, dtype=np.float32)
+    R = oracle.naive(A.astype(np.float64), B.astype(np.float64))
+    e_x3 = check_close(run(h, A, B, 0, swmm.SW_ALGO_NAIVE | X3), R, A, B, tol_tf32x3(k, 0))
+    e_bf = check_close(run(h, A, B, 0, swmm.SW_ALGO_NAIVE | BF), R, A, B, tol_bf16x3(k, 0))
+    e_tf = check_close(run(h, A, B, 0, swmm.SW_ALGO_NAIVE), R, A, B, tol_tf32(k, 0))
+    assert e_x3 < e_tf / 16 and e_x3 < 4 * e_bf, (e_x3, e_bf, e_tf)
+
+
+@pytest.mark.parametrize("algo,sched", [(W, FUSED), (W, TWO), (W, INPL), (W, ALLOC), (S, FUSED), (S, ALLOC),
+                                        (K, FUSED)])
+def test_tf32x3_recursive(h, algo, sched):
+    n, cutoff = 512, 128  # L = 2
+    v = algo | sched | X3
+    L = depth(h, n, n, n, cutoff, v, 4)
+    assert L == 2
+    Ai, Bi = inputs.pair(n, n, n, "int", seed=82, dtype=np.float64, lim=1)
+    assert np.array_equal(run(h, Ai, Bi, cutoff, v), oracle.naive(Ai, Bi))
+    A, B = inputs.pair(n, n, n, "uniform", seed=83, dtype=np.float32)
+    R = oracle.naive(A.astype(np.float64), B.astype(np.float64))
+    check_close(run(h, A, B, cutoff, v), R, A, B, tol_tf32x3(n, L))
+
+
+def test_tf32x3_odd_sizes(h):
+    for m, n, k in [(300, 260, 200), (97, 131, 203)]:
+        A, B = inputs.pair(m, n, k, "int", seed=84, dtype=np.float64, lim=2)
+        for v in (W | FUSED | X3, W | TWO | X3 | swmm.SW_PAD, W | TWO | X3 | swmm.SW_PEEL):
+            assert np.array_equal(run(h, A, B, 40, v), oracle.naive(A, B)), (m, n, k, v)
