@@ -104,6 +104,13 @@ bool make_map_bf16(CUtensorMap* m, const void* base, int rows, int cols, long lo
 
 inline long long round_up(long long x, long long a) { return (x + a - 1) / a * a; }
 
+// SWMM_TF32_BT=1: the TF32 leaves read B as B^T (staged by a transpose) instead of N-major as
+// stored -- a diagnostics switch; the default is N-major everywhere.
+bool tf32_bt_form() {
+    static const bool bt = getenv("SWMM_TF32_BT") != nullptr;
+    return bt;
+}
+
 // Tile-width override for tuning sweeps (SWMM_TF32_BN = 128 or 256); 0 = the planner's choice.
 int bn_override() {
     static int v = -1;
@@ -1218,10 +1225,9 @@ static sw_status build_plan(sw_handle h, int eb, const void* A, int lda, const v
     P.eb = eb;
     P.bf = bf_only;
     P.x3 = x3;
-    // TF32 leaves read B N-major, as stored (no B^T staging), except in serving plans, whose
-    // resident GEMM reads B^T; SWMM_TF32_BT=1 selects the B^T form everywhere (diagnostics)
-    static const bool bt_env = getenv("SWMM_TF32_BT") != nullptr;
-    P.nmaj = eb == 4 && !bf && !server && !bt_env;
+    // TF32 leaves read B N-major, as stored (no B^T staging); SWMM_TF32_BT=1 selects the B^T form
+    // everywhere (diagnostics)
+    P.nmaj = eb == 4 && !bf && !tf32_bt_form();
     P.bt = eb == 4 && !bf && !P.nmaj;
     P.variant = variant;
     P.dry = dry;
@@ -1446,8 +1452,7 @@ static sw_status build_batched_plan(sw_handle h, int count, const sw_problem* pr
     P.batch_pair = pair;
     P.eb = 4;
     P.bf = false;
-    static const bool bt_env = getenv("SWMM_TF32_BT") != nullptr;  // diagnostics: B^T staging
-    P.nmaj = !bt_env;
+    P.nmaj = !tf32_bt_form();
     P.bt = !P.nmaj;
     P.variant = variant;
     P.dry = dry;
@@ -1820,7 +1825,8 @@ struct Server {
 static bool resident_form(const Plan& p) {
     if (p.ops.empty()) return false;
     const Op& o = p.ops.back();
-    return o.kind == OP_GEMM_TF32 && o.bn == 256 && o.nflags == 0 && o.ngmaps == 0 && o.items > 0 &&
+    return o.kind == OP_GEMM_TF32 && o.nmaj == !tf32_bt_form() && !o.pair && o.bn == 256 && o.nflags == 0 &&
+           o.ngmaps == 0 && o.items > 0 &&
            o.nleaves > 0 && (unsigned)o.items <= SRV_MAX_ITEMS / 2 && o.nleaves <= SRV_MAX_LEAVES / 2 &&
            o.ntmaps <= SRV_MAX_TMAPS / 2;
 }
@@ -1972,7 +1978,7 @@ sw_status Server::launch_resident() {
     c.done = done_d();
     c.idle_ns = (unsigned long long)cfg.idle_us * 1000ull;
     cudaError_t e = launch_gemm_tf32_resident(gmaps_d, leaves_d, targets_d, tmaps_d, c, err_d(), cfg.sm_share,
-                                              res_stream);
+                                              res_stream, !tf32_bt_form());
     if (e != cudaSuccess) return SW_ECUDA;
     cudaEventRecord(res_ev, res_stream);
     res_launched = true;
@@ -2291,10 +2297,12 @@ sw_status sw_mm_batched(sw_handle h, int count, const sw_problem* probs, int cut
         if (t != h->tuned.end()) {
             cfg = {t->second.bn, t->second.pair, t->second.cutoff};
         } else {
-            static const bool bt_env = getenv("SWMM_TF32_BT") != nullptr;  // pairs need N-major B
-            const int none = 1 << 30;                                       // no recursion
+            const int none = 1 << 30;  // no recursion
             std::vector<Cfg> cs = {{256, 0, none}, {128, 0, none}};
-            if (!bt_env) { cs.push_back({256, 1, none}); cs.push_back({256, 1, 2048}); }
+            if (!tf32_bt_form()) {     // CTA pairs need N-major B
+                cs.push_back({256, 1, none});
+                cs.push_back({256, 1, 2048});
+            }
             std::vector<PlanBuilder> cands;
             for (const Cfg& c : cs) cands.push_back(builder(c));
             int best = -1;

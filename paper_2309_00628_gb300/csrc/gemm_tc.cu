@@ -703,9 +703,12 @@ static cudaError_t launch_tc_impl(const MapSet& maps, const CUtensorMap* gmaps, 
 
 cudaError_t launch_gemm_tf32_resident(const CUtensorMap* gmaps, const Leaf* leaves, const Target* targets,
                                       const CUtensorMap* tmaps, const ResidentCtl& ctl, int* err, int grid,
-                                      cudaStream_t stream) {
+                                      cudaStream_t stream, bool nmajor) {
     MapSet none;
     memset(&none, 0, sizeof(none));
+    if (nmajor)
+        return launch_tc_impl<MODE_TF32N, 256, true>(none, gmaps, leaves, 0, targets, tmaps, nullptr, 0, 0, err, grid,
+                                                     stream, &ctl);
     return launch_tc_impl<MODE_TF32, 256, true>(none, gmaps, leaves, 0, targets, tmaps, nullptr, 0, 0, err, grid,
                                                 stream, &ctl);
 }

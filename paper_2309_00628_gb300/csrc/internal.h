@@ -40,10 +40,10 @@ cudaError_t launch_gemm_tf32n(int bn, const MapSet& maps, const CUtensorMap* gma
                               int total_items, int* err, int grid, cudaStream_t stream, bool pair = false,
                               const int* item_leaf = nullptr);
 // Resident (serving) form of the TF32 grouped GEMM, BN = 256: runs until ctl.stop, an error, or
-// ctl.idle_ns without newly published items.
+// ctl.idle_ns without newly published items.  nmajor: B maps N-major (as launch_gemm_tf32n), else B^T.
 cudaError_t launch_gemm_tf32_resident(const CUtensorMap* gmaps, const Leaf* leaves, const Target* targets,
                                       const CUtensorMap* tmaps, const ResidentCtl& ctl, int* err, int grid,
-                                      cudaStream_t stream);
+                                      cudaStream_t stream, bool nmajor);
 int tf32_tile_m();
 int tf32_tile_k();
 int bf16x3_tile_k();

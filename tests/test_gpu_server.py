@@ -142,7 +142,7 @@ def test_server_budget_and_timeout(h):
     cfg = swmm.sw_server_cfg(0, 8, 64 << 20, 2000)
     swmm.check(h, swmm.sw_server_start(h, cfg))
     try:
-        # B^T alone needs 256 MiB: more than the arena
+        # the operand sums alone need 512 MiB: more than the arena
         m = n = k = 8192
         big = swmm.sw_request(4, 1 << 20, k, 1 << 20, n, 1 << 20, n, m, n, k, 4096, W | FUSED)
         st, _ = swmm.sw_server_submit(h, big)
