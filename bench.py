@@ -150,6 +150,15 @@ def replica_throughput(times_ms, units_per_rank: float, dist=None, device=None):
     return mx, [units_per_rank * world / (x / 1e3) for x in mx]
 
 
+def workload_config(args, L: int) -> dict:
+    """The bench line's `config`: the same for our arm and the reference (oracle) arm."""
+    n = args.n
+    return {"workload": f"single FP32 product n={n}, uniform[-1,1], {args.algo} {args.sched} "
+                        f"L={L}, TF32 leaves, FP32 accumulation",
+            "n": n, "depth": L, "algo": args.algo, "schedule": args.sched,
+            "l2": "inputs 256 MiB each exceed the 129 MB L2; no flush"}
+
+
 def leaf_flops(n: int, L: int) -> float:
     return 2.0 * (n >> L) ** 3 * 7 ** L
 
@@ -265,6 +274,9 @@ def run_reference(args, rank: int):
         return
     import oracle
     n = args.n
+    if args.cutoff is None:
+        args.cutoff = n // 2
+    L = 0 if args.algo == "naive" else oracle.depth(n, n, n, args.cutoff if args.cutoff > 0 else 8192)
     A, B = inputs.pair(n, n, n, "uniform", seed=0, dtype=np.float32)
     A64, B64 = A.astype(np.float64), B.astype(np.float64)
     threads = oracle.max_threads()
@@ -289,9 +301,10 @@ def run_reference(args, rank: int):
         "value": value, "unit": "TFLOP/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * tot / len(times), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"FP32 product n={n} (uniform[-1,1]); CPU oracle sample", "n": n},
+        "config": workload_config(args, L),
         "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": threads, "kind": "oracle",
-                         "sample": f"{rows} of {n} rows of C = A B per step (Alg. 1, FP64, OpenMP over rows)"},
+                         "sample": f"{rows} of {n} rows of C = A B per step (the FP64 oracle's naive product, "
+                                   f"Alg. 1, OpenMP over rows; the same product in exact arithmetic)"},
         "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -633,10 +646,7 @@ def main():
             "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": K, "warmup": W,
             "ms_per_step": total / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "tf32", "data": "synthetic",
-            "config": {"workload": f"single FP32 product n={n}, uniform[-1,1], {args.algo} {args.sched} "
-                                   f"L={L}, TF32 leaves, FP32 accumulation",
-                       "n": n, "depth": L, "algo": args.algo, "schedule": args.sched,
-                       "l2": "inputs 256 MiB each exceed the 129 MB L2; no flush"},
+            "config": workload_config(args, L),
             "p50_ms": statistics.median(lat), "p99_ms": lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)],
             "plain_gemm": {"value": value0, "unit": "TFLOP/s", "ms_per_step": total0 / K,
                            "p50_ms": statistics.median(per0)},
