@@ -15,6 +15,7 @@
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <cstdio>
 #include <cstdlib>
@@ -136,6 +137,9 @@ struct Op {
     int bn = 256, nleaves = 0, items = 0, ntmaps = 0, nflags = 0;
     bool pair = false;   // TF32: the CTA-pair form (256 x 256 tiles; items count 256-row tiles)
     bool has_item_leaf = false;  // tensor-core GEMM: item -> leaf table at item_leaf_off
+    bool has_layout = false;     // explicit work layout: item_leaf_off (leaf) and item_tile_off (tile)
+    size_t item_tile_off = 0;
+    int units = 0;               // the layout's persistent units
     bool nmaj = false;           // TF32 GEMM reading B N-major (launch_gemm_tf32n)
     size_t item_leaf_off = 0;
     size_t leaves_off = 0, targets_off = 0, refs_off = 0, tmaps_off = 0, flags_off = 0;
@@ -199,6 +203,7 @@ struct Planner {
     bool batch = false;
     bool server = false;  // plan for the serving loop (no ordering counters)
     int force_bn = 0;
+    int sms = 0;              // SMs of the device (explicit work layouts are planned for its units)
     int batch_bn = 256;       // batched launch: tile width of the grouped GEMM (128 or 256)
     bool batch_pair = false;  // batched launch: CTA-pair form (256 x 256 tiles; N-major B only)
     // The CTA-pair TF32 GEMM (cta_group::2) serves single products with 256-wide tiles; batched
@@ -441,7 +446,7 @@ struct Planner {
         o.targets_off = put_blob(tg.data(), tg.size() * sizeof(Target));
         // many leaves: a table of every item's leaf replaces the kernel's per-tile binary search
         if ((o.kind == OP_GEMM_TF32 || o.kind == OP_GEMM_BF16X3 || o.kind == OP_GEMM_TF32X3) && leaves.size() > 4 &&
-            o.items > 0) {
+            o.items > 0 && !o.has_layout) {
             const long long tm = o.pair ? 2 * tf32_tile_m() : tf32_tile_m();
             std::vector<int> il(o.items, 0);
             for (size_t i = 0; i < leaves.size(); ++i) {
@@ -788,6 +793,139 @@ struct Planner {
         return algo == SW_ALGO_STRASSEN ? str : algo == SW_ALGO_WINOGRAD_KNUTH ? knuth : win;
     }
 
+    // ---------------------------------------------------------- accumulation chains (depth 1)
+    // One Winograd level (BDPZ or Knuth's grouping; the same product structure) with the sums
+    // kept in tensor memory: a CTA pair's tile that continues the accumulator of its tile two
+    // items back adds the next product to the running sum, so C receives
+    //   [P1 -> C11 := ; +P6 -> C12 := U2 ; +P7 -> C21 := C22 := U3]  (stores, the first writers)
+    //   [P5 -> C22 += ; +P3 -> C12 += P5 + P3]   [P2 -> C11 +=]   [P4 -> C21 += sign P4]
+    // (4 stores and 4 reduce-adds instead of 4 and 10).  The work layout is explicit: every CTA
+    // pair gets its own item sequence (pairs of positions, so the two accumulators alternate;
+    // stores before adds on every pair; greedy balance), interleaved as item t * units + u.
+    // *done = 1 when the op was emitted; 0 to fall back to the plain FUSED order.
+    bool chain_plan(const ProdTab& T, View A, View B, View C, View SA, View SB, const std::vector<Leaf>& base, int mb,
+                    int kb, int nb, int bn, const std::vector<int>& flag_base, const std::vector<int>& flag_cols,
+                    int nflags, int* done) {
+        static const bool off = getenv("SWMM_NO_CHAINS") != nullptr;  // diagnostics
+        *done = 0;
+        if (off || dry) return true;
+        const int units = gemm_tf32n_pair_units(sms);
+        if (units <= 0) return true;
+        struct Emit { int q, mode; float sign; };
+        struct Chain { int len; int prod[3]; int nemit[3]; Emit emit[3][2]; };
+        const float s4 = T.ntgt[3] == 1 && T.tgt[3][0].q == 2 ? (float)T.tgt[3][0].s : 0.f;
+        const Chain chains[4] = {
+            {3, {0, 5, 6}, {1, 1, 2},
+             {{{0, TGT_STORE, 1.f}}, {{1, TGT_STORE, 1.f}}, {{2, TGT_STORE, 1.f}, {3, TGT_STORE, 1.f}}}},
+            {2, {4, 2, 0}, {1, 1, 0}, {{{3, TGT_ATOMIC, 1.f}}, {{1, TGT_ATOMIC, 1.f}}}},
+            {1, {1, 0, 0}, {1, 0, 0}, {{{0, TGT_ATOMIC, 1.f}}}},
+            {1, {3, 0, 0}, {1, 0, 0}, {{{2, TGT_ATOMIC, s4}}}}};
+        // the chains must add up to the product table's combination, else keep the plain order
+        float coef[7][4] = {}, want[7][4] = {};
+        for (int p = 0; p < 7; ++p)
+            for (int t = 0; t < T.ntgt[p]; ++t) want[p][T.tgt[p][t].q] += (float)T.tgt[p][t].s;
+        for (const Chain& ch : chains)
+            for (int st = 0; st < ch.len; ++st)
+                for (int e = 0; e < ch.nemit[st]; ++e)
+                    for (int j = 0; j <= st; ++j) coef[ch.prod[j]][ch.emit[st][e].q] += ch.emit[st][e].sign;
+        for (int p = 0; p < 7; ++p)
+            for (int q = 0; q < 4; ++q)
+                if (coef[p][q] != want[p][q]) return true;
+        // leaves: one per product (whole quadrant) with its chain step's targets, plus a no-op leaf
+        std::vector<Leaf> leaves(8);
+        std::vector<Target> tg;
+        for (const Chain& ch : chains)
+            for (int st = 0; st < ch.len; ++st) {
+                Leaf lf = base[ch.prod[st]];
+                lf.c_row0 = lf.c_col0 = 0;
+                lf.cont = st > 0 ? 1 : 0;
+                lf.tgt_begin = (int)tg.size();
+                for (int e = 0; e < ch.nemit[st]; ++e) {
+                    const Emit& em = ch.emit[st][e];
+                    const int r = em.q >> 1, c = em.q & 1;
+                    View cv = sub(C, (long long)r * mb, (long long)c * nb, std::min(mb, C.rows - r * mb),
+                                  std::min(nb, C.cols - c * nb), eb);
+                    if (cv.rows <= 0 || cv.cols <= 0) continue;
+                    Target t = make_target(cv, em.sign, em.mode, target_map(cv));
+                    t.flag_base = flag_base[em.q];
+                    t.flag_cols = flag_cols[em.q];
+                    tg.push_back(t);
+                }
+                lf.tgt_count = (int)tg.size() - lf.tgt_begin;
+                leaves[ch.prod[st]] = lf;
+            }
+        Leaf& nop = leaves[7];
+        memset(&nop, 0, sizeof(nop));
+        nop.tag = -1;
+        nop.a_map = 0;
+        nop.b_map = 1;
+        nop.tiles_n = 1;
+        // positions: 256 x 256 tiles of a quadrant, in groups of GR tile rows, column-major in a
+        // group; GR ~ sqrt(2 units) makes the tiles one wave of pair jobs covers about square, so
+        // the A and B blocks they read are shared by as many tiles as possible
+        const int tm2 = (int)ceil_div(mb, 2 * tf32_tile_m()), tn = (int)ceil_div(nb, bn);
+        const int GR = std::max(1, (int)std::lround(std::sqrt(2.0 * units)));
+        std::vector<int> pos;
+        for (int g0 = 0; g0 < tm2; g0 += GR)
+            for (int c = 0; c < tn; ++c)
+                for (int r = g0; r < std::min(tm2, g0 + GR); ++r) pos.push_back(r << 16 | c);
+        const int npos = (int)pos.size();
+        // jobs in order: chain pairs (chains A, B), then single products; each to the least loaded unit
+        std::vector<std::vector<std::pair<int, int>>> seq(units);  // (leaf, tile) per unit
+        std::vector<int> load(units, 0);
+        auto least = [&]() {
+            int u = 0;
+            for (int i = 1; i < units; ++i)
+                if (load[i] < load[u]) u = i;
+            return u;
+        };
+        for (const Chain& ch : chains) {
+            if (ch.len == 1) {
+                for (int p = 0; p < npos; ++p) {
+                    const int u = least();
+                    seq[u].push_back({ch.prod[0], pos[p]});
+                    load[u] += 1;
+                }
+                continue;
+            }
+            for (int p = 0; p < npos; p += 2) {
+                const int u = least();
+                for (int st = 0; st < ch.len; ++st) {
+                    seq[u].push_back({ch.prod[st], pos[p]});
+                    seq[u].push_back(p + 1 < npos ? std::make_pair(ch.prod[st], pos[p + 1]) : std::make_pair(7, 0));
+                }
+                load[u] += ch.len * (p + 1 < npos ? 2 : 1);
+            }
+        }
+        size_t tmax = 0;
+        for (const auto& q : seq) tmax = std::max(tmax, q.size());
+        std::vector<int> il(tmax * units, 7), it(tmax * units, 0);
+        for (int u = 0; u < units; ++u)
+            for (size_t t = 0; t < seq[u].size(); ++t) {
+                il[t * units + u] = seq[u][t].first;
+                it[t * units + u] = seq[u][t].second;
+            }
+        Op o;
+        o.kind = OP_GEMM_TF32;
+        o.bn = bn;
+        o.nmaj = true;
+        o.pair = true;
+        o.items = (int)(tmax * units);
+        o.units = units;
+        o.has_layout = true;
+        o.item_leaf_off = put_blob(il.data(), il.size() * sizeof(int));
+        o.item_tile_off = put_blob(it.data(), it.size() * sizeof(int));
+        if (!make_map_f32(&o.maps.m[0], A.p, C.rows, A.cols, A.ld, 32, tf32_tile_m()) ||
+            !make_map_f32_n(&o.maps.m[1], B.p, A.cols, C.cols, B.ld) ||
+            !make_map_f32(&o.maps.m[2], SA.p, std::max(SA.rows, 1), kb, SA.ld, 32, tf32_tile_m()) ||
+            !make_map_f32_n(&o.maps.m[3], SB.p, std::max(SB.rows, 1), nb, SB.ld)) {
+            err = "tensor map encoding failed";
+            return false;
+        }
+        emit_grouped(o, leaves, tg, nflags);
+        *done = 1;
+        return true;
+    }
     // FUSED plan for C (m x n) <- A (m x k) B (k x n) at depth L (1..3).  `B` is in bt storage
     // on the FP32 path (B^T, n x k).
     bool fused(View A, View B, View C, int L) {
@@ -931,6 +1069,13 @@ struct Planner {
             }
             lf.tgt_count = (int)tg.size() - lf.tgt_begin;
             base_leaves.push_back(lf);
+        }
+        if (ordered && L == 1 && eb == 4 && nmaj && !bf && !x3 && pair_ok(bn) &&
+            (algo == SW_ALGO_WINOGRAD || algo == SW_ALGO_WINOGRAD_KNUTH)) {
+            int done_ = 0;
+            if (!chain_plan(T, A, B, C, SA, SB, base_leaves, mb, kb, nb, bn, flag_base, flag_cols, nflags, &done_))
+                return false;
+            if (done_) return true;
         }
         // Work order: position groups of GM x GN tiles, then leaves, then tiles in the group, so
         // the C tiles every leaf of a group adds into stay in L2 while the group is processed.
@@ -1236,6 +1381,7 @@ static sw_status build_plan(sw_handle h, int eb, const void* A, int lda, const v
     P.sched = (int)sched;
     P.algo = (int)algo;
     P.server = server;
+    P.sms = h->sms;
     if (server && eb == 4 && !bf) P.force_bn = 256;
     const int L = resolve_depth(m, n, k, cutoff, variant, eb);
     plan->depth = L;
@@ -1345,14 +1491,21 @@ static sw_status run_ops(sw_handle h, Plan* plan, cudaStream_t s, size_t first, 
         }
         switch (o.kind) {
             case OP_GEMM_TF32:
-                e = (o.nmaj ? launch_gemm_tf32n : launch_gemm_tf32)(o.bn, o.maps,
-                                     o.ngmaps ? reinterpret_cast<const CUtensorMap*>(blob + o.gmaps_off) : nullptr,
-                                     reinterpret_cast<const Leaf*>(blob + o.leaves_off),
-                                     o.nleaves, reinterpret_cast<const Target*>(blob + o.targets_off),
-                                     o.ntmaps ? reinterpret_cast<const CUtensorMap*>(blob + o.tmaps_off) : nullptr,
-                                     o.nflags ? reinterpret_cast<unsigned*>(blob + o.flags_off) : nullptr,
-                                     o.nflags ? ++o.epoch : 0u, o.items, h->d_err, h->sms, s, o.pair,
-                                     o.has_item_leaf ? reinterpret_cast<const int*>(blob + o.item_leaf_off) : nullptr);
+            {
+                const CUtensorMap* gm = o.ngmaps ? reinterpret_cast<const CUtensorMap*>(blob + o.gmaps_off) : nullptr;
+                const Leaf* lv = reinterpret_cast<const Leaf*>(blob + o.leaves_off);
+                const Target* tv = reinterpret_cast<const Target*>(blob + o.targets_off);
+                const CUtensorMap* tm = o.ntmaps ? reinterpret_cast<const CUtensorMap*>(blob + o.tmaps_off) : nullptr;
+                unsigned* fl = o.nflags ? reinterpret_cast<unsigned*>(blob + o.flags_off) : nullptr;
+                const unsigned ep = o.nflags ? ++o.epoch : 0u;
+                const int* il = (o.has_item_leaf || o.has_layout) ? reinterpret_cast<const int*>(blob + o.item_leaf_off)
+                                                                  : nullptr;
+                const int* it = o.has_layout ? reinterpret_cast<const int*>(blob + o.item_tile_off) : nullptr;
+                e = o.nmaj ? launch_gemm_tf32n(o.bn, o.maps, gm, lv, o.nleaves, tv, tm, fl, ep, o.items, h->d_err, h->sms,
+                                               s, o.pair, il, it, o.units)
+                           : launch_gemm_tf32(o.bn, o.maps, gm, lv, o.nleaves, tv, tm, fl, ep, o.items, h->d_err,
+                                              h->sms, s, o.pair, il);
+            }
                 break;
             case OP_GEMM_SIMT:
                 e = launch_gemm_simt(o.eb, reinterpret_cast<const MatRef*>(blob + o.refs_off),

@@ -127,6 +127,23 @@ __device__ __forceinline__ ItemPos decode_in_leaf(const Leaf* __restrict__ leave
     return p;
 }
 
+// Non-resident item: from the explicit layout (leaf and tile per item), the item -> leaf table, or
+// a search over the leaves' tile ranges.
+template <int TM>
+__device__ __forceinline__ ItemPos decode_any(const Leaf* __restrict__ leaves, int nleaves, const ResidentCtl& ctl,
+                                              int item) {
+    if (ctl.item_tile) {
+        const int t = __ldg(&ctl.item_tile[item]);
+        ItemPos p;
+        p.leaf = __ldg(&ctl.item_leaf[item]);
+        p.tm = t >> 16;
+        p.tn = t & 0xffff;
+        return p;
+    }
+    if (ctl.item_leaf) return decode_in_leaf<TM>(leaves, __ldg(&ctl.item_leaf[item]), item);
+    return decode_item<TM>(leaves, nleaves, item);
+}
+
 __device__ __forceinline__ unsigned ld_acquire_sys_u32(const volatile unsigned* p) {
     unsigned v;
     asm volatile("ld.acquire.sys.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -217,6 +234,10 @@ __global__ void __launch_bounds__(192, 1)
     const bool leader = rank == 0u;
     const int unit = PAIR ? (int)cluster_id_x() : (int)blockIdx.x;
     const int nunits = PAIR ? (int)nclusters_x() : (int)gridDim.x;
+    // an explicit work layout holds only for the number of units it was planned for
+    const bool layout_ok = RES || !ctl.item_tile || nunits == ctl.units;
+    const int n_items = layout_ok ? total_items : 0;
+    if (!layout_ok && threadIdx.x == 0) set_error(err, ERR_UNITS);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < Cfg::STAGES; ++s) {
@@ -267,12 +288,11 @@ __global__ void __launch_bounds__(192, 1)
                     mbar_arrive(&ring_full[rslot]);
                     if (++rslot == 4) { rslot = 0; rph ^= 1u; }
                     if (item < 0) break;
-                } else if (item >= total_items || !ok) {
+                } else if (item >= n_items || !ok) {
                     break;
                 }
                 const ItemPos ip = RES ? decode_in_leaf<Cfg::TM>(leaves, __ldcg(&ctl.item_leaf[item]), item)
-                                   : ctl.item_leaf ? decode_in_leaf<Cfg::TM>(leaves, __ldg(&ctl.item_leaf[item]), item)
-                                                   : decode_item<Cfg::TM>(leaves, nleaves, item);
+                                       : decode_any<Cfg::TM>(leaves, nleaves, ctl, item);
                 const Leaf* L = &leaves[ip.leaf];
                 const int am = __ldg(&L->a_map), bm = __ldg(&L->b_map);
                 const int a_row = __ldg(&L->a_row) + ip.tm * Cfg::TM + (int)rank * TF_BM;
@@ -365,13 +385,13 @@ __global__ void __launch_bounds__(192, 1)
                     mbar_arrive(&ring_empty[rslot]);
                     if (++rslot == 4) { rslot = 0; rph ^= 1u; }
                     if (item < 0) break;
-                } else if (item >= total_items || !ok) {
+                } else if (item >= n_items || !ok) {
                     break;
                 }
                 const ItemPos ip = RES ? decode_in_leaf<Cfg::TM>(leaves, __ldcg(&ctl.item_leaf[item]), item)
-                                   : ctl.item_leaf ? decode_in_leaf<Cfg::TM>(leaves, __ldg(&ctl.item_leaf[item]), item)
-                                                   : decode_item<Cfg::TM>(leaves, nleaves, item);
+                                       : decode_any<Cfg::TM>(leaves, nleaves, ctl, item);
                 const int kb_n = __ldg(&leaves[ip.leaf].kblocks);
+                const uint32_t cont = __ldg(&leaves[ip.leaf].cont) != 0 ? 1u : 0u;  // keep the chain's sum
                 const int acc = local & 1;
                 const uint32_t acc_phase = (local >> 1) & 1;
                 if (!mbar_wait(&tempty[acc], acc_phase ^ 1u, err, ERR_WAIT_ACC_FREE)) { ok = false; break; }
@@ -404,8 +424,9 @@ __global__ void __launch_bounds__(192, 1)
                             const uint64_t bd = MODE == MODE_TF32N
                                                     ? make_sdesc(b_addr + kk * 1024, 4096, 512, SWZ_128B_BASE32B)
                                                     : make_sdesc(b_addr + kk * 32, 16, 1024, SWZ_128B);
-                            if (PAIR) mma_tf32_pair(d_tmem, ad, bd, Cfg::IDESC, (kb | kk) != 0 ? 1u : 0u);
-                            else mma_tf32(d_tmem, ad, bd, Cfg::IDESC, (kb | kk) != 0 ? 1u : 0u);
+                            const uint32_t accum = ((kb | kk) != 0 ? 1u : 0u) | cont;
+                            if (PAIR) mma_tf32_pair(d_tmem, ad, bd, Cfg::IDESC, accum);
+                            else mma_tf32(d_tmem, ad, bd, Cfg::IDESC, accum);
                         }
                     } else {
                         const uint32_t ah = smem_u32(stage_a(stage, 0)), al = smem_u32(stage_a(stage, 1));
@@ -460,12 +481,11 @@ __global__ void __launch_bounds__(192, 1)
                 item = __shfl_sync(0xffffffffu, it, 0);
                 if (++rslot == 4) { rslot = 0; rph ^= 1u; }
                 if (item < 0) break;
-            } else if (item >= total_items) {
+            } else if (item >= n_items) {
                 break;
             }
             const ItemPos ip = RES ? decode_in_leaf<Cfg::TM>(leaves, __ldcg(&ctl.item_leaf[item]), item)
-                               : ctl.item_leaf ? decode_in_leaf<Cfg::TM>(leaves, __ldg(&ctl.item_leaf[item]), item)
-                                               : decode_item<Cfg::TM>(leaves, nleaves, item);
+                                   : decode_any<Cfg::TM>(leaves, nleaves, ctl, item);
             const Leaf* L = &leaves[ip.leaf];
             const int acc = local & 1;
             const uint32_t acc_phase = (local >> 1) & 1;
@@ -634,13 +654,11 @@ __global__ void __launch_bounds__(192, 1)
     }
 }
 
-template <int MODE, int BN, bool RES = false, bool PAIR = false>
-static cudaError_t launch_tc_impl(const MapSet& maps, const CUtensorMap* gmaps, const Leaf* leaves, int nleaves,
-                                  const Target* targets, const CUtensorMap* tmaps, unsigned* flags, unsigned epoch,
-                                  int total_items, int* err, int grid, cudaStream_t stream,
-                                  const ResidentCtl* ctl = nullptr, const int* item_leaf = nullptr) {
+// One-time set-up of a kernel instance: its shared-memory size and, for CTA pairs, how many
+// clusters of two fit on the GPU at once (one CTA per SM).
+template <int MODE, int BN, bool RES, bool PAIR>
+static cudaError_t tc_setup(int* pairs_out) {
     using Cfg = TfCfg<MODE, BN, PAIR>;
-    static_assert(Cfg::SMEM_BYTES <= 232448, "shared memory budget");
     auto kern = gemm_tc_kernel<MODE, BN, RES, PAIR>;
     static bool attr_set = false;
     static int max_pairs = 0;
@@ -666,6 +684,22 @@ static cudaError_t launch_tc_impl(const MapSet& maps, const CUtensorMap* gmaps, 
         }
         attr_set = true;
     }
+    if (pairs_out) *pairs_out = max_pairs;
+    return cudaSuccess;
+}
+
+template <int MODE, int BN, bool RES = false, bool PAIR = false>
+static cudaError_t launch_tc_impl(const MapSet& maps, const CUtensorMap* gmaps, const Leaf* leaves, int nleaves,
+                                  const Target* targets, const CUtensorMap* tmaps, unsigned* flags, unsigned epoch,
+                                  int total_items, int* err, int grid, cudaStream_t stream,
+                                  const ResidentCtl* ctl = nullptr, const int* item_leaf = nullptr,
+                                  const int* item_tile = nullptr, int units = 0) {
+    using Cfg = TfCfg<MODE, BN, PAIR>;
+    static_assert(Cfg::SMEM_BYTES <= 232448, "shared memory budget");
+    auto kern = gemm_tc_kernel<MODE, BN, RES, PAIR>;
+    int max_pairs = 0;
+    cudaError_t se = tc_setup<MODE, BN, RES, PAIR>(&max_pairs);
+    if (se != cudaSuccess) return se;
     ResidentCtl c;
     memset(&c, 0, sizeof(c));
     if (RES) {
@@ -674,9 +708,12 @@ static cudaError_t launch_tc_impl(const MapSet& maps, const CUtensorMap* gmaps, 
     } else {
         if (total_items <= 0) return cudaSuccess;
         c.item_leaf = item_leaf;  // optional item -> leaf table (nullptr: binary search)
+        c.item_tile = item_tile;  // optional explicit layout, planned for `units` units
+        c.units = units;
         if (PAIR) grid = std::min(grid / 2, max_pairs);
         if (grid > total_items) grid = total_items;
         if (grid < 1) grid = 1;
+        if (item_tile) grid = units;  // the layout's own unit count (the kernel checks it)
     }
     if (PAIR) {
         cudaLaunchConfig_t cfg = {};
@@ -730,15 +767,22 @@ cudaError_t launch_gemm_tf32(int bn, const MapSet& maps, const CUtensorMap* gmap
 cudaError_t launch_gemm_tf32n(int bn, const MapSet& maps, const CUtensorMap* gmaps, const Leaf* leaves, int nleaves,
                               const Target* targets, const CUtensorMap* tmaps, unsigned* flags, unsigned epoch,
                               int total_items, int* err, int grid, cudaStream_t stream, bool pair,
-                              const int* item_leaf) {
+                              const int* item_leaf, const int* item_tile, int units) {
     if (pair)
         return launch_tc_impl<MODE_TF32N, 256, false, true>(maps, gmaps, leaves, nleaves, targets, tmaps, flags,
-                                                            epoch, total_items, err, grid, stream, nullptr, item_leaf);
+                                                            epoch, total_items, err, grid, stream, nullptr, item_leaf,
+                                                            item_tile, units);
     if (bn == 256)
         return launch_tc_impl<MODE_TF32N, 256>(maps, gmaps, leaves, nleaves, targets, tmaps, flags, epoch,
-                                               total_items, err, grid, stream, nullptr, item_leaf);
+                                               total_items, err, grid, stream, nullptr, item_leaf, item_tile, units);
     return launch_tc_impl<MODE_TF32N, 128>(maps, gmaps, leaves, nleaves, targets, tmaps, flags, epoch, total_items,
-                                           err, grid, stream, nullptr, item_leaf);
+                                           err, grid, stream, nullptr, item_leaf, item_tile, units);
+}
+
+int gemm_tf32n_pair_units(int sms) {
+    int max_pairs = 0;
+    if (tc_setup<MODE_TF32N, 256, false, true>(&max_pairs) != cudaSuccess || max_pairs <= 0) return 0;
+    return std::min(sms / 2, max_pairs);
 }
 
 cudaError_t launch_gemm_tf32x3(int bn, const MapSet& maps, const CUtensorMap* gmaps, const Leaf* leaves, int nleaves,

@@ -21,6 +21,7 @@ enum : int {
     ERR_WAIT_DRAIN = 5,     // final drain of in-flight copies / MMAs
     ERR_ALIGN = 6,          // a TMA coordinate violated the 16-byte rule (the copy was skipped)
     ERR_ORDER = 7,          // an ordered epilogue waited too long for its predecessor
+    ERR_UNITS = 9,          // a launch with an explicit work layout got another number of units
 };
 
 // With ordering counters (flag_base >= 0), the STORE of a tile is the block's first write: its
@@ -56,7 +57,9 @@ struct Leaf {
     int tiles_n;
     int c_row0, c_col0;  // position of the leaf's tile (0, 0) inside its target blocks
     int tag;             // resident server: completion counter of the leaf's request (-1: none)
-    int pad_[3];
+    int cont;            // 1: the tile continues the accumulator of this CTA's tile two items back
+                         //    (an accumulation chain; needs an explicit item table, see ResidentCtl)
+    int pad_[2];
 };
 
 // Work source of the resident (serving) form of the grouped GEMM: items are published by the
@@ -70,6 +73,11 @@ struct ResidentCtl {
     const int* item_leaf;             // device: leaf index of every published item
     unsigned* done;                   // device: per-request completion counters
     unsigned long long idle_ns;
+    // Non-resident launches may carry an explicit work layout: item_tile[i] = tile row << 16 | tile
+    // column of item i (with item_leaf[i] its leaf), planned for exactly `units` persistent units
+    // (CTAs, or CTA pairs) so that unit u processes items u, u + units, ... in order.
+    const int* item_tile;
+    int units;
 };
 
 }  // namespace swk

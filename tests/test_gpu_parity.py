@@ -451,3 +451,19 @@ def test_tf32x3_odd_sizes(h):
         A, B = inputs.pair(m, n, k, "int", seed=84, dtype=np.float64, lim=2)
         for v in (W | FUSED | X3, W | TWO | X3 | swmm.SW_PAD, W | TWO | X3 | swmm.SW_PEEL):
             assert np.array_equal(run(h, A, B, 40, v), oracle.naive(A, B)), (m, n, k, v)
+
+
+# ------------------------------------------------------------------ depth-1 accumulation chains
+@pytest.mark.parametrize("algo", [W, K])
+@pytest.mark.parametrize("m,n,k", [(1024, 1024, 1024), (1000, 1500, 700), (2304, 520, 300), (3000, 2900, 2000),
+                                   (600, 9000, 520)])
+def test_fused_depth1_wide_quadrants_integers_bit_exact(h, algo, m, n, k):
+    # quadrants wider than 128 columns: the CTA-pair leaf launch with the products of a tile
+    # position summed in tensor memory (stores, then reduce-adds); odd position counts leave
+    # unpaired chains and balanced per-unit sequences
+    cutoff = min(m, n, k) - 1
+    v = algo | FUSED
+    assert depth(h, m, n, k, cutoff, v, 4) == 1
+    assert exact_int_safe(4, k, 1)
+    A, B = inputs.pair(m, n, k, "int", seed=90, dtype=np.float64, lim=4)
+    assert np.array_equal(run(h, A, B, cutoff, v), oracle.naive(A, B)), (algo, m, n, k)
