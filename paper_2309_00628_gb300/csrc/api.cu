@@ -154,6 +154,8 @@ struct Op {
     const void* y = nullptr;
     float sy = 1.f;
     PreaddArgs pre;
+    PreaddArgs pre_b;       // FP32: the B side of the same pass (pre_two: one launch for both)
+    bool pre_two = false;
 };
 
 struct Plan {
@@ -979,29 +981,35 @@ struct Planner {
                 for (int j = 0; j < 2; ++j) halves[i][j] = talloc_half(hr[i], hc[i]);
         }
         if (dry) return true;
+        // operand-sum passes over A and over B (FP32: one launch for both sides)
+        Op pa, pb;
         if (na > 0) {
-            Op o;
-            o.kind = OP_PREADD;
-            o.eb = eb;
-            PreaddArgs& p = o.pre;
+            pa.kind = OP_PREADD;
+            pa.eb = eb;
+            PreaddArgs& p = pa.pre;
             memset(&p, 0, sizeof(p));
             p.x = A.p; p.ldx = A.ld; p.rows = m; p.cols = k; p.brows = mb; p.bcols = kb;
             p.out = SA.p; p.L = L; p.alg = algo == SW_ALGO_STRASSEN ? 1 : algo == SW_ALGO_WINOGRAD_KNUTH ? 3 : 2; p.bside = 0; p.bt = 0;
             for (int w = 0; w < 343; ++w) p.slot_of[w] = w < nleaf ? slot_a[w] : (short)-1;
-            push(o);
         }
         if (nbs > 0) {
-            Op o;
-            o.kind = OP_PREADD;
-            o.eb = eb;
-            PreaddArgs& p = o.pre;
+            pb.kind = OP_PREADD;
+            pb.eb = eb;
+            PreaddArgs& p = pb.pre;
             memset(&p, 0, sizeof(p));
             p.x = B.p; p.ldx = B.ld;
             if (bt) { p.rows = n; p.cols = k; p.brows = nb; p.bcols = kb; }
             else { p.rows = k; p.cols = n; p.brows = kb; p.bcols = nb; }
             p.out = SB.p; p.L = L; p.alg = algo == SW_ALGO_STRASSEN ? 1 : algo == SW_ALGO_WINOGRAD_KNUTH ? 3 : 2; p.bside = 1; p.bt = bt ? 1 : 0;
             for (int w = 0; w < 343; ++w) p.slot_of[w] = w < nleaf ? slot_b[w] : (short)-1;
-            push(o);
+        }
+        if (na > 0 && nbs > 0 && eb == 4) {
+            pa.pre_b = pb.pre;
+            pa.pre_two = true;
+            push(pa);
+        } else {
+            if (na > 0) push(pa);
+            if (nbs > 0) push(pb);
         }
         // Each C block's first writer (the first leaf, in leaf order, that adds into it) stores
         // instead of adding; later leaves wait for it tile by tile.  Used at depth 1 on the TF32
@@ -1556,7 +1564,7 @@ static sw_status run_ops(sw_handle h, Plan* plan, cudaStream_t s, size_t first, 
                 e = launch_copy_pad(o.eb, o.rows, o.cols, o.z, o.ldz, o.x, o.ldx, o.src_rows, o.src_cols, s);
                 break;
             case OP_PREADD:
-                e = launch_preadd(o.eb, o.pre, s);
+                e = o.pre_two ? launch_preadd2(o.pre, o.pre_b, s) : launch_preadd(o.eb, o.pre, s);
                 break;
             case OP_MEMSET:
                 e = cudaMemset2DAsync(o.z, (size_t)o.ldz * o.eb, 0, (size_t)o.cols * o.eb, (size_t)o.rows, s);

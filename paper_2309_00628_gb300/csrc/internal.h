@@ -110,6 +110,9 @@ struct PreaddArgs {
     short slot_of[343];  // leaf word -> output slot, -1 = pure (not written)
 };
 cudaError_t launch_preadd(int elem_bytes, const PreaddArgs& a, cudaStream_t stream);
+// The A-side (a) and B-side (b) passes of one FP32 product in a single launch (falls back to two
+// launches where the vector path or the shapes do not allow it).
+cudaError_t launch_preadd2(const PreaddArgs& a, const PreaddArgs& b, cudaStream_t stream);
 
 // One FP32 copy (or transpose) job of a batched launch: out (out_rows x out_cols) <- x or x^T,
 // zero outside the source extent; tile_begin is the job's first BCOPY_TILE x BCOPY_TILE output

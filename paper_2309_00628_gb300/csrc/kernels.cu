@@ -12,6 +12,7 @@
 //  * transposes  B -> B^T (with zero fill) and in-place square transposes: the TF32 tensor-core
 //                path consumes B as B^T.
 //  * norms       FP64 max-reductions for max|C - R|, max|A|, max|B|.
+#include <algorithm>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <cstdint>
@@ -190,6 +191,15 @@ __device__ __forceinline__ V form(int p, const V& x11, const V& x12, const V& x2
     }
 }
 
+// The sums are written once and read back by the leaf GEMM from DRAM (the slot stack is far
+// larger than L2): streaming stores keep them from displacing cached lines.
+template <typename V>
+__device__ __forceinline__ void store_slot(void* p, const V& v) { *reinterpret_cast<V*>(p) = v; }
+template <>
+__device__ __forceinline__ void store_slot<Vec<float, 4>>(void* p, const Vec<float, 4>& v) {
+    __stcs(reinterpret_cast<float4*>(p), make_float4(v.e[0], v.e[1], v.e[2], v.e[3]));
+}
+
 template <typename V>
 struct SlotWriter {
     const short* slot_of;
@@ -199,7 +209,7 @@ struct SlotWriter {
     bool valid;
     __device__ __forceinline__ void put(int w, const V& v) {
         const int s = slot_of[w];
-        if (s >= 0 && valid) *reinterpret_cast<V*>(out + s * slot_stride + off) = v;
+        if (s >= 0 && valid) store_slot<V>(out + s * slot_stride + off, v);
     }
 };
 
@@ -236,19 +246,19 @@ struct Expand<ALG, BSIDE, BT, 0, V> {
     }
 };
 
-// One thread = VEC consecutive columns of one row position inside the leaf block.
+// One thread = VEC consecutive columns of one row position inside the leaf block; blocks
+// `block` of `nblocks` share one side's work.
 template <typename T, int VEC, int L, int ALG, bool BSIDE, bool BT>
-__global__ void __launch_bounds__(256) preadd_kernel(const PreaddArgs a) {
+__device__ __forceinline__ void preadd_body(const PreaddArgs& a, int block, int nblocks, short* slot_of) {
     using V = Vec<T, VEC>;
     constexpr int N = 1 << L;
     const int cpr = a.bcols / VEC;  // vector columns per block row
     const long long total = (long long)a.brows * cpr;
     const T* x = reinterpret_cast<const T*>(a.x);
-    __shared__ short slot_of[343];
     for (int i = threadIdx.x; i < 343; i += blockDim.x) slot_of[i] = a.slot_of[i];
     __syncthreads();
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-         e += (long long)gridDim.x * blockDim.x) {
+    for (long long e = block * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)nblocks * blockDim.x) {
         const int i = (int)(e / cpr);
         const int j = (int)(e - (long long)i * cpr) * VEC;
         V v[N * N];
@@ -278,6 +288,20 @@ __global__ void __launch_bounds__(256) preadd_kernel(const PreaddArgs a) {
     }
 }
 
+template <typename T, int VEC, int L, int ALG, bool BSIDE, bool BT>
+__global__ void __launch_bounds__(256) preadd_kernel(const PreaddArgs a) {
+    __shared__ short slot_of[343];
+    preadd_body<T, VEC, L, ALG, BSIDE, BT>(a, blockIdx.x, gridDim.x, slot_of);
+}
+
+// Both sides in one launch: blocks [0, grid_a) form A's sums, the rest B's.
+template <typename T, int VEC, int L, int ALG, bool BT>
+__global__ void __launch_bounds__(256) preadd2_kernel(const PreaddArgs a, const PreaddArgs b, int grid_a) {
+    __shared__ short slot_of[343];
+    if ((int)blockIdx.x < grid_a) preadd_body<T, VEC, L, ALG, false, false>(a, blockIdx.x, grid_a, slot_of);
+    else preadd_body<T, VEC, L, ALG, true, BT>(b, blockIdx.x - grid_a, gridDim.x - grid_a, slot_of);
+}
+
 template <typename T, int VEC, int L>
 static void preadd_dispatch_alg(const PreaddArgs& a, int grid, cudaStream_t s) {
     if (a.alg == 3) {
@@ -293,6 +317,33 @@ static void preadd_dispatch_alg(const PreaddArgs& a, int grid, cudaStream_t s) {
         else if (a.bside) preadd_kernel<T, VEC, L, 1, true, false><<<grid, 256, 0, s>>>(a);
         else preadd_kernel<T, VEC, L, 1, false, false><<<grid, 256, 0, s>>>(a);
     }
+}
+
+cudaError_t launch_preadd2(const PreaddArgs& a, const PreaddArgs& b, cudaStream_t s) {
+    // FP32, vector path, depth 1 or 2, the same algorithm on both sides (else two launches)
+    auto vec = [](const PreaddArgs& p) {
+        return (p.bcols % 4) == 0 && (p.ldx % 4) == 0 && (reinterpret_cast<uintptr_t>(p.x) & 15) == 0 &&
+               (reinterpret_cast<uintptr_t>(p.out) & 15) == 0 && p.brows > 0 && p.bcols > 0;
+    };
+    if (!vec(a) || !vec(b) || a.L != b.L || a.alg != b.alg || a.L < 1 || a.L > 2 || a.bside || !b.bside) {
+        cudaError_t e = launch_preadd(4, a, s);
+        return e != cudaSuccess ? e : launch_preadd(4, b, s);
+    }
+    const long long wa = (long long)a.brows * a.bcols / 4, wb = (long long)b.brows * b.bcols / 4;
+    const int g = grid_for(wa + wb, 256);
+    const int ga = std::max(1, std::min(g - 1, (int)((g * wa + (wa + wb) / 2) / (wa + wb))));
+#define SW_PRE2(L_, ALG_)                                                                     \
+    do {                                                                                      \
+        if (b.bt) preadd2_kernel<float, 4, L_, ALG_, true><<<g, 256, 0, s>>>(a, b, ga);      \
+        else preadd2_kernel<float, 4, L_, ALG_, false><<<g, 256, 0, s>>>(a, b, ga);          \
+    } while (0)
+    if (a.L == 1) {
+        if (a.alg == 1) SW_PRE2(1, 1); else if (a.alg == 2) SW_PRE2(1, 2); else SW_PRE2(1, 3);
+    } else {
+        if (a.alg == 1) SW_PRE2(2, 1); else if (a.alg == 2) SW_PRE2(2, 2); else SW_PRE2(2, 3);
+    }
+#undef SW_PRE2
+    return cudaGetLastError();
 }
 
 cudaError_t launch_preadd(int elem_bytes, const PreaddArgs& a, cudaStream_t s) {
