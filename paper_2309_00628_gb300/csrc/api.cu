@@ -805,13 +805,16 @@ struct Planner {
     // pair gets its own item sequence (pairs of positions, so the two accumulators alternate;
     // stores before adds on every pair; greedy balance), interleaved as item t * units + u.
     // *done = 1 when the op was emitted; 0 to fall back to the plain FUSED order.
-    bool chain_plan(const ProdTab& T, View A, View B, View C, View SA, View SB, const std::vector<Leaf>& base, int mb,
-                    int kb, int nb, int bn, const std::vector<int>& flag_base, const std::vector<int>& flag_cols,
-                    int nflags, int* done) {
+    // `o` is the depth-1 grouped-GEMM op with its kind, tile width and operand maps set (TF32 on
+    // CTA pairs, or split-BF16 on single CTAs).
+    bool chain_plan(const ProdTab& T, Op o, View C, const std::vector<Leaf>& base, int mb, int nb, int bn,
+                    const std::vector<int>& flag_base, const std::vector<int>& flag_cols, int nflags, int* done) {
         static const bool off = getenv("SWMM_NO_CHAINS") != nullptr;  // diagnostics
         *done = 0;
         if (off || dry) return true;
-        const int units = gemm_tf32n_pair_units(sms);
+        const bool pairs = o.kind == OP_GEMM_TF32;
+        const int units = pairs ? gemm_tf32n_pair_units(sms) : sms;  // one CTA per SM, all resident
+        const int tile_m = pairs ? 2 * tf32_tile_m() : tf32_tile_m();
         if (units <= 0) return true;
         struct Emit { int q, mode; float sign; };
         struct Chain { int len; int prod[3]; int nemit[3]; Emit emit[3][2]; };
@@ -862,10 +865,10 @@ struct Planner {
         nop.a_map = 0;
         nop.b_map = 1;
         nop.tiles_n = 1;
-        // positions: 256 x 256 tiles of a quadrant, in groups of GR tile rows, column-major in a
-        // group; GR ~ sqrt(2 units) makes the tiles one wave of pair jobs covers about square, so
-        // the A and B blocks they read are shared by as many tiles as possible
-        const int tm2 = (int)ceil_div(mb, 2 * tf32_tile_m()), tn = (int)ceil_div(nb, bn);
+        // positions: tiles of a quadrant, in groups of GR tile rows, column-major in a group;
+        // GR ~ sqrt(2 units) makes the tiles one wave of pair jobs covers about square, so the A
+        // and B blocks they read are shared by as many tiles as possible
+        const int tm2 = (int)ceil_div(mb, tile_m), tn = (int)ceil_div(nb, bn);
         const int GR = std::max(1, (int)std::lround(std::sqrt(2.0 * units)));
         std::vector<int> pos;
         for (int g0 = 0; g0 < tm2; g0 += GR)
@@ -907,23 +910,11 @@ struct Planner {
                 il[t * units + u] = seq[u][t].first;
                 it[t * units + u] = seq[u][t].second;
             }
-        Op o;
-        o.kind = OP_GEMM_TF32;
-        o.bn = bn;
-        o.nmaj = true;
-        o.pair = true;
         o.items = (int)(tmax * units);
         o.units = units;
         o.has_layout = true;
         o.item_leaf_off = put_blob(il.data(), il.size() * sizeof(int));
         o.item_tile_off = put_blob(it.data(), it.size() * sizeof(int));
-        if (!make_map_f32(&o.maps.m[0], A.p, C.rows, A.cols, A.ld, 32, tf32_tile_m()) ||
-            !make_map_f32_n(&o.maps.m[1], B.p, A.cols, C.cols, B.ld) ||
-            !make_map_f32(&o.maps.m[2], SA.p, std::max(SA.rows, 1), kb, SA.ld, 32, tf32_tile_m()) ||
-            !make_map_f32_n(&o.maps.m[3], SB.p, std::max(SB.rows, 1), nb, SB.ld)) {
-            err = "tensor map encoding failed";
-            return false;
-        }
         emit_grouped(o, leaves, tg, nflags);
         *done = 1;
         return true;
@@ -1078,13 +1069,6 @@ struct Planner {
             lf.tgt_count = (int)tg.size() - lf.tgt_begin;
             base_leaves.push_back(lf);
         }
-        if (ordered && L == 1 && eb == 4 && nmaj && !bf && !x3 && pair_ok(bn) &&
-            (algo == SW_ALGO_WINOGRAD || algo == SW_ALGO_WINOGRAD_KNUTH)) {
-            int done_ = 0;
-            if (!chain_plan(T, A, B, C, SA, SB, base_leaves, mb, kb, nb, bn, flag_base, flag_cols, nflags, &done_))
-                return false;
-            if (done_) return true;
-        }
         // Work order: position groups of GM x GN tiles, then leaves, then tiles in the group, so
         // the C tiles every leaf of a group adds into stay in L2 while the group is processed.
         std::vector<Leaf> leaves;
@@ -1169,6 +1153,13 @@ struct Planner {
             MatRef refs[4] = {{A.p, A.ld, m, k}, {B.p, B.ld, k, n}, {SA.p, SA.ld, SA.rows, kb},
                               {SB.p, SB.ld, SB.rows, nb}};
             o.refs_off = put_blob(refs, sizeof(refs));
+        }
+        // depth-1 accumulation chains: TF32 on CTA pairs, split-BF16 on single CTAs
+        if (ordered && L == 1 && (algo == SW_ALGO_WINOGRAD || algo == SW_ALGO_WINOGRAD_KNUTH) &&
+            ((o.kind == OP_GEMM_TF32 && o.nmaj && o.pair) || o.kind == OP_GEMM_BF16X3)) {
+            int done_ = 0;
+            if (!chain_plan(T, o, C, base_leaves, mb, nb, bn, flag_base, flag_cols, nflags, &done_)) return false;
+            if (done_) return true;
         }
         emit_grouped(o, leaves, tg, nflags);
         return true;
@@ -1554,8 +1545,11 @@ static sw_status run_ops(sw_handle h, Plan* plan, cudaStream_t s, size_t first, 
                                        o.ntmaps ? reinterpret_cast<const CUtensorMap*>(blob + o.tmaps_off) : nullptr,
                                        o.nflags ? reinterpret_cast<unsigned*>(blob + o.flags_off) : nullptr,
                                        o.nflags ? ++o.epoch : 0u, o.items, h->d_err, h->sms, s,
-                                       o.has_item_leaf ? reinterpret_cast<const int*>(blob + o.item_leaf_off)
-                                                       : nullptr);
+                                       (o.has_item_leaf || o.has_layout)
+                                           ? reinterpret_cast<const int*>(blob + o.item_leaf_off)
+                                           : nullptr,
+                                       o.has_layout ? reinterpret_cast<const int*>(blob + o.item_tile_off) : nullptr,
+                                       o.units);
                 break;
             case OP_ADDSUB:
                 e = launch_addsub(o.eb, o.rows, o.cols, o.z, o.ldz, o.x, o.ldx, o.y, o.ldy, o.sy, s);

@@ -439,7 +439,7 @@ __global__ void __launch_bounds__(192, 1)
                             const uint64_t dal = make_sdesc(al + kk * 32, 16, 1024, SWZ_128B);
                             const uint64_t dbh = make_sdesc(bh + kk * 2048, 8192, 1024, SWZ_128B);
                             const uint64_t dbl = make_sdesc(bl + kk * 2048, 8192, 1024, SWZ_128B);
-                            mma_f16(d_tmem, dal, dbh, Cfg::IDESC, (kb | kk) != 0 ? 1u : 0u);  // lo * hi
+                            mma_f16(d_tmem, dal, dbh, Cfg::IDESC, ((kb | kk) != 0 ? 1u : 0u) | cont);  // lo * hi
                             mma_f16(d_tmem, dah, dbl, Cfg::IDESC, 1u);                           // hi * lo
                             mma_f16(d_tmem, dah, dbh, Cfg::IDESC, 1u);                           // hi * hi
                         }
@@ -797,12 +797,13 @@ cudaError_t launch_gemm_tf32x3(int bn, const MapSet& maps, const CUtensorMap* gm
 
 cudaError_t launch_gemm_bf16x3(int bn, const MapSet& maps, const CUtensorMap* gmaps, const Leaf* leaves, int nleaves,
                                const Target* targets, const CUtensorMap* tmaps, unsigned* flags, unsigned epoch,
-                               int total_items, int* err, int grid, cudaStream_t stream, const int* item_leaf) {
+                               int total_items, int* err, int grid, cudaStream_t stream, const int* item_leaf,
+                               const int* item_tile, int units) {
     if (bn == 256)
         return launch_tc_impl<MODE_BF16X3, 256>(maps, gmaps, leaves, nleaves, targets, tmaps, flags, epoch,
-                                                total_items, err, grid, stream, nullptr, item_leaf);
+                                                total_items, err, grid, stream, nullptr, item_leaf, item_tile, units);
     return launch_tc_impl<MODE_BF16X3, 128>(maps, gmaps, leaves, nleaves, targets, tmaps, flags, epoch, total_items,
-                                            err, grid, stream, nullptr, item_leaf);
+                                            err, grid, stream, nullptr, item_leaf, item_tile, units);
 }
 
 int tf32_tile_m() { return TF_BM; }

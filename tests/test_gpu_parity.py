@@ -454,15 +454,16 @@ def test_tf32x3_odd_sizes(h):
 
 
 # ------------------------------------------------------------------ depth-1 accumulation chains
+@pytest.mark.parametrize("leaf", [swmm.SW_LEAF_TF32, swmm.SW_LEAF_BF16X3])
 @pytest.mark.parametrize("algo", [W, K])
 @pytest.mark.parametrize("m,n,k", [(1024, 1024, 1024), (1000, 1500, 700), (2304, 520, 300), (3000, 2900, 2000),
                                    (600, 9000, 520)])
-def test_fused_depth1_wide_quadrants_integers_bit_exact(h, algo, m, n, k):
-    # quadrants wider than 128 columns: the CTA-pair leaf launch with the products of a tile
-    # position summed in tensor memory (stores, then reduce-adds); odd position counts leave
-    # unpaired chains and balanced per-unit sequences
+def test_fused_depth1_wide_quadrants_integers_bit_exact(h, leaf, algo, m, n, k):
+    # depth-1 leaf launches with the products of a tile position summed in tensor memory (TF32:
+    # CTA pairs, quadrants wider than 128 columns; split-BF16: single CTAs), stores before
+    # reduce-adds; odd position counts leave unpaired chains and balanced per-unit sequences
     cutoff = min(m, n, k) - 1
-    v = algo | FUSED
+    v = algo | FUSED | leaf
     assert depth(h, m, n, k, cutoff, v, 4) == 1
     assert exact_int_safe(4, k, 1)
     A, B = inputs.pair(m, n, k, "int", seed=90, dtype=np.float64, lim=4)
