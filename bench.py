@@ -44,6 +44,8 @@ def parse():
     p.add_argument("--n", type=int, default=8192)
     p.add_argument("--algo", choices=["winograd", "knuth", "strassen", "naive"], default="winograd")
     p.add_argument("--sched", choices=["fused", "two_temp", "in_place", "alloc"], default="fused")
+    p.add_argument("--leaf", choices=["tf32", "bf16x3", "tf32x3"], default="tf32",
+                   help="leaf precision of the profile case (the headline line is TF32)")
     p.add_argument("--cutoff", type=int, default=None,
                    help="recursion cutoff (default n / 2: one level); 0 = the library's autotuner")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-oracle sample budget")
@@ -405,11 +407,13 @@ def main():
         return
 
     if args.profile_case:
+        leafbits = {"tf32": swmm.SW_LEAF_TF32, "bf16x3": swmm.SW_LEAF_BF16X3, "tf32x3": swmm.SW_LEAF_TF32X3}[args.leaf]
         for _ in range(args.warmup + 1):
-            product(variant, args.cutoff)
+            product(variant | leafbits, args.cutoff)
         swmm.check(h, swmm.sw_sync(h, sp))
         if rank == 0:
-            print(json.dumps({"profile_case": args.algo, "schedule": args.sched, "n": n, "depth": L}), flush=True)
+            print(json.dumps({"profile_case": args.algo, "schedule": args.sched, "leaf": args.leaf, "n": n, "depth": L}),
+                  flush=True)
         swmm.sw_destroy(h)
         return
 

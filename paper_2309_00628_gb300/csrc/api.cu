@@ -208,11 +208,12 @@ struct Planner {
     int sms = 0;              // SMs of the device (explicit work layouts are planned for its units)
     int batch_bn = 256;       // batched launch: tile width of the grouped GEMM (128 or 256)
     bool batch_pair = false;  // batched launch: CTA-pair form (256 x 256 tiles; N-major B only)
-    // The CTA-pair TF32 GEMM (cta_group::2) serves single products with 256-wide tiles; batched
-    // and serving launches keep the one-CTA form.  SWMM_NO_PAIR=1 disables it (diagnostics).
+    // The CTA-pair GEMM (cta_group::2; TF32 and split-BF16 leaves) serves single products with
+    // 256-wide tiles; batched and serving launches keep the one-CTA form unless told otherwise.
+    // SWMM_NO_PAIR=1 disables it (diagnostics).
     bool pair_ok(int bn) const {
         static const bool off = getenv("SWMM_NO_PAIR") != nullptr;
-        return !off && bn == 256 && !batch && !server && !bf && !x3 && eb == 4;
+        return !off && bn == 256 && !batch && !server && !x3 && eb == 4;
     }
     // rows of one B-side TMA box: half the tile width for a CTA pair
     int b_box(int bn) const { return pair_ok(bn) ? bn / 2 : bn; }
@@ -535,7 +536,7 @@ struct Planner {
             lf.tgt_count = 1;
             Op o;
             o.kind = x3 ? OP_GEMM_TF32X3 : OP_GEMM_BF16X3;
-            o.bn = bn_override() ? bn_override() : 128;
+            o.bn = bn_override() ? bn_override() : (x3 || c.cols <= 128 ? 128 : 256);
             lf.kblocks = (int)ceil_div(a.cols, x3 ? tf32_tile_k() : bf16x3_tile_k());
             lf.tiles_n = (int)ceil_div(c.cols, o.bn);
             if (x3)
@@ -550,6 +551,10 @@ struct Planner {
                      make_map_bf16(&o.maps.m[3], bl.p, bl.rows, bl.cols, bl.ld, 64);
             if (!ok) err = "split-leaf tensor map encoding failed";
             o.items = (int)(ceil_div(c.rows, tf32_tile_m()) * lf.tiles_n);
+            if (!x3 && pair_ok(o.bn)) {  // 256-row tiles on CTA pairs
+                o.items = (int)(ceil_div(c.rows, 2 * tf32_tile_m()) * lf.tiles_n);
+                o.pair = true;
+            }
             o.nleaves = 1;
             o.leaves_off = put_blob(&lf, sizeof(lf));
             o.targets_off = put_blob(&t, sizeof(t));
@@ -812,8 +817,9 @@ struct Planner {
         static const bool off = getenv("SWMM_NO_CHAINS") != nullptr;  // diagnostics
         *done = 0;
         if (off || dry) return true;
-        const bool pairs = o.kind == OP_GEMM_TF32;
-        const int units = pairs ? gemm_tf32n_pair_units(sms) : sms;  // one CTA per SM, all resident
+        const bool pairs = o.pair;
+        const int units = !pairs ? sms  // one CTA per SM, all resident
+                                 : o.kind == OP_GEMM_TF32 ? gemm_tf32n_pair_units(sms) : gemm_bf16x3_pair_units(sms);
         const int tile_m = pairs ? 2 * tf32_tile_m() : tf32_tile_m();
         if (units <= 0) return true;
         struct Emit { int q, mode; float sign; };
@@ -1011,7 +1017,7 @@ struct Planner {
         if (!ordered) memset0(C);
         const int bn_o = eb == 8 ? F64_BN
                                  : force_bn ? force_bn
-                                            : (bn_override() ? bn_override() : (bf || x3 || nb <= 128 ? 128 : 256));
+                                            : (bn_override() ? bn_override() : (x3 || nb <= 128 ? 128 : 256));
         std::vector<int> first_writer(1 << (2 * L), -1), flag_base(1 << (2 * L), -1), flag_cols(1 << (2 * L), 0);
         int nflags = 0;
         // leaves and their Kronecker-product targets
@@ -1132,6 +1138,7 @@ struct Planner {
                     return false;
                 }
             }
+            if (!x3 && pair_ok(bn)) to_pair(o, leaves);
         } else if (eb == 4) {
             o.kind = OP_GEMM_TF32;
             o.bn = bn;
@@ -1549,7 +1556,7 @@ static sw_status run_ops(sw_handle h, Plan* plan, cudaStream_t s, size_t first, 
                                            ? reinterpret_cast<const int*>(blob + o.item_leaf_off)
                                            : nullptr,
                                        o.has_layout ? reinterpret_cast<const int*>(blob + o.item_tile_off) : nullptr,
-                                       o.units);
+                                       o.units, o.pair);
                 break;
             case OP_ADDSUB:
                 e = launch_addsub(o.eb, o.rows, o.cols, o.z, o.ldz, o.x, o.ldx, o.y, o.ldy, o.sy, s);

@@ -73,7 +73,7 @@ struct TfCfg {
         TF ? ((1u << 4) | (2u << 7) | (2u << 10) | (BN_MAJOR32 ? (1u << 16) : 0u) |
               ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24))
             : ((1u << 4) | (1u << 7) | (1u << 10) | (1u << 16) | ((uint32_t)(BN >> 3) << 17) |
-               ((uint32_t)(TF_BM >> 4) << 24));
+               ((uint32_t)(TM >> 4) << 24));
 };
 
 struct ItemPos {
@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(192, 1)
                      const Leaf* __restrict__ leaves, int nleaves, const Target* __restrict__ targets,
                      const CUtensorMap* __restrict__ tmaps, unsigned* __restrict__ flags, unsigned epoch,
                      int total_items, int* err, const ResidentCtl ctl) {
-    static_assert(!PAIR || ((MODE == MODE_TF32 || MODE == MODE_TF32N) && !RES), "CTA pairs: TF32, non-resident only");
+    static_assert(!PAIR || (MODE != MODE_TF32X3 && !RES), "CTA pairs: TF32 / split-BF16, non-resident only");
     using Cfg = TfCfg<MODE, BN, PAIR>;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw_addr = smem_u32(smem_raw);
@@ -320,6 +320,21 @@ __global__ void __launch_bounds__(192, 1)
                         // both halves land on the leader's full barrier
                         if (leader) mbar_arrive_expect_tx(&full[stage], 2 * Cfg::STAGE_BYTES);
                         const uint32_t fb = mapa_shared(smem_u32(&full[stage]), 0u);
+                        if (MODE == MODE_BF16X3) {
+#pragma unroll
+                            for (int op = 0; op < 2; ++op) {  // hi, lo
+                                const CUtensorMap* ma = pick_map(maps, gmaps, am * 2 + op);
+                                const CUtensorMap* mb = pick_map(maps, gmaps, bm * 2 + op);
+                                tma_load_2d_pair(stage_a(stage, op), ma, fb, a_col + kb * Cfg::BK, a_row);
+#pragma unroll
+                                for (int c = 0; c < Cfg::B_ROWS / 64; ++c)  // 64 N-columns x 64 K-rows per box
+                                    tma_load_2d_pair(stage_b(stage, op) + c * 8192, mb, fb, b_col + c * 64,
+                                                     b_row + kb * Cfg::BK);
+                            }
+                            ++issued;
+                            if (++stage == Cfg::STAGES) { stage = 0; phase ^= 1u; }
+                            continue;
+                        }
                         tma_load_2d_pair(stage_a(stage, 0), pick_map(maps, gmaps, am), fb, a_col + kb * Cfg::BK,
                                          a_row);
                         if (MODE == MODE_TF32N) {
@@ -439,9 +454,16 @@ __global__ void __launch_bounds__(192, 1)
                             const uint64_t dal = make_sdesc(al + kk * 32, 16, 1024, SWZ_128B);
                             const uint64_t dbh = make_sdesc(bh + kk * 2048, 8192, 1024, SWZ_128B);
                             const uint64_t dbl = make_sdesc(bl + kk * 2048, 8192, 1024, SWZ_128B);
-                            mma_f16(d_tmem, dal, dbh, Cfg::IDESC, ((kb | kk) != 0 ? 1u : 0u) | cont);  // lo * hi
-                            mma_f16(d_tmem, dah, dbl, Cfg::IDESC, 1u);                           // hi * lo
-                            mma_f16(d_tmem, dah, dbh, Cfg::IDESC, 1u);                           // hi * hi
+                            const uint32_t first = ((kb | kk) != 0 ? 1u : 0u) | cont;
+                            if (PAIR) {
+                                mma_f16_pair(d_tmem, dal, dbh, Cfg::IDESC, first);  // lo * hi
+                                mma_f16_pair(d_tmem, dah, dbl, Cfg::IDESC, 1u);     // hi * lo
+                                mma_f16_pair(d_tmem, dah, dbh, Cfg::IDESC, 1u);     // hi * hi
+                            } else {
+                                mma_f16(d_tmem, dal, dbh, Cfg::IDESC, first);  // lo * hi
+                                mma_f16(d_tmem, dah, dbl, Cfg::IDESC, 1u);     // hi * lo
+                                mma_f16(d_tmem, dah, dbh, Cfg::IDESC, 1u);     // hi * hi
+                            }
                         }
                     }
                     // stage is free once these MMAs have read it (in both CTAs of a pair)
@@ -785,6 +807,12 @@ int gemm_tf32n_pair_units(int sms) {
     return std::min(sms / 2, max_pairs);
 }
 
+int gemm_bf16x3_pair_units(int sms) {
+    int max_pairs = 0;
+    if (tc_setup<MODE_BF16X3, 256, false, true>(&max_pairs) != cudaSuccess || max_pairs <= 0) return 0;
+    return std::min(sms / 2, max_pairs);
+}
+
 cudaError_t launch_gemm_tf32x3(int bn, const MapSet& maps, const CUtensorMap* gmaps, const Leaf* leaves, int nleaves,
                                const Target* targets, const CUtensorMap* tmaps, unsigned* flags, unsigned epoch,
                                int total_items, int* err, int grid, cudaStream_t stream, const int* item_leaf) {
@@ -798,7 +826,11 @@ cudaError_t launch_gemm_tf32x3(int bn, const MapSet& maps, const CUtensorMap* gm
 cudaError_t launch_gemm_bf16x3(int bn, const MapSet& maps, const CUtensorMap* gmaps, const Leaf* leaves, int nleaves,
                                const Target* targets, const CUtensorMap* tmaps, unsigned* flags, unsigned epoch,
                                int total_items, int* err, int grid, cudaStream_t stream, const int* item_leaf,
-                               const int* item_tile, int units) {
+                               const int* item_tile, int units, bool pair) {
+    if (pair)
+        return launch_tc_impl<MODE_BF16X3, 256, false, true>(maps, gmaps, leaves, nleaves, targets, tmaps, flags,
+                                                             epoch, total_items, err, grid, stream, nullptr, item_leaf,
+                                                             item_tile, units);
     if (bn == 256)
         return launch_tc_impl<MODE_BF16X3, 256>(maps, gmaps, leaves, nleaves, targets, tmaps, flags, epoch,
                                                 total_items, err, grid, stream, nullptr, item_leaf, item_tile, units);

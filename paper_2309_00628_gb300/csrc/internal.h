@@ -58,7 +58,10 @@ int bf16x3_tile_k();
 cudaError_t launch_gemm_bf16x3(int bn, const MapSet& maps, const CUtensorMap* gmaps, const Leaf* leaves, int nleaves,
                                const Target* targets, const CUtensorMap* tmaps, unsigned* flags, unsigned epoch,
                                int total_items, int* err, int grid, cudaStream_t stream,
-                               const int* item_leaf = nullptr, const int* item_tile = nullptr, int units = 0);
+                               const int* item_leaf = nullptr, const int* item_tile = nullptr, int units = 0,
+                               bool pair = false);
+// Persistent units (CTA pairs) of a pair-form split-BF16 launch on `sms` SMs (0: unavailable).
+int gemm_bf16x3_pair_units(int sms);
 
 // Compensated-TF32 leaves: operand map index i refers to maps 2i (hi) and 2i+1 (lo), FP32 halves
 // with hi = tf32(x), lo = x - hi; A K-major (make_map_f32, 128-row boxes), B N-major
