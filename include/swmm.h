@@ -240,9 +240,9 @@ sw_status sw_error_norms(sw_handle h, int elem_bytes, int m, int n, int k, const
  * read (then resets).  Kinds: 0 tensor-core leaf GEMM (TF32), 1 SIMT leaf GEMM, 2 block addition,
  * 3 padded copy, 4 operand-sum pass, 5 memset, 6 transpose, 7 in-place transpose, 8 bf16 split,
  * 9 tensor-core leaf GEMM (split BF16), 10 batched copy / transpose (sw_mm_batched staging),
- * 11 tf32 split, 12 tensor-core leaf GEMM (compensated TF32).
- * `nkinds` is the length of both output arrays (entries beyond 13 are set to 0). */
-#define SW_PROFILE_KINDS 13
+ * 11 tf32 split, 12 tensor-core leaf GEMM (compensated TF32), 13 operand sums with split-BF16 output.
+ * `nkinds` is the length of both output arrays (entries beyond 14 are set to 0). */
+#define SW_PROFILE_KINDS 14
 sw_status sw_profile(sw_handle h, int enable);
 sw_status sw_profile_read(sw_handle h, int nkinds, int *launches, double *ms);
 

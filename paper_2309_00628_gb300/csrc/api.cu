@@ -127,7 +127,7 @@ inline long long ceil_div(long long x, long long a) { return (x + a - 1) / a; }
 // ------------------------------------------------------------------ plan
 enum OpKind {
     OP_GEMM_TF32, OP_GEMM_SIMT, OP_ADDSUB, OP_COPY_PAD, OP_PREADD, OP_MEMSET, OP_TRANSPOSE, OP_TRANSPOSE_SQ,
-    OP_SPLIT, OP_GEMM_BF16X3, OP_BATCH_COPY, OP_SPLIT_TF32, OP_GEMM_TF32X3
+    OP_SPLIT, OP_GEMM_BF16X3, OP_BATCH_COPY, OP_SPLIT_TF32, OP_GEMM_TF32X3, OP_PREADD_SPLIT
 };
 
 struct Op {
@@ -156,6 +156,8 @@ struct Op {
     PreaddArgs pre;
     PreaddArgs pre_b;       // FP32: the B side of the same pass (pre_two: one launch for both)
     bool pre_two = false;
+    PreaddSplitOut sout;    // OP_PREADD_SPLIT: bf16 halves of A and of its sums (sout_b: of B)
+    PreaddSplitOut sout_b;
 };
 
 struct Plan {
@@ -960,15 +962,18 @@ struct Planner {
                 slot_b[w] = (short)nbs++;
             }
         }
+        // Split-BF16 leaves at depth 1 or 2 with A and B read as stored: one pass per side writes the
+        // bf16 halves of the operand and of its sums (no FP32 sum slots, no separate split passes)
+        const bool split_sums = bf && !x3 && L <= 2 && na > 0 && nbs > 0 && !bt && vec_ok(A) && vec_ok(B) &&
+                                (kb % 8) == 0 && (nb % 8) == 0;
         // scratch for the materialised operand sums: dense slots, row stride = block width
-        const size_t mark = ws_top;
-        View SA = talloc(std::max(na, 1) * mb, kb);
+        View SA = split_sums ? View{nullptr, kb, na * mb, kb} : talloc(std::max(na, 1) * mb, kb);
         SA.rows = na * mb;
         SA.ld = kb;
-        View SB = bt ? talloc(std::max(nbs, 1) * nb, kb) : talloc(std::max(nbs, 1) * kb, nb);
+        View SB = split_sums ? View{nullptr, nb, nbs * kb, nb}
+                             : bt ? talloc(std::max(nbs, 1) * nb, kb) : talloc(std::max(nbs, 1) * kb, nb);
         SB.rows = bt ? nbs * nb : nbs * kb;
         SB.ld = bt ? kb : nb;
-        (void)mark;
         // split-BF16 leaves: (hi, lo) halves of A, B and the S / T sums (sized in the dry run too)
         View halves[4][2];
         if (bf || x3) {
@@ -978,7 +983,8 @@ struct Planner {
                 for (int j = 0; j < 2; ++j) halves[i][j] = talloc_half(hr[i], hc[i]);
         }
         if (dry) return true;
-        // operand-sum passes over A and over B (FP32: one launch for both sides)
+        // operand-sum passes over A and over B (FP32: one launch for both sides; split-BF16: the
+        // halves of A, B and their sums in one pass per side)
         Op pa, pb;
         if (na > 0) {
             pa.kind = OP_PREADD;
@@ -1000,7 +1006,18 @@ struct Planner {
             p.out = SB.p; p.L = L; p.alg = algo == SW_ALGO_STRASSEN ? 1 : algo == SW_ALGO_WINOGRAD_KNUTH ? 3 : 2; p.bside = 1; p.bt = bt ? 1 : 0;
             for (int w = 0; w < 343; ++w) p.slot_of[w] = w < nleaf ? slot_b[w] : (short)-1;
         }
-        if (na > 0 && nbs > 0 && eb == 4) {
+        if (split_sums) {
+            pa.kind = OP_PREADD_SPLIT;
+            pa.sout = {reinterpret_cast<__nv_bfloat16*>(halves[0][0].p), reinterpret_cast<__nv_bfloat16*>(halves[0][1].p),
+                       halves[0][0].ld, reinterpret_cast<__nv_bfloat16*>(halves[2][0].p),
+                       reinterpret_cast<__nv_bfloat16*>(halves[2][1].p)};
+            pb.sout = {reinterpret_cast<__nv_bfloat16*>(halves[1][0].p), reinterpret_cast<__nv_bfloat16*>(halves[1][1].p),
+                       halves[1][0].ld, reinterpret_cast<__nv_bfloat16*>(halves[3][0].p),
+                       reinterpret_cast<__nv_bfloat16*>(halves[3][1].p)};
+            pa.pre_b = pb.pre;
+            pa.sout_b = pb.sout;
+            push(pa);
+        } else if (na > 0 && nbs > 0 && eb == 4) {
             pa.pre_b = pb.pre;
             pa.pre_two = true;
             push(pa);
@@ -1122,7 +1139,7 @@ struct Planner {
             for (int i = 0; i < 4; ++i) {
                 const View& hi = halves[i][0];
                 const View& lo = halves[i][1];
-                if (srcs[i].rows > 0) split_into(srcs[i], hi, lo);
+                if (srcs[i].rows > 0 && !split_sums) split_into(srcs[i], hi, lo);
                 bool mok;
                 if (x3)  // A side K-major, B side N-major (i odd: B and the T sums)
                     mok = (i & 1) ? make_map_f32_n(&o.maps.m[2 * i], hi.p, hi.rows, hi.cols, hi.ld) &&
@@ -1566,6 +1583,9 @@ static sw_status run_ops(sw_handle h, Plan* plan, cudaStream_t s, size_t first, 
                 break;
             case OP_PREADD:
                 e = o.pre_two ? launch_preadd2(o.pre, o.pre_b, s) : launch_preadd(o.eb, o.pre, s);
+                break;
+            case OP_PREADD_SPLIT:
+                e = launch_preadd_split(o.pre, o.sout, o.pre_b, o.sout_b, s);
                 break;
             case OP_MEMSET:
                 e = cudaMemset2DAsync(o.z, (size_t)o.ldz * o.eb, 0, (size_t)o.cols * o.eb, (size_t)o.rows, s);

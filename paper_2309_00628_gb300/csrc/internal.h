@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda.h>
 #include <cuda_runtime.h>
+#include <cuda_bf16.h>
 #include <cstdint>
 
 #include "plan.h"
@@ -113,6 +114,20 @@ struct PreaddArgs {
     short slot_of[343];  // leaf word -> output slot, -1 = pure (not written)
 };
 cudaError_t launch_preadd(int elem_bytes, const PreaddArgs& a, cudaStream_t stream);
+// Operand sums with split-BF16 output (depth 1 or 2, FP32 vector path, X as stored), both sides
+// in one launch: writes the bf16 halves of X (xh / xl, leading dimension ldx_out, a multiple of 8)
+// and of every sum slot (sh / sl, slot s at element s * brows * bcols, row stride bcols, a
+// multiple of 8); 16-byte aligned buffers.
+struct PreaddSplitOut {
+    __nv_bfloat16* xh;
+    __nv_bfloat16* xl;
+    long long ldx_out;
+    __nv_bfloat16* sh;
+    __nv_bfloat16* sl;
+};
+cudaError_t launch_preadd_split(const PreaddArgs& a, const PreaddSplitOut& oa, const PreaddArgs& b,
+                                const PreaddSplitOut& ob, cudaStream_t stream);
+
 // The A-side (a) and B-side (b) passes of one FP32 product in a single launch (falls back to two
 // launches where the vector path or the shapes do not allow it).
 cudaError_t launch_preadd2(const PreaddArgs& a, const PreaddArgs& b, cudaStream_t stream);

@@ -319,6 +319,136 @@ static void preadd_dispatch_alg(const PreaddArgs& a, int grid, cudaStream_t s) {
     }
 }
 
+// ------------------------------------------------------------ operand sums + split-BF16 halves
+// The split-BF16 leaves read every operand as bf16 halves hi = bf16(x), lo = bf16(x - hi).  This
+// pass reads the 2^L x 2^L block grid of X once and writes the halves of X itself (its blocks are
+// the pure leaf operands) and the halves of every operand sum -- instead of a sum pass followed by
+// split passes over X and over the sums.
+// hi / lo bf16 halves of eight consecutive FP32 values, as two 16-byte words
+__device__ __forceinline__ void split8(const Vec<float, 8>& v, uint4& hi, uint4& lo) {
+    unsigned h[4], l[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const __nv_bfloat162 hh = __floats2bfloat162_rn(v.e[2 * i], v.e[2 * i + 1]);
+        const float2 f = __bfloat1622float2(hh);
+        const __nv_bfloat162 ll = __floats2bfloat162_rn(v.e[2 * i] - f.x, v.e[2 * i + 1] - f.y);
+        h[i] = *reinterpret_cast<const unsigned*>(&hh);
+        l[i] = *reinterpret_cast<const unsigned*>(&ll);
+    }
+    hi = make_uint4(h[0], h[1], h[2], h[3]);
+    lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+struct SplitSlotWriter {
+    const short* slot_of;
+    uint4* hi;             // slot stack halves (bf16), slot s at element s * slot_elems
+    uint4* lo;
+    long long slot_q;      // 8-element groups between slots
+    long long off_q;       // this thread's 8-element group inside a slot
+    __device__ __forceinline__ void put(int w, const Vec<float, 8>& v) {
+        const int sl = slot_of[w];
+        if (sl < 0) return;
+        uint4 h, l;
+        split8(v, h, l);
+        __stcs(hi + sl * slot_q + off_q, h);
+        __stcs(lo + sl * slot_q + off_q, l);
+    }
+};
+
+// One thread = eight consecutive columns of one row position inside the block; blocks `block` of
+// `nblocks` share one side's work.
+template <int L, int ALG, bool BSIDE>
+__device__ __forceinline__ void preadd_split_body(const PreaddArgs& a, const PreaddSplitOut& o, int block,
+                                                  int nblocks, short* slot_of) {
+    using V = Vec<float, 8>;
+    constexpr int N = 1 << L;
+    const int cpr = a.bcols / 8;
+    const long long total = (long long)a.brows * cpr;
+    const float* x = reinterpret_cast<const float*>(a.x);
+    for (int i = threadIdx.x; i < 343; i += blockDim.x) slot_of[i] = a.slot_of[i];
+    __syncthreads();
+    uint4* xh = reinterpret_cast<uint4*>(o.xh);
+    uint4* xl = reinterpret_cast<uint4*>(o.xl);
+    for (long long e = block * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)nblocks * blockDim.x) {
+        const int i = (int)(e / cpr);
+        const int j = (int)(e - (long long)i * cpr) * 8;
+        V v[N * N];
+#pragma unroll
+        for (int br = 0; br < N; ++br) {
+#pragma unroll
+            for (int bc = 0; bc < N; ++bc) {
+                const int gr = br * a.brows + i, gc = bc * a.bcols + j;
+                V t;
+                if (gr < a.rows && gc + 8 <= a.cols) {
+                    const float4 f0 = *reinterpret_cast<const float4*>(x + gr * a.ldx + gc);
+                    const float4 f1 = *reinterpret_cast<const float4*>(x + gr * a.ldx + gc + 4);
+                    t.e[0] = f0.x; t.e[1] = f0.y; t.e[2] = f0.z; t.e[3] = f0.w;
+                    t.e[4] = f1.x; t.e[5] = f1.y; t.e[6] = f1.z; t.e[7] = f1.w;
+                    uint4 h, l;  // the halves of X itself
+                    split8(t, h, l);
+                    __stcs(xh + (gr * o.ldx_out + gc) / 8, h);
+                    __stcs(xl + (gr * o.ldx_out + gc) / 8, l);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 8; ++q)
+                        t.e[q] = (gr < a.rows && gc + q < a.cols) ? x[gr * a.ldx + gc + q] : 0.f;
+                    if (gr < a.rows) {  // a ragged right edge: element by element
+                        for (int q = 0; q < 8 && gc + q < a.cols; ++q) {
+                            const __nv_bfloat16 h = __float2bfloat16_rn(t.e[q]);
+                            o.xh[gr * o.ldx_out + gc + q] = h;
+                            o.xl[gr * o.ldx_out + gc + q] = __float2bfloat16_rn(t.e[q] - __bfloat162float(h));
+                        }
+                    }
+                }
+                v[br * N + bc] = t;
+            }
+        }
+        SplitSlotWriter wr;
+        wr.slot_of = slot_of;
+        wr.hi = reinterpret_cast<uint4*>(o.sh);
+        wr.lo = reinterpret_cast<uint4*>(o.sl);
+        wr.slot_q = (long long)a.brows * a.bcols / 8;
+        wr.off_q = ((long long)i * a.bcols + j) / 8;
+        Expand<ALG, BSIDE, false, L, V>::run(v, 0, wr);
+    }
+}
+
+// Both sides in one launch: blocks [0, grid_a) handle A (a, oa), the rest B (b, ob).
+template <int L, int ALG>
+__global__ void __launch_bounds__(256) preadd_split_kernel(const PreaddArgs a, PreaddSplitOut oa, const PreaddArgs b,
+                                                           PreaddSplitOut ob, int grid_a) {
+    __shared__ short slot_of[343];
+    if ((int)blockIdx.x < grid_a) preadd_split_body<L, ALG, false>(a, oa, blockIdx.x, grid_a, slot_of);
+    else preadd_split_body<L, ALG, true>(b, ob, blockIdx.x - grid_a, gridDim.x - grid_a, slot_of);
+}
+
+cudaError_t launch_preadd_split(const PreaddArgs& a, const PreaddSplitOut& oa, const PreaddArgs& b,
+                                const PreaddSplitOut& ob, cudaStream_t s) {
+    if (a.L < 1 || a.L > 2 || a.L != b.L || a.alg != b.alg || a.bt || b.bt || a.bside || !b.bside)
+        return cudaErrorInvalidValue;
+    auto ok = [](const PreaddArgs& p, const PreaddSplitOut& o) {
+        return (p.bcols % 8) == 0 && (p.ldx % 4) == 0 && (o.ldx_out % 8) == 0 &&
+               (reinterpret_cast<uintptr_t>(p.x) & 15) == 0 &&
+               ((reinterpret_cast<uintptr_t>(o.xh) | reinterpret_cast<uintptr_t>(o.xl) |
+                 reinterpret_cast<uintptr_t>(o.sh) | reinterpret_cast<uintptr_t>(o.sl)) & 15) == 0;
+    };
+    if (!ok(a, oa) || !ok(b, ob)) return cudaErrorInvalidValue;
+    const long long wa = (long long)a.brows * a.bcols / 8, wb = (long long)b.brows * b.bcols / 8;
+    if (wa + wb <= 0) return cudaSuccess;
+    const int g = std::max(2, grid_for(wa + wb, 256));
+    const int ga = std::max(1, std::min(g - 1, (int)((g * wa + (wa + wb) / 2) / (wa + wb))));
+    if (a.L == 1) {
+        if (a.alg == 1) preadd_split_kernel<1, 1><<<g, 256, 0, s>>>(a, oa, b, ob, ga);
+        else if (a.alg == 2) preadd_split_kernel<1, 2><<<g, 256, 0, s>>>(a, oa, b, ob, ga);
+        else preadd_split_kernel<1, 3><<<g, 256, 0, s>>>(a, oa, b, ob, ga);
+    } else {
+        if (a.alg == 1) preadd_split_kernel<2, 1><<<g, 256, 0, s>>>(a, oa, b, ob, ga);
+        else if (a.alg == 2) preadd_split_kernel<2, 2><<<g, 256, 0, s>>>(a, oa, b, ob, ga);
+        else preadd_split_kernel<2, 3><<<g, 256, 0, s>>>(a, oa, b, ob, ga);
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_preadd2(const PreaddArgs& a, const PreaddArgs& b, cudaStream_t s) {
     // FP32, vector path, depth 1 or 2, the same algorithm on both sides (else two launches)
     auto vec = [](const PreaddArgs& p) {

@@ -155,7 +155,8 @@ def sw_error_norms(h, elem_bytes, m, n, k, A, lda, B, ldb, C, ldc, R, ldr, strea
 
 
 PROFILE_KINDS = ["gemm_tf32", "gemm_simt", "addsub", "copy_pad", "preadd", "memset", "transpose", "transpose_sq",
-                 "split_bf16", "gemm_bf16x3", "batch_copy", "split_tf32", "gemm_tf32x3"]
+                 "split_bf16", "gemm_bf16x3", "batch_copy", "split_tf32", "gemm_tf32x3",
+                 "preadd_split"]
 
 
 def sw_profile(h, enable: bool) -> int:
