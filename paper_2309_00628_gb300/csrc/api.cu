@@ -143,7 +143,6 @@ struct Op {
     bool nmaj = false;           // TF32 GEMM reading B N-major (launch_gemm_tf32n)
     size_t item_leaf_off = 0;
     size_t leaves_off = 0, targets_off = 0, refs_off = 0, tmaps_off = 0, flags_off = 0;
-    unsigned epoch = 0;  // launches of this op so far (its ordering counters grow by 4 per launch)
     int ngmaps = 0, njobs = 0, tiles = 0, transpose = 0;
     size_t gmaps_off = 0, jobs_off = 0;  // operand maps in global memory; batched copy jobs
     // elementwise
@@ -464,7 +463,7 @@ struct Planner {
         }
         flush_tmaps(o);
         if (nflags > 0) {
-            std::vector<unsigned> zeros(nflags, 0u);
+            std::vector<unsigned> zeros(nflags + 2, 0u);  // + the launch epoch and finished-CTA count
             o.nflags = nflags;
             o.flags_off = put_blob(zeros.data(), zeros.size() * sizeof(unsigned));
         }
@@ -513,7 +512,96 @@ struct Planner {
         std::vector<Leaf> lv(1, lf);
         std::vector<Target> tv(1, t);
         if (pair_ok(o.bn)) to_pair(o, lv);
+        if (o.pair && o.nmaj && mode == TGT_STORE && !batch && !server && split_tail(o, lf, t, c)) return true;
         emit_grouped(o, lv, tv, 0);
+        return true;
+    }
+
+    // A plain product on CTA pairs whose tiles leave the last wave partly idle (T tiles, U pairs,
+    // T mod U != 0): its last R tile rows run as two K halves per tile -- the first half stores,
+    // the second reduce-adds once that store is complete (ordering counters) -- and the work is
+    // laid out explicitly.  In half-tile units every pair then carries at most
+    // max(2 ceil(H / U), ceil(2 T / U)) with H = T - R tiles_n whole tiles, against 2 ceil(T / U)
+    // without the split; R is the fewest tail rows that reach ceil(2 T / U).  Whole tiles keep the
+    // kernel's own raster (groups of 1024 rows, column-major inside a group) in round-robin order,
+    // then the halves fill the least loaded pairs, stores before adds on every pair (so no pair
+    // waits on a store queued behind its own wait).  Returns false to keep the plain launch.
+    bool split_tail(Op o, Leaf lf, const Target& t, View c) {
+        static const bool off = getenv("SWMM_NO_TAIL_SPLIT") != nullptr;  // diagnostics
+        const int units = off ? 0 : gemm_tf32n_pair_units(sms);
+        const int tile_m = 2 * tf32_tile_m();
+        const int tmr = (int)ceil_div(lf.m, tile_m), tn = lf.tiles_n;
+        const long long T = (long long)tmr * tn;
+        if (units <= 0 || T <= units || T % units == 0 || lf.kblocks < 16) return false;
+        const long long best = ceil_div(2 * T, units);
+        if (best >= 2 * ceil_div(T, units)) return false;
+        int R = 1;
+        while (R < tmr && 2 * ceil_div(T - (long long)R * tn, units) > best) ++R;
+        if (R >= tmr) return false;
+        const int head_rows = tmr - R;
+        const int k1 = lf.kblocks / 2;  // k blocks of the first half (a multiple of BK columns)
+        // leaves: 0 whole tiles of the head rows, 1 / 2 the K halves of the tail rows, 3 no-op
+        std::vector<Leaf> leaves(4, lf);
+        leaves[0].m = head_rows * tile_m;
+        View ct = sub(c, (long long)head_rows * tile_m, 0, c.rows - head_rows * tile_m, c.cols, eb);
+        Target ts = make_target(ct, 1.f, TGT_STORE, target_map(ct));
+        ts.flag_base = 0;
+        ts.flag_cols = tn;
+        Target ta = ts;
+        ta.mode = TGT_ATOMIC;
+        std::vector<Target> tg = {t, ts, ta};
+        for (int h = 1; h <= 2; ++h) {
+            Leaf& x = leaves[h];
+            x.a_row = lf.a_row + head_rows * tile_m;
+            x.m = lf.m - head_rows * tile_m;
+            x.a_col = lf.a_col + (h == 2 ? k1 * tf32_tile_k() : 0);
+            x.b_row = lf.b_row + (h == 2 ? k1 * tf32_tile_k() : 0);  // B N-major: rows are K
+            x.kblocks = h == 1 ? k1 : lf.kblocks - k1;
+            x.tgt_begin = h;
+            x.tgt_count = 1;
+        }
+        Leaf& nop = leaves[3];
+        memset(&nop, 0, sizeof(nop));
+        nop.tag = -1;
+        nop.a_map = 0;
+        nop.b_map = 1;
+        nop.tiles_n = 1;
+        // per-unit sequences of (leaf, tile position)
+        std::vector<std::vector<std::pair<int, int>>> seq(units);
+        std::vector<long long> load(units, 0);
+        const int G = std::max(1, 1024 / tile_m);
+        long long next = 0;
+        for (int g0 = 0; g0 < head_rows; g0 += G)
+            for (int cc = 0; cc < tn; ++cc)
+                for (int r = g0; r < std::min(head_rows, g0 + G); ++r, ++next) {
+                    const int u = (int)(next % units);
+                    seq[u].push_back({0, r << 16 | cc});
+                    load[u] += 2;
+                }
+        for (int h = 1; h <= 2; ++h)
+            for (int r = 0; r < R; ++r)
+                for (int cc = 0; cc < tn; ++cc) {
+                    int u = 0;
+                    for (int i = 1; i < units; ++i)
+                        if (load[i] < load[u]) u = i;
+                    seq[u].push_back({h, r << 16 | cc});
+                    load[u] += 1;
+                }
+        size_t tmax = 0;
+        for (const auto& q : seq) tmax = std::max(tmax, q.size());
+        std::vector<int> il(tmax * units, 3), it(tmax * units, 0);
+        for (int u = 0; u < units; ++u)
+            for (size_t i = 0; i < seq[u].size(); ++i) {
+                il[i * units + u] = seq[u][i].first;
+                it[i * units + u] = seq[u][i].second;
+            }
+        o.items = (int)(tmax * units);
+        o.units = units;
+        o.has_layout = true;
+        o.item_leaf_off = put_blob(il.data(), il.size() * sizeof(int));
+        o.item_tile_off = put_blob(it.data(), it.size() * sizeof(int));
+        const int nflags = (int)ceil_div(ct.rows, tf32_tile_m()) * tn;  // one per 128-row half tile
+        emit_grouped(o, leaves, tg, nflags);
         return true;
     }
 
@@ -1520,13 +1608,12 @@ static sw_status run_ops(sw_handle h, Plan* plan, cudaStream_t s, size_t first, 
                 const Target* tv = reinterpret_cast<const Target*>(blob + o.targets_off);
                 const CUtensorMap* tm = o.ntmaps ? reinterpret_cast<const CUtensorMap*>(blob + o.tmaps_off) : nullptr;
                 unsigned* fl = o.nflags ? reinterpret_cast<unsigned*>(blob + o.flags_off) : nullptr;
-                const unsigned ep = o.nflags ? ++o.epoch : 0u;
                 const int* il = (o.has_item_leaf || o.has_layout) ? reinterpret_cast<const int*>(blob + o.item_leaf_off)
                                                                   : nullptr;
                 const int* it = o.has_layout ? reinterpret_cast<const int*>(blob + o.item_tile_off) : nullptr;
-                e = o.nmaj ? launch_gemm_tf32n(o.bn, o.maps, gm, lv, o.nleaves, tv, tm, fl, ep, o.items, h->d_err, h->sms,
+                e = o.nmaj ? launch_gemm_tf32n(o.bn, o.maps, gm, lv, o.nleaves, tv, tm, fl, o.items, h->d_err, h->sms,
                                                s, o.pair, il, it, o.units)
-                           : launch_gemm_tf32(o.bn, o.maps, gm, lv, o.nleaves, tv, tm, fl, ep, o.items, h->d_err,
+                           : launch_gemm_tf32(o.bn, o.maps, gm, lv, o.nleaves, tv, tm, fl, o.items, h->d_err,
                                               h->sms, s, o.pair, il);
             }
                 break;
@@ -1559,7 +1646,7 @@ static sw_status run_ops(sw_handle h, Plan* plan, cudaStream_t s, size_t first, 
                                        o.nleaves, reinterpret_cast<const Target*>(blob + o.targets_off),
                                        o.ntmaps ? reinterpret_cast<const CUtensorMap*>(blob + o.tmaps_off) : nullptr,
                                        o.nflags ? reinterpret_cast<unsigned*>(blob + o.flags_off) : nullptr,
-                                       o.nflags ? ++o.epoch : 0u, o.items, h->d_err, h->sms, s,
+                                       o.items, h->d_err, h->sms, s,
                                        o.has_item_leaf ? reinterpret_cast<const int*>(blob + o.item_leaf_off)
                                                        : nullptr);
                 break;
@@ -1568,7 +1655,7 @@ static sw_status run_ops(sw_handle h, Plan* plan, cudaStream_t s, size_t first, 
                                        o.nleaves, reinterpret_cast<const Target*>(blob + o.targets_off),
                                        o.ntmaps ? reinterpret_cast<const CUtensorMap*>(blob + o.tmaps_off) : nullptr,
                                        o.nflags ? reinterpret_cast<unsigned*>(blob + o.flags_off) : nullptr,
-                                       o.nflags ? ++o.epoch : 0u, o.items, h->d_err, h->sms, s,
+                                       o.items, h->d_err, h->sms, s,
                                        (o.has_item_leaf || o.has_layout)
                                            ? reinterpret_cast<const int*>(blob + o.item_leaf_off)
                                            : nullptr,

@@ -202,7 +202,7 @@ template <int MODE, int BN, bool RES, bool PAIR>
 __global__ void __launch_bounds__(192, 1)
     gemm_tc_kernel(const __grid_constant__ MapSet maps, const CUtensorMap* __restrict__ gmaps,
                      const Leaf* __restrict__ leaves, int nleaves, const Target* __restrict__ targets,
-                     const CUtensorMap* __restrict__ tmaps, unsigned* __restrict__ flags, unsigned epoch,
+                     const CUtensorMap* __restrict__ tmaps, unsigned* __restrict__ flags,
                      int total_items, int* err, const ResidentCtl ctl) {
     static_assert(!PAIR || (MODE != MODE_TF32X3 && !RES), "CTA pairs: TF32 / split-BF16, non-resident only");
     using Cfg = TfCfg<MODE, BN, PAIR>;
@@ -236,6 +236,11 @@ __global__ void __launch_bounds__(192, 1)
     const int nunits = PAIR ? (int)nclusters_x() : (int)gridDim.x;
     // an explicit work layout holds only for the number of units it was planned for
     const bool layout_ok = RES || !ctl.item_tile || nunits == ctl.units;
+    // ordering counters: flags[0] holds the epoch of the last completed launch, flags[1] counts the
+    // CTAs that have finished this one, the per-tile counters follow; every launch (a graph replay
+    // too) adds 4 to each counter it orders on, so this launch waits for 4 * (flags[0] + 1)
+    unsigned* const ctr = flags ? flags + 2 : nullptr;
+    const unsigned epoch = flags ? ld_acquire_u32(flags) + 1u : 0u;
     const int n_items = layout_ok ? total_items : 0;
     if (!layout_ok && threadIdx.x == 0) set_error(err, ERR_UNITS);
 
@@ -537,7 +542,7 @@ __global__ void __launch_bounds__(192, 1)
                     if (__ldg(&targets[tb + t].mode) == TGT_STORE) { has_first = true; continue; }
                     if (lane == 0) {
                         const int idx = fb + (row_t / TF_BM) * __ldg(&targets[tb + t].flag_cols) + col_t / BN;
-                        ordered_ok &= wait_counter(flags + idx, 4u * epoch, err, ERR_ORDER);
+                        ordered_ok &= wait_counter(ctr + idx, 4u * epoch, err, ERR_ORDER);
                     }
                 }
                 if (lane == 0) fence_async_global();
@@ -633,7 +638,7 @@ __global__ void __launch_bounds__(192, 1)
                         const int fb = __ldg(&targets[tb + t].flag_base);
                         if (fb < 0 || __ldg(&targets[tb + t].mode) != TGT_STORE) continue;
                         if (row_t >= __ldg(&targets[tb + t].rows) || col_t >= __ldg(&targets[tb + t].cols)) continue;
-                        red_release_add_u32(flags + fb + (row_t / TF_BM) * __ldg(&targets[tb + t].flag_cols) + col_t / BN,
+                        red_release_add_u32(ctr + fb + (row_t / TF_BM) * __ldg(&targets[tb + t].flag_cols) + col_t / BN,
                                             1u);
                     }
                 }
@@ -659,6 +664,16 @@ __global__ void __launch_bounds__(192, 1)
 
     tc_fence_before();
     __syncthreads();
+    // the last CTA to finish publishes this launch's epoch for the next one (every CTA read the
+    // old value at its start, before it finished)
+    if (flags && threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(flags + 1, 1u) == gridDim.x - 1) {
+            flags[1] = 0u;
+            __threadfence();
+            red_release_add_u32(flags, 1u);
+        }
+    }
     if (PAIR) {
         // no MMA of the pair may still read this CTA's shared memory or write its tensor memory,
         // and neither CTA leaves while the other may still arrive on its barriers
@@ -712,7 +727,7 @@ static cudaError_t tc_setup(int* pairs_out) {
 
 template <int MODE, int BN, bool RES = false, bool PAIR = false>
 static cudaError_t launch_tc_impl(const MapSet& maps, const CUtensorMap* gmaps, const Leaf* leaves, int nleaves,
-                                  const Target* targets, const CUtensorMap* tmaps, unsigned* flags, unsigned epoch,
+                                  const Target* targets, const CUtensorMap* tmaps, unsigned* flags,
                                   int total_items, int* err, int grid, cudaStream_t stream,
                                   const ResidentCtl* ctl = nullptr, const int* item_leaf = nullptr,
                                   const int* item_tile = nullptr, int units = 0) {
@@ -750,12 +765,12 @@ static cudaError_t launch_tc_impl(const MapSet& maps, const CUtensorMap* gmaps, 
         cfg.stream = stream;
         cfg.attrs = at;
         cfg.numAttrs = 1;
-        cudaError_t e = cudaLaunchKernelEx(&cfg, kern, maps, gmaps, leaves, nleaves, targets, tmaps, flags, epoch,
+        cudaError_t e = cudaLaunchKernelEx(&cfg, kern, maps, gmaps, leaves, nleaves, targets, tmaps, flags,
                                            total_items, err, c);
         if (e != cudaSuccess) return e;
         return cudaGetLastError();
     }
-    kern<<<grid, 192, Cfg::SMEM_BYTES, stream>>>(maps, gmaps, leaves, nleaves, targets, tmaps, flags, epoch,
+    kern<<<grid, 192, Cfg::SMEM_BYTES, stream>>>(maps, gmaps, leaves, nleaves, targets, tmaps, flags,
                                                  total_items, err, c);
     return cudaGetLastError();
 }
@@ -766,38 +781,38 @@ cudaError_t launch_gemm_tf32_resident(const CUtensorMap* gmaps, const Leaf* leav
     MapSet none;
     memset(&none, 0, sizeof(none));
     if (nmajor)
-        return launch_tc_impl<MODE_TF32N, 256, true>(none, gmaps, leaves, 0, targets, tmaps, nullptr, 0, 0, err, grid,
+        return launch_tc_impl<MODE_TF32N, 256, true>(none, gmaps, leaves, 0, targets, tmaps, nullptr, 0, err, grid,
                                                      stream, &ctl);
-    return launch_tc_impl<MODE_TF32, 256, true>(none, gmaps, leaves, 0, targets, tmaps, nullptr, 0, 0, err, grid,
+    return launch_tc_impl<MODE_TF32, 256, true>(none, gmaps, leaves, 0, targets, tmaps, nullptr, 0, err, grid,
                                                 stream, &ctl);
 }
 
 cudaError_t launch_gemm_tf32(int bn, const MapSet& maps, const CUtensorMap* gmaps, const Leaf* leaves, int nleaves,
-                             const Target* targets, const CUtensorMap* tmaps, unsigned* flags, unsigned epoch,
+                             const Target* targets, const CUtensorMap* tmaps, unsigned* flags,
                              int total_items, int* err, int grid, cudaStream_t stream, bool pair,
                              const int* item_leaf) {
     if (pair)
-        return launch_tc_impl<MODE_TF32, 256, false, true>(maps, gmaps, leaves, nleaves, targets, tmaps, flags, epoch,
+        return launch_tc_impl<MODE_TF32, 256, false, true>(maps, gmaps, leaves, nleaves, targets, tmaps, flags,
                                                            total_items, err, grid, stream, nullptr, item_leaf);
     if (bn == 256)
-        return launch_tc_impl<MODE_TF32, 256>(maps, gmaps, leaves, nleaves, targets, tmaps, flags, epoch, total_items,
+        return launch_tc_impl<MODE_TF32, 256>(maps, gmaps, leaves, nleaves, targets, tmaps, flags, total_items,
                                               err, grid, stream, nullptr, item_leaf);
-    return launch_tc_impl<MODE_TF32, 128>(maps, gmaps, leaves, nleaves, targets, tmaps, flags, epoch, total_items, err,
+    return launch_tc_impl<MODE_TF32, 128>(maps, gmaps, leaves, nleaves, targets, tmaps, flags, total_items, err,
                                           grid, stream, nullptr, item_leaf);
 }
 
 cudaError_t launch_gemm_tf32n(int bn, const MapSet& maps, const CUtensorMap* gmaps, const Leaf* leaves, int nleaves,
-                              const Target* targets, const CUtensorMap* tmaps, unsigned* flags, unsigned epoch,
+                              const Target* targets, const CUtensorMap* tmaps, unsigned* flags,
                               int total_items, int* err, int grid, cudaStream_t stream, bool pair,
                               const int* item_leaf, const int* item_tile, int units) {
     if (pair)
         return launch_tc_impl<MODE_TF32N, 256, false, true>(maps, gmaps, leaves, nleaves, targets, tmaps, flags,
-                                                            epoch, total_items, err, grid, stream, nullptr, item_leaf,
+                                                            total_items, err, grid, stream, nullptr, item_leaf,
                                                             item_tile, units);
     if (bn == 256)
-        return launch_tc_impl<MODE_TF32N, 256>(maps, gmaps, leaves, nleaves, targets, tmaps, flags, epoch,
+        return launch_tc_impl<MODE_TF32N, 256>(maps, gmaps, leaves, nleaves, targets, tmaps, flags,
                                                total_items, err, grid, stream, nullptr, item_leaf, item_tile, units);
-    return launch_tc_impl<MODE_TF32N, 128>(maps, gmaps, leaves, nleaves, targets, tmaps, flags, epoch, total_items,
+    return launch_tc_impl<MODE_TF32N, 128>(maps, gmaps, leaves, nleaves, targets, tmaps, flags, total_items,
                                            err, grid, stream, nullptr, item_leaf, item_tile, units);
 }
 
@@ -814,27 +829,27 @@ int gemm_bf16x3_pair_units(int sms) {
 }
 
 cudaError_t launch_gemm_tf32x3(int bn, const MapSet& maps, const CUtensorMap* gmaps, const Leaf* leaves, int nleaves,
-                               const Target* targets, const CUtensorMap* tmaps, unsigned* flags, unsigned epoch,
+                               const Target* targets, const CUtensorMap* tmaps, unsigned* flags,
                                int total_items, int* err, int grid, cudaStream_t stream, const int* item_leaf) {
     if (bn == 256)
-        return launch_tc_impl<MODE_TF32X3, 256>(maps, gmaps, leaves, nleaves, targets, tmaps, flags, epoch,
+        return launch_tc_impl<MODE_TF32X3, 256>(maps, gmaps, leaves, nleaves, targets, tmaps, flags,
                                                 total_items, err, grid, stream, nullptr, item_leaf);
-    return launch_tc_impl<MODE_TF32X3, 128>(maps, gmaps, leaves, nleaves, targets, tmaps, flags, epoch, total_items,
+    return launch_tc_impl<MODE_TF32X3, 128>(maps, gmaps, leaves, nleaves, targets, tmaps, flags, total_items,
                                             err, grid, stream, nullptr, item_leaf);
 }
 
 cudaError_t launch_gemm_bf16x3(int bn, const MapSet& maps, const CUtensorMap* gmaps, const Leaf* leaves, int nleaves,
-                               const Target* targets, const CUtensorMap* tmaps, unsigned* flags, unsigned epoch,
+                               const Target* targets, const CUtensorMap* tmaps, unsigned* flags,
                                int total_items, int* err, int grid, cudaStream_t stream, const int* item_leaf,
                                const int* item_tile, int units, bool pair) {
     if (pair)
         return launch_tc_impl<MODE_BF16X3, 256, false, true>(maps, gmaps, leaves, nleaves, targets, tmaps, flags,
-                                                             epoch, total_items, err, grid, stream, nullptr, item_leaf,
+                                                             total_items, err, grid, stream, nullptr, item_leaf,
                                                              item_tile, units);
     if (bn == 256)
-        return launch_tc_impl<MODE_BF16X3, 256>(maps, gmaps, leaves, nleaves, targets, tmaps, flags, epoch,
+        return launch_tc_impl<MODE_BF16X3, 256>(maps, gmaps, leaves, nleaves, targets, tmaps, flags,
                                                 total_items, err, grid, stream, nullptr, item_leaf, item_tile, units);
-    return launch_tc_impl<MODE_BF16X3, 128>(maps, gmaps, leaves, nleaves, targets, tmaps, flags, epoch, total_items,
+    return launch_tc_impl<MODE_BF16X3, 128>(maps, gmaps, leaves, nleaves, targets, tmaps, flags, total_items,
                                             err, grid, stream, nullptr, item_leaf, item_tile, units);
 }
 

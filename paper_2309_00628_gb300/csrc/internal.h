@@ -31,7 +31,7 @@ struct MatRef {
 // of SMs to use (rounded down to whole pairs).  item_leaf: optional device table of the leaf of
 // every work item (saves the per-tile binary search over the leaves; nullptr: search).
 cudaError_t launch_gemm_tf32(int bn, const MapSet& maps, const CUtensorMap* gmaps, const Leaf* leaves, int nleaves,
-                             const Target* targets, const CUtensorMap* tmaps, unsigned* flags, unsigned epoch,
+                             const Target* targets, const CUtensorMap* tmaps, unsigned* flags,
                              int total_items, int* err, int grid, cudaStream_t stream, bool pair = false,
                              const int* item_leaf = nullptr);
 // TF32 leaves with B N-major (k x n as stored; maps from make_map_f32_n, Leaf::b_row = K,
@@ -40,7 +40,7 @@ cudaError_t launch_gemm_tf32(int bn, const MapSet& maps, const CUtensorMap* gmap
 // leaf) planned for exactly `units` persistent units; the launch uses that many (accumulation
 // chains rely on unit u taking items u, u + units, ...).
 cudaError_t launch_gemm_tf32n(int bn, const MapSet& maps, const CUtensorMap* gmaps, const Leaf* leaves, int nleaves,
-                              const Target* targets, const CUtensorMap* tmaps, unsigned* flags, unsigned epoch,
+                              const Target* targets, const CUtensorMap* tmaps, unsigned* flags,
                               int total_items, int* err, int grid, cudaStream_t stream, bool pair = false,
                               const int* item_leaf = nullptr, const int* item_tile = nullptr, int units = 0);
 // Persistent units (CTA pairs) of a pair-form N-major TF32 launch on `sms` SMs (0: unavailable).
@@ -57,7 +57,7 @@ int bf16x3_tile_k();
 // Split-BF16 leaves: operand map index i refers to maps 2i (hi) and 2i+1 (lo); B is N-major
 // (k x n as stored); Leaf::kblocks counts 64-deep k blocks.
 cudaError_t launch_gemm_bf16x3(int bn, const MapSet& maps, const CUtensorMap* gmaps, const Leaf* leaves, int nleaves,
-                               const Target* targets, const CUtensorMap* tmaps, unsigned* flags, unsigned epoch,
+                               const Target* targets, const CUtensorMap* tmaps, unsigned* flags,
                                int total_items, int* err, int grid, cudaStream_t stream,
                                const int* item_leaf = nullptr, const int* item_tile = nullptr, int units = 0,
                                bool pair = false);
@@ -68,7 +68,7 @@ int gemm_bf16x3_pair_units(int sms);
 // with hi = tf32(x), lo = x - hi; A K-major (make_map_f32, 128-row boxes), B N-major
 // (make_map_f32_n); Leaf::kblocks counts 32-deep k blocks.
 cudaError_t launch_gemm_tf32x3(int bn, const MapSet& maps, const CUtensorMap* gmaps, const Leaf* leaves, int nleaves,
-                               const Target* targets, const CUtensorMap* tmaps, unsigned* flags, unsigned epoch,
+                               const Target* targets, const CUtensorMap* tmaps, unsigned* flags,
                                int total_items, int* err, int grid, cudaStream_t stream,
                                const int* item_leaf = nullptr);
 // hi = tf32(x) (round to nearest, ties away), lo = x - hi (exact), elementwise on a rows x cols

@@ -223,7 +223,7 @@ extern "C" sw_status sw_smm_noalloc(const float* A, int lda, const float* B, int
     int sms = 148;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
-        e = swk::launch_gemm_tf32(bn, maps, nullptr, leaves, 7, targets, nullptr, nullptr, 0, 7 * tiles_per_leaf, err,
+        e = swk::launch_gemm_tf32(bn, maps, nullptr, leaves, 7, targets, nullptr, nullptr, 7 * tiles_per_leaf, err,
                                   sms, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     int code = 0;

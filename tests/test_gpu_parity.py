@@ -468,3 +468,47 @@ def test_fused_depth1_wide_quadrants_integers_bit_exact(h, leaf, algo, m, n, k):
     assert exact_int_safe(4, k, 1)
     A, B = inputs.pair(m, n, k, "int", seed=90, dtype=np.float64, lim=4)
     assert np.array_equal(run(h, A, B, cutoff, v), oracle.naive(A, B)), (algo, m, n, k)
+
+
+@pytest.mark.parametrize("leaf", [swmm.SW_LEAF_TF32, swmm.SW_LEAF_BF16X3])
+def test_ordered_depth1_graph_replay_integers_bit_exact(h, leaf):
+    # a depth-1 product whose C blocks take a store then reduce-adds (ordering counters) captured
+    # once into a CUDA graph and replayed on new data in the same buffers: every replay orders its
+    # adds after its own stores (the launch epoch lives on the device, not in the captured args)
+    m = n = k = 1536
+    cutoff = 1000
+    v = W | FUSED | leaf
+    assert depth(h, m, n, k, cutoff, v, 4) == 1
+    dA = torch.zeros((m, k), dtype=torch.float32, device="cuda")
+    dB = torch.zeros((k, n), dtype=torch.float32, device="cuda")
+    dC = torch.zeros((m, n), dtype=torch.float32, device="cuda")
+    args = (ctypes.c_void_p(dA.data_ptr()), k, ctypes.c_void_p(dB.data_ptr()), n, ctypes.c_void_p(dC.data_ptr()), n,
+            m, n, k, cutoff, v)
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        # plan once outside the capture (the plan's upload is not capturable)
+        swmm.check(h, swmm.sw_smm(h, *args, ctypes.c_void_p(side.cuda_stream)))
+    side.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        st = swmm.sw_smm(h, *args, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    swmm.check(h, st)
+    for seed in (91, 92, 93):
+        A, B = inputs.pair(m, n, k, "int", seed=seed, dtype=np.float64, lim=4)
+        dA.copy_(torch.from_numpy(A.astype(np.float32)))
+        dB.copy_(torch.from_numpy(B.astype(np.float32)))
+        dC.fill_(float("nan"))
+        g.replay()
+        torch.cuda.synchronize()
+        swmm.check(h, swmm.sw_sync(h, None))
+        assert np.array_equal(dC.cpu().numpy().astype(np.float64), oracle.naive_mt(A, B)), seed
+
+
+@pytest.mark.parametrize("m,n,k", [(4096, 4096, 4096), (2000, 3000, 1000), (4100, 2304, 700)])
+def test_plain_tail_split_integers_bit_exact(h, m, n, k):
+    # plain products whose 256 x 256 tiles leave the last wave of CTA pairs partly idle: the last
+    # tile rows run as two K halves (a store, then a reduce-add ordered after it), including a
+    # ragged last tile row and a ragged last k block
+    A, B = inputs.pair(m, n, k, "int", seed=95, dtype=np.float64, lim=4)
+    assert exact_int_safe(4, k, 0)
+    assert np.array_equal(run(h, A, B, 0, swmm.SW_ALGO_NAIVE), oracle.naive_mt(A, B)), (m, n, k)
