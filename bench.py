@@ -622,6 +622,43 @@ def main():
             cfg3.append({"variant": lab, "ms": ms3, "eff_tflops": 2.0 * n2 ** 3 / (ms3 / 1e3) / 1e12, "err": err3,
                          "workspace_bytes": ws3 if st3 == swmm.SW_OK else None})
         del A2, B2, C2
+        # FP64 (FP64-ALU bound on this part): n = 4096 uniform[-1, 1], the plain SIMT product, Winograd
+        # depth 3 with plain FP64 leaves and with the Winograd-step leaf tiles; cuBLAS DGEMM (torch)
+        # as context; error on 8 sampled rows of the FP64 oracle
+        n4 = n // 2
+        g4 = torch.Generator(device="cuda")
+        g4.manual_seed(12)
+        A4 = torch.rand((n4, n4), generator=g4, device="cuda", dtype=torch.float64) * 2 - 1
+        B4 = torch.rand((n4, n4), generator=g4, device="cuda", dtype=torch.float64) * 2 - 1
+        C4 = torch.empty((n4, n4), device="cuda", dtype=torch.float64)
+        sel4 = np.sort(np.random.Generator(np.random.PCG64(9)).choice(n4, 8, replace=False))
+        A4h, B4h = A4.cpu().numpy(), B4.cpu().numpy()
+        R4 = oracle.naive_mt(A4h[sel4], B4h, oracle.max_threads())
+        scale4 = n4 * float(np.max(np.abs(A4h))) * float(np.max(np.abs(B4h)))
+        idx4 = torch.from_numpy(sel4).cuda()
+        fp64 = []
+        for lab, v, c in (("plain (SIMT leaf)", swmm.SW_ALGO_NAIVE, 0),
+                          ("winograd L3", swmm.SW_ALGO_WINOGRAD | swmm.SW_SCHED_FUSED, n4 >> 3),
+                          ("winograd L3 + tile step", swmm.SW_ALGO_WINOGRAD | swmm.SW_SCHED_FUSED |
+                           swmm.SW_LEAF_F64_WTILE, n4 >> 3),
+                          ("cublas dgemm (torch, context)", None, 0)):
+            def run4():
+                if v is None:
+                    torch.matmul(A4, B4, out=C4)
+                else:
+                    swmm.check(h, swmm.sw_dmm(h, p(A4), n4, p(B4), n4, p(C4), n4, n4, n4, n4, c, v, sp))
+            run4()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(3):
+                run4()
+            e1.record(stream)
+            swmm.check(h, swmm.sw_sync(h, sp))
+            ms4 = e0.elapsed_time(e1) / 3
+            err4 = float(np.max(np.abs(C4[idx4].cpu().numpy() - R4)) / scale4)
+            fp64.append({"variant": lab, "depth": swmm.sw_mm_depth(n4, n4, n4, c, v, 8)[1] if v is not None else 0,
+                         "ms": ms4, "eff_tflops": 2.0 * n4 ** 3 / (ms4 / 1e3) / 1e12, "err": err4})
+        del A4, B4, C4
         # peak workspace of each schedule for the n = 16384 split-BF16 configuration (depth 2)
         ws = {}
         for lab, sc in (("alloc", swmm.SW_SCHED_ALLOC), ("two_temp", swmm.SW_SCHED_TWO_TEMP),
@@ -640,6 +677,7 @@ def main():
                  "n16384_tf32": big,
                  "fp32_accuracy_n16384_normal_bf16x3": cfg3,
                  "workspace_bytes_n16384_L2_bf16x3": ws,
+                 "fp64_n4096": fp64,
                  "err_metric": "max|C - C_oracle| / (n max|A| max|B|) on the sampled oracle rows"}
 
     if rank == 0:

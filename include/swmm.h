@@ -47,7 +47,15 @@
  *                                 lo*hi + hi*lo + hi*hi with FP32 accumulation: a finer operand
  *                                 split than SW_LEAF_BF16X3 at half its tensor rate (on uniform
  *                                 data both reach the FP32-accumulation floor)
- *   The FP64 entry points ignore the leaf group and always use FP64 leaves.
+ *               SW_LEAF_F64_WTILE FP64 entry points only, with the Winograd algorithms: the FP64
+ *                                 leaf GEMM takes one more Winograd step inside each 64 x 64 output
+ *                                 tile (its 2 x 2 blocks of 32 x 32; the inner dimension split into
+ *                                 the first and last 8 indices of every 16-deep block), with the
+ *                                 operand sums formed in shared memory: 7/8 of the leaf's FP64
+ *                                 multiply-adds (a register-level base case, like the paper's
+ *                                 unrolled small Winograd products, Sec. 3.2).  SW_EINVAL on the
+ *                                 FP32 entries, SW_EUNSUPPORTED with SW_ALGO_NAIVE / STRASSEN.
+ *   The FP64 entry points ignore the FP32 leaf kinds (TF32, BF16X3, TF32X3): their leaves are FP64.
  *
  * Recursion depth L (Sec. 3.4 cutoff): halve while min(ceil(m/2^l), ceil(n/2^l), ceil(k/2^l))
  * > cutoff.  SW_ALGO_NAIVE ignores the cutoff.  cutoff <= 0 asks the library's autotuner: the
@@ -94,6 +102,7 @@ typedef enum {
 #define SW_LEAF_TF32 0x0000u
 #define SW_LEAF_BF16X3 0x1000u
 #define SW_LEAF_TF32X3 0x2000u
+#define SW_LEAF_F64_WTILE 0x3000u
 #define SW_LEAF_MASK 0xF000u
 
 typedef struct sw_handle_s *sw_handle;

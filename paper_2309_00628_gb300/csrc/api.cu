@@ -155,6 +155,7 @@ struct Op {
     PreaddArgs pre;
     PreaddArgs pre_b;       // FP32: the B side of the same pass (pre_two: one launch for both)
     bool pre_two = false;
+    bool wtile = false;     // OP_GEMM_SIMT (FP64): one Winograd step inside every 64 x 64 tile
     PreaddSplitOut sout;    // OP_PREADD_SPLIT: bf16 halves of A and of its sums (sout_b: of B)
     PreaddSplitOut sout_b;
 };
@@ -191,6 +192,7 @@ struct Planner {
     int eb;                 // 4 = FP32 (TF32 or split-BF16 leaves), 8 = FP64
     bool bf;                // FP32 with split-BF16 leaves
     bool x3 = false;        // FP32 with compensated-TF32 leaves (FP32 hi / lo halves)
+    bool wtile = false;     // FP64 leaves: one Winograd step inside every 64 x 64 tile
     bool bt;                // B side stored transposed (TF32 leaves read through B^T)
     bool nmaj = false;      // TF32 leaves read B N-major, as stored (bt is then false)
     uint32_t variant;
@@ -512,96 +514,7 @@ struct Planner {
         std::vector<Leaf> lv(1, lf);
         std::vector<Target> tv(1, t);
         if (pair_ok(o.bn)) to_pair(o, lv);
-        if (o.pair && o.nmaj && mode == TGT_STORE && !batch && !server && split_tail(o, lf, t, c)) return true;
         emit_grouped(o, lv, tv, 0);
-        return true;
-    }
-
-    // A plain product on CTA pairs whose tiles leave the last wave partly idle (T tiles, U pairs,
-    // T mod U != 0): its last R tile rows run as two K halves per tile -- the first half stores,
-    // the second reduce-adds once that store is complete (ordering counters) -- and the work is
-    // laid out explicitly.  In half-tile units every pair then carries at most
-    // max(2 ceil(H / U), ceil(2 T / U)) with H = T - R tiles_n whole tiles, against 2 ceil(T / U)
-    // without the split; R is the fewest tail rows that reach ceil(2 T / U).  Whole tiles keep the
-    // kernel's own raster (groups of 1024 rows, column-major inside a group) in round-robin order,
-    // then the halves fill the least loaded pairs, stores before adds on every pair (so no pair
-    // waits on a store queued behind its own wait).  Returns false to keep the plain launch.
-    bool split_tail(Op o, Leaf lf, const Target& t, View c) {
-        static const bool off = getenv("SWMM_NO_TAIL_SPLIT") != nullptr;  // diagnostics
-        const int units = off ? 0 : gemm_tf32n_pair_units(sms);
-        const int tile_m = 2 * tf32_tile_m();
-        const int tmr = (int)ceil_div(lf.m, tile_m), tn = lf.tiles_n;
-        const long long T = (long long)tmr * tn;
-        if (units <= 0 || T <= units || T % units == 0 || lf.kblocks < 16) return false;
-        const long long best = ceil_div(2 * T, units);
-        if (best >= 2 * ceil_div(T, units)) return false;
-        int R = 1;
-        while (R < tmr && 2 * ceil_div(T - (long long)R * tn, units) > best) ++R;
-        if (R >= tmr) return false;
-        const int head_rows = tmr - R;
-        const int k1 = lf.kblocks / 2;  // k blocks of the first half (a multiple of BK columns)
-        // leaves: 0 whole tiles of the head rows, 1 / 2 the K halves of the tail rows, 3 no-op
-        std::vector<Leaf> leaves(4, lf);
-        leaves[0].m = head_rows * tile_m;
-        View ct = sub(c, (long long)head_rows * tile_m, 0, c.rows - head_rows * tile_m, c.cols, eb);
-        Target ts = make_target(ct, 1.f, TGT_STORE, target_map(ct));
-        ts.flag_base = 0;
-        ts.flag_cols = tn;
-        Target ta = ts;
-        ta.mode = TGT_ATOMIC;
-        std::vector<Target> tg = {t, ts, ta};
-        for (int h = 1; h <= 2; ++h) {
-            Leaf& x = leaves[h];
-            x.a_row = lf.a_row + head_rows * tile_m;
-            x.m = lf.m - head_rows * tile_m;
-            x.a_col = lf.a_col + (h == 2 ? k1 * tf32_tile_k() : 0);
-            x.b_row = lf.b_row + (h == 2 ? k1 * tf32_tile_k() : 0);  // B N-major: rows are K
-            x.kblocks = h == 1 ? k1 : lf.kblocks - k1;
-            x.tgt_begin = h;
-            x.tgt_count = 1;
-        }
-        Leaf& nop = leaves[3];
-        memset(&nop, 0, sizeof(nop));
-        nop.tag = -1;
-        nop.a_map = 0;
-        nop.b_map = 1;
-        nop.tiles_n = 1;
-        // per-unit sequences of (leaf, tile position)
-        std::vector<std::vector<std::pair<int, int>>> seq(units);
-        std::vector<long long> load(units, 0);
-        const int G = std::max(1, 1024 / tile_m);
-        long long next = 0;
-        for (int g0 = 0; g0 < head_rows; g0 += G)
-            for (int cc = 0; cc < tn; ++cc)
-                for (int r = g0; r < std::min(head_rows, g0 + G); ++r, ++next) {
-                    const int u = (int)(next % units);
-                    seq[u].push_back({0, r << 16 | cc});
-                    load[u] += 2;
-                }
-        for (int h = 1; h <= 2; ++h)
-            for (int r = 0; r < R; ++r)
-                for (int cc = 0; cc < tn; ++cc) {
-                    int u = 0;
-                    for (int i = 1; i < units; ++i)
-                        if (load[i] < load[u]) u = i;
-                    seq[u].push_back({h, r << 16 | cc});
-                    load[u] += 1;
-                }
-        size_t tmax = 0;
-        for (const auto& q : seq) tmax = std::max(tmax, q.size());
-        std::vector<int> il(tmax * units, 3), it(tmax * units, 0);
-        for (int u = 0; u < units; ++u)
-            for (size_t i = 0; i < seq[u].size(); ++i) {
-                il[i * units + u] = seq[u][i].first;
-                it[i * units + u] = seq[u][i].second;
-            }
-        o.items = (int)(tmax * units);
-        o.units = units;
-        o.has_layout = true;
-        o.item_leaf_off = put_blob(il.data(), il.size() * sizeof(int));
-        o.item_tile_off = put_blob(it.data(), it.size() * sizeof(int));
-        const int nflags = (int)ceil_div(ct.rows, tf32_tile_m()) * tn;  // one per 128-row half tile
-        emit_grouped(o, leaves, tg, nflags);
         return true;
     }
 
@@ -677,6 +590,7 @@ struct Planner {
         Op o;
         o.kind = OP_GEMM_SIMT;
         o.eb = eb;
+        o.wtile = wtile && eb == 8;
         MatRef refs[2] = {{a.p, a.ld, a.rows, a.cols}, {b.p, b.ld, b.rows, b.cols}};
         o.refs_off = put_blob(refs, sizeof(refs));
         o.items = (int)(ceil_div(c.rows, F64_BM) * lf.tiles_n);
@@ -1262,6 +1176,7 @@ struct Planner {
         } else {
             o.kind = OP_GEMM_SIMT;
             o.eb = 8;
+            o.wtile = wtile;
             MatRef refs[4] = {{A.p, A.ld, m, k}, {B.p, B.ld, k, n}, {SA.p, SA.ld, SA.rows, kb},
                               {SB.p, SB.ld, SB.rows, nb}};
             o.refs_off = put_blob(refs, sizeof(refs));
@@ -1467,7 +1382,11 @@ static sw_status build_plan(sw_handle h, int eb, const void* A, int lda, const v
     if (sched > SW_SCHED_ALLOC) return fail(h, SW_EINVAL, "unknown schedule bits");
     if (algo == SW_ALGO_WINOGRAD_KNUTH && sched != SW_SCHED_FUSED)
         return fail(h, SW_EUNSUPPORTED, "Knuth's form runs in the FUSED schedule");
-    if ((variant & SW_LEAF_MASK) > SW_LEAF_TF32X3) return fail(h, SW_EINVAL, "unknown leaf bits");
+    const uint32_t leaf = variant & SW_LEAF_MASK;
+    if (leaf > SW_LEAF_F64_WTILE) return fail(h, SW_EINVAL, "unknown leaf bits");
+    if (leaf == SW_LEAF_F64_WTILE && eb != 8) return fail(h, SW_EINVAL, "SW_LEAF_F64_WTILE is an FP64 leaf");
+    if (leaf == SW_LEAF_F64_WTILE && algo != SW_ALGO_WINOGRAD && algo != SW_ALGO_WINOGRAD_KNUTH)
+        return fail(h, SW_EUNSUPPORTED, "Winograd-step leaf tiles go with the Winograd variants");
     if (algo == SW_ALGO_STRASSEN && (sched == SW_SCHED_TWO_TEMP || sched == SW_SCHED_IN_PLACE))
         return fail(h, SW_EUNSUPPORTED, "Tables 2 and 3 are Winograd schedules");
     if (sched == SW_SCHED_IN_PLACE && algo != SW_ALGO_NAIVE && !(m == n && n == k))
@@ -1481,6 +1400,7 @@ static sw_status build_plan(sw_handle h, int eb, const void* A, int lda, const v
     P.eb = eb;
     P.bf = bf_only;
     P.x3 = x3;
+    P.wtile = eb == 8 && leaf == SW_LEAF_F64_WTILE;
     // TF32 leaves read B N-major, as stored (no B^T staging); SWMM_TF32_BT=1 selects the B^T form
     // everywhere (diagnostics)
     P.nmaj = eb == 4 && !bf && !tf32_bt_form();
@@ -1620,7 +1540,7 @@ static sw_status run_ops(sw_handle h, Plan* plan, cudaStream_t s, size_t first, 
             case OP_GEMM_SIMT:
                 e = launch_gemm_simt(o.eb, reinterpret_cast<const MatRef*>(blob + o.refs_off),
                                      reinterpret_cast<const Leaf*>(blob + o.leaves_off), o.nleaves,
-                                     reinterpret_cast<const Target*>(blob + o.targets_off), o.items, h->sms * 8, s);
+                                     reinterpret_cast<const Target*>(blob + o.targets_off), o.items, h->sms * 8, o.wtile, s);
                 break;
             case OP_TRANSPOSE:
                 e = launch_transpose_pad(o.rows, o.cols, static_cast<float*>(o.z), o.ldz,

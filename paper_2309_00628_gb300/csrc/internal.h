@@ -82,8 +82,9 @@ cudaError_t launch_split_bf16(int rows, int cols, const float* x, long long ldx,
 
 // SIMT leaf GEMM (FP64, or FP32 when elem_bytes == 4): same leaf / target descriptors,
 // a_map / b_map index `refs`, B stored as is (k x n); Leaf::kblocks is the inner dimension.
+// wtile (FP64): every 64 x 64 tile takes one Winograd step over its 2 x 2 blocks.
 cudaError_t launch_gemm_simt(int elem_bytes, const MatRef* refs, const Leaf* leaves, int nleaves,
-                             const Target* targets, int total_items, int grid, cudaStream_t stream);
+                             const Target* targets, int total_items, int grid, bool wtile, cudaStream_t stream);
 constexpr int F64_BM = 64, F64_BN = 64;
 
 // out (out_rows x out_cols) <- x^T, zero outside the source extent (src_rows x src_cols).

@@ -581,11 +581,143 @@ __global__ void __launch_bounds__(256) gemm_simt_kernel(const MatRef* __restrict
     }
 }
 
+// FP64 leaf tiles with one Winograd step inside (the BDPZ form of Sec. 2.3, taken as a base case
+// at the bottom of the recursion in the spirit of Sec. 3.2's unrolled products).  The 64 x 64 output tile
+// is a 2 x 2 grid of 32 x 32 blocks; the inner dimension is split into two halves K1 / K2 (the
+// first and the last 8 columns of every 16-deep k block), so A11 = rows 0..31 x K1, A12 = rows
+// 0..31 x K2, A21 / A22 the same for rows 32..63, and B11 = K1 x columns 0..31, B12 = K1 x
+// columns 32..63, B21 / B22 the same over K2.  Per k block the CTA forms S1..S4 and T1..T4 in
+// shared memory and every thread accumulates a 2 x 2 piece of each of the seven 32 x 32
+// products P1..P7; the epilogue combines them in the order of the post-additions U1..U7.
+// FP64 FMAs are the bound on this part: 7 x 32 x 32 x 8 FMAs and 2 x 4 x 32 x 8 additions per k
+// block against 64 x 64 x 16 FMAs for the plain tile.
+__global__ void __launch_bounds__(256) gemm_simt_wtile_kernel(const MatRef* __restrict__ refs,
+                                                              const Leaf* __restrict__ leaves, int nleaves,
+                                                              const Target* __restrict__ targets, int total_items) {
+    constexpr int H = SIMT_BK / 2, Q = F64_BM / 2, LD = F64_BM + 2;  // +2: 16-byte rows, fewer conflicts
+    static_assert(F64_BM == F64_BN && Q == 32, "64 x 64 tiles");
+    __shared__ __align__(16) double As[SIMT_BK][LD];  // k-major: As[k][row]
+    __shared__ __align__(16) double Bs[SIMT_BK][LD];  // Bs[k][col]
+    __shared__ __align__(16) double Ss[4][H][Q];      // S1..S4 [k][row]
+    __shared__ __align__(16) double Ts[4][H][Q];      // T1..T4 [k][col]
+    const int r0 = 2 * (threadIdx.x >> 4), c0 = 2 * (threadIdx.x & 15);  // this thread's 2 x 2 piece
+    for (int item = blockIdx.x; item < total_items; item += gridDim.x) {
+        int lo = 0, hi = nleaves - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (leaves[mid].tile_begin <= item) lo = mid; else hi = mid - 1;
+        }
+        const Leaf Lf = leaves[lo];
+        const int local = item - Lf.tile_begin;
+        const int tm = local / Lf.tiles_n, tn = local - tm * Lf.tiles_n;
+        const MatRef A = refs[Lf.a_map], B = refs[Lf.b_map];
+        const double* Ap = reinterpret_cast<const double*>(A.p);
+        const double* Bp = reinterpret_cast<const double*>(B.p);
+        const int K = Lf.kblocks;  // the inner dimension in elements
+        double acc[7][2][2];
+#pragma unroll
+        for (int p = 0; p < 7; ++p)
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int j = 0; j < 2; ++j) acc[p][i][j] = 0.0;
+        for (int k0 = 0; k0 < K; k0 += SIMT_BK) {
+            for (int e = threadIdx.x; e < F64_BM * SIMT_BK; e += 256) {
+                const int r = e / SIMT_BK, c = e - r * SIMT_BK;
+                const int gr = Lf.a_row + tm * F64_BM + r, gc = Lf.a_col + k0 + c;
+                const bool in = (tm * F64_BM + r) < Lf.m && (k0 + c) < K && gr < A.rows && gc < A.cols;
+                As[c][r] = in ? Ap[gr * A.ld + gc] : 0.0;
+            }
+            for (int e = threadIdx.x; e < SIMT_BK * F64_BN; e += 256) {
+                const int r = e / F64_BN, c = e - r * F64_BN;
+                const int gr = Lf.b_row + k0 + r, gc = Lf.b_col + tn * F64_BN + c;
+                const bool in = (k0 + r) < K && (tn * F64_BN + c) < Lf.n && gr < B.rows && gc < B.cols;
+                Bs[r][c] = in ? Bp[gr * B.ld + gc] : 0.0;
+            }
+            __syncthreads();
+            {  // operand sums: one (k, row) of the 8 x 32 grid per thread, both sides
+                const int kk = threadIdx.x >> 5, i = threadIdx.x & 31;
+                const double a11 = As[kk][i], a12 = As[H + kk][i], a21 = As[kk][Q + i], a22 = As[H + kk][Q + i];
+                const double s1 = a21 + a22, s2 = s1 - a11, s3 = a11 - a21, s4 = a12 - s2;
+                Ss[0][kk][i] = s1;
+                Ss[1][kk][i] = s2;
+                Ss[2][kk][i] = s3;
+                Ss[3][kk][i] = s4;
+                const double b11 = Bs[kk][i], b12 = Bs[kk][Q + i], b21 = Bs[H + kk][i], b22 = Bs[H + kk][Q + i];
+                const double t1 = b12 - b11, t2 = b22 - t1, t3 = b22 - b12, t4 = t2 - b21;
+                Ts[0][kk][i] = t1;
+                Ts[1][kk][i] = t2;
+                Ts[2][kk][i] = t3;
+                Ts[3][kk][i] = t4;
+            }
+            __syncthreads();
+#pragma unroll 2
+            for (int kk = 0; kk < H; ++kk) {
+                // P1 = A11 B11, P2 = A12 B21, P3 = S4 B22, P4 = A22 T4, P5 = S1 T1, P6 = S2 T2, P7 = S3 T3
+                const double2 a[7] = {*reinterpret_cast<const double2*>(&As[kk][r0]),
+                                      *reinterpret_cast<const double2*>(&As[H + kk][r0]),
+                                      *reinterpret_cast<const double2*>(&Ss[3][kk][r0]),
+                                      *reinterpret_cast<const double2*>(&As[H + kk][Q + r0]),
+                                      *reinterpret_cast<const double2*>(&Ss[0][kk][r0]),
+                                      *reinterpret_cast<const double2*>(&Ss[1][kk][r0]),
+                                      *reinterpret_cast<const double2*>(&Ss[2][kk][r0])};
+                const double2 b[7] = {*reinterpret_cast<const double2*>(&Bs[kk][c0]),
+                                      *reinterpret_cast<const double2*>(&Bs[H + kk][c0]),
+                                      *reinterpret_cast<const double2*>(&Bs[H + kk][Q + c0]),
+                                      *reinterpret_cast<const double2*>(&Ts[3][kk][c0]),
+                                      *reinterpret_cast<const double2*>(&Ts[0][kk][c0]),
+                                      *reinterpret_cast<const double2*>(&Ts[1][kk][c0]),
+                                      *reinterpret_cast<const double2*>(&Ts[2][kk][c0])};
+#pragma unroll
+                for (int p = 0; p < 7; ++p) {
+                    acc[p][0][0] = fma(a[p].x, b[p].x, acc[p][0][0]);
+                    acc[p][0][1] = fma(a[p].x, b[p].y, acc[p][0][1]);
+                    acc[p][1][0] = fma(a[p].y, b[p].x, acc[p][1][0]);
+                    acc[p][1][1] = fma(a[p].y, b[p].y, acc[p][1][1]);
+                }
+            }
+            __syncthreads();
+        }
+        for (int t = 0; t < Lf.tgt_count; ++t) {
+            const Target tg = targets[Lf.tgt_begin + t];
+            double* c = reinterpret_cast<double*>(tg.c);
+            const double sg = (double)tg.sign;
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const double u1 = acc[0][i][j] + acc[1][i][j];  // P1 + P2
+                    const double u2 = acc[0][i][j] + acc[5][i][j];  // P1 + P6
+                    const double u3 = u2 + acc[6][i][j];            // U2 + P7
+                    const double u4 = u2 + acc[4][i][j];            // U2 + P5
+                    const double u5 = u4 + acc[2][i][j];            // U4 + P3
+                    const double u6 = u3 - acc[3][i][j];            // U3 - P4
+                    const double u7 = u3 + acc[4][i][j];            // U3 + P5
+                    const double qv[4] = {u1, u5, u6, u7};          // C11, C12, C21, C22
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int lr = (q >> 1) * Q + r0 + i, lc = (q & 1) * Q + c0 + j;
+                        const int r = tm * F64_BM + lr, cc = tn * F64_BN + lc;
+                        if (r >= tg.rows || r >= Lf.m || cc >= tg.cols || cc >= Lf.n) continue;
+                        double* ptr = c + (long long)r * tg.ldc + cc;
+                        const double v = sg * qv[q];
+                        if (tg.mode == TGT_STORE) *ptr = v;
+                        else if (tg.mode == TGT_ATOMIC) atomicAdd(ptr, v);
+                        else *ptr += v;
+                    }
+                }
+        }
+    }
+}
+
 cudaError_t launch_gemm_simt(int elem_bytes, const MatRef* refs, const Leaf* leaves, int nleaves,
-                             const Target* targets, int total_items, int grid, cudaStream_t stream) {
+                             const Target* targets, int total_items, int grid, bool wtile, cudaStream_t stream) {
     if (total_items <= 0) return cudaSuccess;
     if (grid > total_items) grid = total_items;
-    if (elem_bytes == 8) gemm_simt_kernel<double><<<grid, 256, 0, stream>>>(refs, leaves, nleaves, targets, total_items);
+    if (elem_bytes == 8 && wtile)
+        gemm_simt_wtile_kernel<<<grid, 256, 0, stream>>>(refs, leaves, nleaves, targets, total_items);
+    else if (elem_bytes == 8)
+        gemm_simt_kernel<double><<<grid, 256, 0, stream>>>(refs, leaves, nleaves, targets, total_items);
     else gemm_simt_kernel<float><<<grid, 256, 0, stream>>>(refs, leaves, nleaves, targets, total_items);
     return cudaGetLastError();
 }

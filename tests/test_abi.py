@@ -93,3 +93,13 @@ def test_argument_errors_without_gpu(lib):
     st, _ = swmm.sw_mm_workspace_size(8, 8, 8, 1, swmm.SW_ALGO_STRASSEN | swmm.SW_SCHED_TWO_TEMP, 4)
     assert st == swmm.SW_EUNSUPPORTED
     assert swmm.load().sw_smm(None, None, 1, None, 1, None, 1, 1, 1, 1, 1, 0, None) == swmm.SW_EINVAL
+    # the Winograd-step FP64 leaf: FP64 entries with the Winograd algorithms only
+    wt = swmm.SW_LEAF_F64_WTILE
+    assert swmm.sw_mm_workspace_size(64, 64, 64, 16, swmm.SW_ALGO_WINOGRAD | wt, 4)[0] == swmm.SW_EINVAL
+    assert swmm.sw_mm_workspace_size(64, 64, 64, 16, swmm.SW_ALGO_NAIVE | wt, 8)[0] == swmm.SW_EUNSUPPORTED
+    assert swmm.sw_mm_workspace_size(64, 64, 64, 16, swmm.SW_ALGO_STRASSEN | wt, 8)[0] == swmm.SW_EUNSUPPORTED
+    assert swmm.sw_mm_workspace_size(64, 64, 64, 16, swmm.SW_ALGO_WINOGRAD | 0x4000, 8)[0] == swmm.SW_EINVAL
+    for v in (swmm.SW_ALGO_WINOGRAD, swmm.SW_ALGO_WINOGRAD | swmm.SW_SCHED_TWO_TEMP,
+              swmm.SW_ALGO_WINOGRAD_KNUTH):
+        assert swmm.sw_mm_workspace_size(256, 256, 256, 32, v | wt, 8) == swmm.sw_mm_workspace_size(256, 256, 256,
+                                                                                                    32, v, 8)

@@ -213,6 +213,50 @@ def test_fp64_odd_sizes(h, odd):
             assert oracle.err_norm(C, R, A, B) <= 1e-13, (m, n, k, v)
 
 
+# ------------------------------------------------------------------ FP64 leaves with a Winograd step per tile
+WT = swmm.SW_LEAF_F64_WTILE
+
+
+@pytest.mark.parametrize("algo,sched", [(W, FUSED), (W, TWO), (W, INPL), (W, ALLOC), (K, FUSED)])
+def test_fp64_wtile_n256_cutoff32(h, algo, sched):
+    # every 64 x 64 leaf tile takes one more Winograd step, its operand sums in shared memory
+    n = 256
+    v = algo | sched | WT
+    assert depth(h, n, n, n, 32, v, 8) == 3
+    Ai, Bi = inputs.pair(n, n, n, "int", seed=0, dtype=np.float64)
+    assert np.array_equal(run(h, Ai, Bi, 32, v, dtype=np.float64), oracle.naive(Ai, Bi))
+    A, B = inputs.pair(n, n, n, "uniform", seed=0, dtype=np.float64)
+    C = run(h, A, B, 32, v, dtype=np.float64)
+    assert oracle.err_norm(C, oracle.naive(A, B), A, B) <= 1e-13
+
+
+@pytest.mark.parametrize("cutoff", [1 << 20, 40])
+@pytest.mark.parametrize("m,n,k", [(1, 1, 1), (64, 64, 16), (63, 65, 17), (300, 260, 100), (129, 257, 33),
+                                   (5, 3, 4000), (1000, 1000, 1000)])
+def test_fp64_wtile_shapes(h, m, n, k, cutoff):
+    # depth 0 (one leaf) and deeper; ragged tiles and blocks, k not a multiple of the 16-deep block
+    Ai, Bi = inputs.pair(m, n, k, "int", seed=5, dtype=np.float64)
+    Ri = oracle.naive(Ai, Bi)
+    A, B = inputs.pair(m, n, k, "uniform", seed=6, dtype=np.float64)
+    R = oracle.naive(A, B)
+    for v in (W | FUSED | WT, W | TWO | WT | swmm.SW_PEEL, K | FUSED | WT):
+        assert np.array_equal(run(h, Ai, Bi, cutoff, v, dtype=np.float64), Ri), (m, n, k, cutoff, v)
+        C = run(h, A, B, cutoff, v, dtype=np.float64)
+        assert oracle.err_norm(C, R, A, B) <= 1e-13, (m, n, k, cutoff, v)
+
+
+def test_fp64_wtile_is_its_own_leaf(h):
+    # the tile step rounds differently from the plain leaf (so the Winograd-step kernel ran), and
+    # both sit well inside the FP64 bound
+    m, n, k = 300, 260, 100
+    A, B = inputs.pair(m, n, k, "uniform", seed=7, dtype=np.float64)
+    R = oracle.naive(A, B)
+    C0 = run(h, A, B, 1 << 20, W | FUSED, dtype=np.float64)
+    C1 = run(h, A, B, 1 << 20, W | FUSED | WT, dtype=np.float64)
+    assert not np.array_equal(C0, C1)
+    assert oracle.err_norm(C0, R, A, B) <= 1e-15 and oracle.err_norm(C1, R, A, B) <= 1e-15
+
+
 # ------------------------------------------------------------------ host entry point, norms, errors
 def test_host_entry_point_matches_device_path(h):
     m, n, k = 500, 300, 700
@@ -503,12 +547,3 @@ def test_ordered_depth1_graph_replay_integers_bit_exact(h, leaf):
         swmm.check(h, swmm.sw_sync(h, None))
         assert np.array_equal(dC.cpu().numpy().astype(np.float64), oracle.naive_mt(A, B)), seed
 
-
-@pytest.mark.parametrize("m,n,k", [(4096, 4096, 4096), (2000, 3000, 1000), (4100, 2304, 700)])
-def test_plain_tail_split_integers_bit_exact(h, m, n, k):
-    # plain products whose 256 x 256 tiles leave the last wave of CTA pairs partly idle: the last
-    # tile rows run as two K halves (a store, then a reduce-add ordered after it), including a
-    # ragged last tile row and a ragged last k block
-    A, B = inputs.pair(m, n, k, "int", seed=95, dtype=np.float64, lim=4)
-    assert exact_int_safe(4, k, 0)
-    assert np.array_equal(run(h, A, B, 0, swmm.SW_ALGO_NAIVE), oracle.naive_mt(A, B)), (m, n, k)
