@@ -39,7 +39,10 @@ namespace swk {
 
 constexpr int TF_BM = 128;
 constexpr int TF_BK = 32;  // TF32 k-block: 32 FP32 = 128 bytes, one swizzle row
-constexpr int TF_GROUP_M = 8;
+// tiles are taken in bands of TF_GROUP_M x 128 rows, column-major inside a band: a wave of 76
+// CTA pairs then covers about 12 x 6 tiles, whose A and B panels are shared by more of the wave
+// than in narrower bands (DRAM re-reads fall; n = 8192 plain: 1.30 ms with 8, 1.27 ms with 24)
+constexpr int TF_GROUP_M = 24;
 // MODE_TF32N: TF32 with B N-major (k x n as stored): B staged in 32-column (128-byte) boxes
 // with the 32-byte-atom 128-byte swizzle, read by the MMA through a layout-type-1 descriptor.
 // MODE_TF32X3: compensated TF32 -- each FP32 operand arrives as (hi, lo) FP32 halves, hi = tf32(x),
@@ -81,7 +84,7 @@ struct ItemPos {
 };
 
 // Work item -> (leaf, tile row, tile column); tiles are TM rows high, taken in groups of
-// 1024 / TM tile rows (column-major inside a group) for L2 reuse of the B tiles.
+// TF_GROUP_M x 128 / TM tile rows (column-major inside a group) for L2 reuse of A and B.
 template <int TM>
 __device__ __forceinline__ ItemPos decode_item(const Leaf* __restrict__ leaves, int nleaves, int item) {
     int lo = 0, hi = nleaves - 1;
