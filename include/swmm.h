@@ -138,9 +138,14 @@ sw_status sw_smm(sw_handle h, const float *A, int lda, const float *B, int ldb, 
 sw_status sw_dmm(sw_handle h, const double *A, int lda, const double *B, int ldb, double *C, int ldc,
                  int m, int n, int k, int cutoff, uint32_t variant, void *stream);
 
-/* FP32 product with HOST operands: copies A and B to the device, runs sw_smm and copies C back,
- * all on `stream`; returns after the stream has finished (synchronous).  Pinned host memory
- * gives the fastest copies.  Device buffers come from the handle's workspace. */
+/* FP32 product with HOST operands: copies A and B to the device, runs sw_smm and copies C back;
+ * returns after the work has finished (synchronous).  Pinned host memory gives the fastest
+ * copies.  Device buffers come from the handle's workspace.  Large products (n, k >= 1024, at
+ * least two row panels, 64 MB of operands) of the FUSED schedule or the naive algorithm with
+ * cutoff > 0 move A and C in row panels on two library streams ordered after `stream`: B goes
+ * first, then panel i of A; C's panel i = A_i B runs on `stream` at the whole product's depth and
+ * comes back while later panels still arrive (the panels' Winograd block partitions differ from
+ * one whole-matrix call, so the rounding can differ from sw_smm's within the same bound). */
 sw_status sw_smm_host(sw_handle h, const float *A_host, int lda, const float *B_host, int ldb,
                       float *C_host, int ldc, int m, int n, int k, int cutoff, uint32_t variant,
                       void *stream);

@@ -1301,6 +1301,9 @@ struct sw_handle_s {
     std::vector<ProfRec> prof_live;
     std::vector<cudaEvent_t> prof_free;
     cudaStream_t capture_stream = nullptr;  // private stream for CUDA-graph capture
+    // host-operand path: copy-in / copy-out streams and the events that order the panels
+    cudaStream_t io_in = nullptr, io_out = nullptr;
+    std::vector<cudaEvent_t> io_ev;
     // autotuner (cutoff <= 0): decisions per problem signature, and the last one made
     struct Tune { int cutoff = 0, bn = 0, pair = 0, candidates = 0; double ms = 0.0; };
     std::unordered_map<std::string, Tune> tuned;
@@ -2414,6 +2417,9 @@ sw_status sw_destroy(sw_handle h) {
     for (auto& r : h->prof_live) { cudaEventDestroy(r.e0); cudaEventDestroy(r.e1); }
     for (auto e : h->prof_free) cudaEventDestroy(e);
     if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
+    if (h->io_in) cudaStreamDestroy(h->io_in);
+    if (h->io_out) cudaStreamDestroy(h->io_out);
+    for (auto e : h->io_ev) cudaEventDestroy(e);
     delete h;
     return SW_OK;
 }
@@ -2531,6 +2537,67 @@ sw_status sw_last_tuning(sw_handle h, int* cutoff, int* tile_n, int* cta_pair, d
     return SW_OK;
 }
 
+// Host-operand product in row panels of height mp (the last one lower): B goes over first, then
+// panel i of A on the copy-in stream; panel i of C = A_i B runs on the caller's stream at the
+// whole product's depth L (the panel's cutoff is its own smallest block side at depth L, which
+// gives exactly L levels while that side is >= 2); panel i of C comes back on the copy-out stream
+// while later panels still arrive and compute.  Row panels keep every copy one contiguous run.
+static sw_status host_panels(sw_handle h, const float* A, int lda, const float* B, int ldb, float* C, int ldc, int m,
+                             int n, int k, int cutoff, uint32_t variant, int L, int mp, float* dA, long long lda2,
+                             float* dB, long long ldb2, float* dC, long long ldc2, cudaStream_t s) {
+    const int npan = (int)ceil_div(m, mp);
+    {
+        std::lock_guard<std::mutex> lock(h->mu);
+        cudaSetDevice(h->device);
+        if (!h->io_in && cudaStreamCreateWithFlags(&h->io_in, cudaStreamNonBlocking) != cudaSuccess)
+            return cuda_fail(h, cudaGetLastError(), "copy stream");
+        if (!h->io_out && cudaStreamCreateWithFlags(&h->io_out, cudaStreamNonBlocking) != cudaSuccess)
+            return cuda_fail(h, cudaGetLastError(), "copy stream");
+        while ((int)h->io_ev.size() < 2 * npan + 2) {
+            cudaEvent_t ev;
+            if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess)
+                return cuda_fail(h, cudaGetLastError(), "copy event");
+            h->io_ev.push_back(ev);
+        }
+    }
+    cudaEvent_t* ev = h->io_ev.data();  // [0] start, [1 + i] A_i arrived, [1 + npan + i] C_i done, [last] out done
+    cudaError_t e = cudaEventRecord(ev[0], s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->io_in, ev[0], 0);
+    if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(dB, ldb2 * 4, B, (size_t)ldb * 4, (size_t)n * 4, k, cudaMemcpyHostToDevice, h->io_in);
+    for (int i = 0; i < npan && e == cudaSuccess; ++i) {
+        const int r0 = i * mp, hgt = std::min(mp, m - r0);
+        e = cudaMemcpy2DAsync(dA + r0 * lda2, lda2 * 4, A + (size_t)r0 * lda, (size_t)lda * 4, (size_t)k * 4, hgt,
+                              cudaMemcpyHostToDevice, h->io_in);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[1 + i], h->io_in);
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "host to device copy");
+    for (int i = 0; i < npan; ++i) {
+        const int r0 = i * mp, hgt = std::min(mp, m - r0);
+        e = cudaStreamWaitEvent(s, ev[1 + i], 0);
+        if (e != cudaSuccess) return cuda_fail(h, e, "panel order");
+        int cut = cutoff;
+        if ((variant & SW_ALGO_MASK) != SW_ALGO_NAIVE) {
+            const long long d = 1LL << L;
+            cut = (int)std::min(std::min(ceil_div(hgt, d), ceil_div(n, d)), ceil_div(k, d));
+            if (cut < 2 || resolve_depth(hgt, n, k, cut, variant, 4) != L) cut = cutoff;  // low last panel
+        }
+        sw_status st = sw_smm(h, dA + r0 * lda2, (int)lda2, dB, (int)ldb2, dC + r0 * ldc2, (int)ldc2, hgt, n, k, cut,
+                              variant, s);
+        if (st != SW_OK) return st;
+        e = cudaEventRecord(ev[1 + npan + i], s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->io_out, ev[1 + npan + i], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpy2DAsync(C + (size_t)r0 * ldc, (size_t)ldc * 4, dC + r0 * ldc2, ldc2 * 4, (size_t)n * 4, hgt,
+                                  cudaMemcpyDeviceToHost, h->io_out);
+        if (e != cudaSuccess) return cuda_fail(h, e, "device to host copy");
+    }
+    e = cudaEventRecord(ev[1 + 2 * npan], h->io_out);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[1 + 2 * npan], 0);
+    if (e != cudaSuccess) return cuda_fail(h, e, "panel order");
+    return sw_sync(h, s);
+}
+
 sw_status sw_smm_host(sw_handle h, const float* A, int lda, const float* B, int ldb, float* C, int ldc, int m, int n,
                       int k, int cutoff, uint32_t variant, void* stream) {
     if (!h) return SW_EINVAL;
@@ -2558,6 +2625,17 @@ sw_status sw_smm_host(sw_handle h, const float* A, int lda, const float* B, int 
     float* dB = reinterpret_cast<float*>(h->io + ba);
     float* dC = reinterpret_cast<float*>(h->io + ba + bb);
     cudaError_t e = cudaSuccess;
+    // large FUSED / naive products with a given cutoff: A and C move in row panels so the copies
+    // overlap the panel products and each other (the link is duplex)
+    const uint32_t algo = variant & SW_ALGO_MASK, sched = variant & SW_SCHED_MASK;
+    const int L = resolve_depth(m, n, k, cutoff, variant, 4);
+    const long long unit = 256LL << L;  // panel height granularity: whole 256-row tiles per block
+    const int P = 4;
+    const long long mp = round_up(ceil_div(m, P), unit);
+    if ((cutoff > 0 || algo == SW_ALGO_NAIVE) && (algo == SW_ALGO_NAIVE || sched == SW_SCHED_FUSED) &&
+        n >= 1024 && k >= 1024 && m >= 2 * mp && (long long)m * n + (long long)k * n + (long long)m * k >= (16LL << 20))
+        return host_panels(h, A, lda, B, ldb, C, ldc, m, n, k, cutoff, variant, L, (int)mp, dA, lda2, dB, ldb2, dC,
+                           ldc2, s);
     if (m && k) e = cudaMemcpy2DAsync(dA, lda2 * 4, A, (size_t)lda * 4, (size_t)k * 4, m, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && k && n)
         e = cudaMemcpy2DAsync(dB, ldb2 * 4, B, (size_t)ldb * 4, (size_t)n * 4, k, cudaMemcpyHostToDevice, s);

@@ -271,6 +271,30 @@ def test_host_entry_point_matches_device_path(h):
     assert np.max(np.abs(C - Cd)) <= 1e-3
 
 
+@pytest.mark.parametrize("algo", [W, K, swmm.SW_ALGO_NAIVE])
+def test_host_entry_point_row_panels(h, algo):
+    # a large host-operand product moves A and C in row panels (copies overlap the panel
+    # products); each panel runs at the whole product's depth, the last panel lower
+    m, n, k, cutoff = 4500, 2000, 1500, 400
+    v = algo | FUSED
+    L = depth(h, m, n, k, cutoff, v, 4)
+    assert L == (0 if algo == swmm.SW_ALGO_NAIVE else 2)
+    assert exact_int_safe(2, k, L)
+    for kind in ("int", "uniform"):
+        A, B = inputs.pair(m, n, k, kind, seed=62, dtype=np.float32, **({"lim": 2} if kind == "int" else {}))
+        hA, hB = torch.from_numpy(A).pin_memory(), torch.from_numpy(B).pin_memory()
+        hC = torch.full((m, n), float("nan")).pin_memory()
+        st = swmm.sw_smm_host(h, ctypes.c_void_p(hA.data_ptr()), k, ctypes.c_void_p(hB.data_ptr()), n,
+                              ctypes.c_void_p(hC.data_ptr()), n, m, n, k, cutoff, v, None)
+        swmm.check(h, st)
+        C = hC.numpy().astype(np.float64)
+        R = oracle.naive_mt(A.astype(np.float64), B.astype(np.float64))
+        if kind == "int":
+            assert np.array_equal(C, R)
+        else:
+            check_close(C, R, A, B, tol_tf32(k, L))
+
+
 def test_error_norms_match_numpy(h):
     m, n, k = 300, 200, 100
     A, B = inputs.pair(m, n, k, "uniform", seed=61, dtype=np.float32)
