@@ -108,7 +108,11 @@ typedef enum {
 typedef struct sw_handle_s *sw_handle;
 
 /* Create a handle on the current CUDA device.  `workspace_budget_bytes` caps the device
- * memory the library may hold for temporaries (0 = no cap).  Memory is taken lazily. */
+ * memory the library may hold for temporaries (0 = no cap).  Memory is taken lazily.
+ * A handle's workspace, cached plans and host-operand buffers serve all its products: issue the
+ * products of one handle from one host thread at a time and on one stream (or order the streams
+ * yourself); use one handle per stream for independent concurrent work.  The serving calls
+ * (sw_server_*) are the exception and may be used from any thread. */
 sw_status sw_create(sw_handle *h, size_t workspace_budget_bytes);
 
 /* Release the handle and all memory it holds.  Synchronises the device first. */
