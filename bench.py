@@ -638,6 +638,8 @@ def main():
         idx4 = torch.from_numpy(sel4).cuda()
         fp64 = []
         for lab, v, c in (("plain (SIMT leaf)", swmm.SW_ALGO_NAIVE, 0),
+                          ("tile step only (depth 0)", swmm.SW_ALGO_WINOGRAD | swmm.SW_SCHED_FUSED |
+                           swmm.SW_LEAF_F64_WTILE, 1 << 30),
                           ("winograd L3", swmm.SW_ALGO_WINOGRAD | swmm.SW_SCHED_FUSED, n4 >> 3),
                           ("winograd L3 + tile step", swmm.SW_ALGO_WINOGRAD | swmm.SW_SCHED_FUSED |
                            swmm.SW_LEAF_F64_WTILE, n4 >> 3),
@@ -659,6 +661,14 @@ def main():
             fp64.append({"variant": lab, "depth": swmm.sw_mm_depth(n4, n4, n4, c, v, 8)[1] if v is not None else 0,
                          "ms": ms4, "eff_tflops": 2.0 * n4 ** 3 / (ms4 / 1e3) / 1e12, "err": err4})
         del A4, B4, C4
+        # FP64 ALU roofline of the two leaf kernels (depth 0: one launch per product); the peak is
+        # the FP64 units' nominal rate, about 2 FP64 FMAs per clock per SM x 152 SMs x 2.07 GHz
+        fp64_peak = 1.25
+        fp64_roof = {"bound": "alu", "peak": fp64_peak, "unit": "TFLOP/s", "peak_source": "nominal FP64 rate",
+                     "plain_leaf": {"achieved": fp64[0]["eff_tflops"], "frac": fp64[0]["eff_tflops"] / fp64_peak},
+                     "tile_step_leaf": {"achieved": fp64[1]["eff_tflops"] * 7 / 8,
+                                        "frac": fp64[1]["eff_tflops"] * 7 / 8 / fp64_peak,
+                                        "note": "executed FMAs: 7/8 of 2n^3 (tile sums not counted)"}}
         # peak workspace of each schedule for the n = 16384 split-BF16 configuration (depth 2)
         ws = {}
         for lab, sc in (("alloc", swmm.SW_SCHED_ALLOC), ("two_temp", swmm.SW_SCHED_TWO_TEMP),
@@ -678,6 +688,7 @@ def main():
                  "fp32_accuracy_n16384_normal_bf16x3": cfg3,
                  "workspace_bytes_n16384_L2_bf16x3": ws,
                  "fp64_n4096": fp64,
+                 "fp64_roofline": fp64_roof,
                  "err_metric": "max|C - C_oracle| / (n max|A| max|B|) on the sampled oracle rows"}
 
     if rank == 0:
