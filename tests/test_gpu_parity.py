@@ -571,3 +571,35 @@ def test_ordered_depth1_graph_replay_integers_bit_exact(h, leaf):
         swmm.check(h, swmm.sw_sync(h, None))
         assert np.array_equal(dC.cpu().numpy().astype(np.float64), oracle.naive_mt(A, B)), seed
 
+
+
+@pytest.mark.parametrize("algo,cutoff", [(W, 23200), (swmm.SW_ALGO_NAIVE, 0)])
+def test_max_size_past_2_31_elements_sampled_entries(h, algo, cutoff):
+    # 46400 x 46400 operands hold 2.15e9 elements each, past 2^31: the operand-sum pass, the
+    # tensor maps and the epilogue index them in 64 bits.  Integer inputs in [-2, 2] keep every
+    # partial sum exact; sampled rows x sampled columns (first, last, block edges, random) of C
+    # are compared bit-exactly with the oracle on the matching slices of A and B.
+    n = 46400
+    if torch.cuda.mem_get_info()[0] < 64e9:
+        pytest.skip("needs 64 GB of free device memory")
+    v = algo | FUSED
+    L = depth(h, n, n, n, cutoff, v, 4)
+    assert L == (1 if algo == W else 0) and exact_int_safe(2, n, L)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(96)
+    dA = torch.randint(-2, 3, (n, n), generator=g, device="cuda", dtype=torch.float32)
+    dB = torch.randint(-2, 3, (n, n), generator=g, device="cuda", dtype=torch.float32)
+    dC = torch.full((n, n), float("nan"), device="cuda")
+    st = swmm.sw_smm(h, ctypes.c_void_p(dA.data_ptr()), n, ctypes.c_void_p(dB.data_ptr()), n,
+                     ctypes.c_void_p(dC.data_ptr()), n, n, n, n, cutoff, v, None)
+    swmm.check(h, st)
+    swmm.check(h, swmm.sw_sync(h, None))
+    rng = np.random.Generator(np.random.PCG64(97))
+    idx = np.unique(np.concatenate([[0, 1, n // 2 - 1, n // 2, n - 2, n - 1], rng.choice(n, 10, replace=False)]))
+    ti = torch.from_numpy(idx).cuda()
+    Ar = dA[ti].double().cpu().numpy()
+    Bc = dB[:, ti].double().cpu().numpy()
+    Cs = dC[ti][:, ti].double().cpu().numpy()
+    del dA, dB, dC
+    torch.cuda.empty_cache()
+    assert np.array_equal(Cs, oracle.naive(Ar, Bc))
