@@ -643,6 +643,10 @@ def main():
                           ("winograd L3", swmm.SW_ALGO_WINOGRAD | swmm.SW_SCHED_FUSED, n4 >> 3),
                           ("winograd L3 + tile step", swmm.SW_ALGO_WINOGRAD | swmm.SW_SCHED_FUSED |
                            swmm.SW_LEAF_F64_WTILE, n4 >> 3),
+                          ("winograd L5 (2 Table 2 levels over a fused L3)", swmm.SW_ALGO_WINOGRAD |
+                           swmm.SW_SCHED_FUSED, n4 >> 5),
+                          ("winograd L5 + tile step", swmm.SW_ALGO_WINOGRAD | swmm.SW_SCHED_FUSED |
+                           swmm.SW_LEAF_F64_WTILE, n4 >> 5),
                           ("cublas dgemm (torch, context)", None, 0)):
             def run4():
                 if v is None:

@@ -193,6 +193,7 @@ struct Planner {
     bool bf;                // FP32 with split-BF16 leaves
     bool x3 = false;        // FP32 with compensated-TF32 leaves (FP32 hi / lo halves)
     bool wtile = false;     // FP64 leaves: one Winograd step inside every 64 x 64 tile
+    int fused_below = 0;    // deep FUSED (FP64): sub-products at this depth or less are fused
     bool bt;                // B side stored transposed (TF32 leaves read through B^T)
     bool nmaj = false;      // TF32 leaves read B N-major, as stored (bt is then false)
     uint32_t variant;
@@ -604,7 +605,15 @@ struct Planner {
     // ---------------------------------------------------------- materialised schedules
     bool product(View a, View b, View c, int L) {
         if (L == 0) return gemm(a, b, c, TGT_STORE);
-        if (sched == SW_SCHED_TWO_TEMP) return two_temp(a, b, c, L);
+        if (fused_below > 0 && L <= fused_below) {
+            // the fused bottom of a deep FUSED product; its sum slots are free again once its
+            // launches are queued (everything after it runs later on the same stream)
+            const size_t mark = ws_top;
+            const bool ok = fused(a, b, c, L);
+            ws_top = mark;
+            return ok;
+        }
+        if (sched == SW_SCHED_TWO_TEMP || (fused_below > 0 && algo == SW_ALGO_WINOGRAD)) return two_temp(a, b, c, L);
         if (sched == SW_SCHED_IN_PLACE) return in_place(a, b, c, L);
         return algo == SW_ALGO_STRASSEN ? alloc_strassen(a, b, c, L) : alloc_winograd(a, b, c, L);
     }
@@ -1361,15 +1370,32 @@ static int resolve_depth(int m, int n, int k, int cutoff, uint32_t variant, int 
     if ((variant & SW_ALGO_MASK) == SW_ALGO_NAIVE) return 0;
     // static default where the autotuner does not run (stream capture, IN_PLACE, sw_mm_depth):
     // from the bench's sweeps, one TF32 Winograd level pays from n = 16384 on; FP64 leaves are
-    // ALU-bound and gain from depth early
-    if (cutoff <= 0) cutoff = eb == 4 ? 8192 : 64;
+    // ALU-bound and gain from every level while the leaves keep >= 128 rows (the grouped FP64
+    // launch then still fills the GPU with 64 x 64 tiles)
+    if (cutoff <= 0) cutoff = eb == 4 ? 8192 : 128;
     int L = 0;
     while (L < 20) {
         const long long s = 1LL << L;
         const long long lo = std::min(std::min(ceil_div(m, s), ceil_div(n, s)), ceil_div(k, s));
         if (lo > cutoff) ++L; else break;
     }
-    if ((variant & SW_SCHED_MASK) == SW_SCHED_FUSED && L > 3) L = 3;
+    if ((variant & SW_SCHED_MASK) == SW_SCHED_FUSED) {
+        // three levels fuse into one operand-sum pass and one grouped launch; FP64 Strassen /
+        // BDPZ products go deeper by Alg. 2 / Table 2 steps above the fused bottom, one per
+        // exact halving of m, n and k (at most three) while the fused bottom keeps a smallest side
+        // of >= 1024 (smaller bottoms give their grouped launch too few tiles and spend more on
+        // the bottom's FP64 reduce-adds than the level saves)
+        int cap = 3;
+        const uint32_t algo = variant & SW_ALGO_MASK;
+        if (eb == 8 && (algo == SW_ALGO_STRASSEN || algo == SW_ALGO_WINOGRAD)) {
+            const int dmin = std::min(m, std::min(n, k));
+            int t = 0;
+            while (t < 3 && m % (2 << t) == 0 && n % (2 << t) == 0 && k % (2 << t) == 0 && (dmin >> (t + 1)) >= 1024)
+                ++t;
+            cap += t;
+        }
+        if (L > cap) L = cap;
+    }
     return L;
 }
 
@@ -1451,7 +1477,11 @@ static sw_status build_plan(sw_handle h, int eb, const void* A, int lda, const v
         if (!c_ok) c2 = P.talloc(m, n);
         View b2 = stage_b(Bv, k, n);
         if (L == 0 || algo == SW_ALGO_NAIVE) ok = P.gemm(a2, b2, c2, TGT_STORE);
-        else ok = P.fused(a2, b2, c2, L);
+        else if (L <= 3) ok = P.fused(a2, b2, c2, L);
+        else {  // FP64 deeper than three levels: Table 2 (BDPZ) or Alg. 2 (Strassen) steps on top
+            P.fused_below = 3;
+            ok = P.product(a2, b2, c2, L);
+        }
         if (!c_ok) P.copy_pad(Cv, c2);
     } else if (L > 5) {
         return fail(h, SW_EUNSUPPORTED, "materialised schedules stop at depth 5 (7^5 leaf launches); raise the cutoff");
@@ -1819,10 +1849,18 @@ static sw_status do_mm(sw_handle h, int eb, const void* A, int lda, const void* 
         } else {
             // depths whose leaves stay large enough to keep the leaf kernels efficient
             const bool tc = eb == 4;
-            const int leaf_min = tc ? 1024 : 128, lmax = sched == SW_SCHED_FUSED ? (tc ? 2 : 3) : 2;
+            const int leaf_min = tc ? 1024 : 128, lmax = sched == SW_SCHED_FUSED ? (tc ? 2 : 6) : 2;
             const int dmin = std::min(m, std::min(n, k));
             std::vector<int> cuts;
-            for (int L = 0; L <= lmax && (dmin >> L) >= leaf_min; ++L) cuts.push_back((int)ceil_div(dmin, 1LL << L));
+            for (int L = 0, prev = -1; L <= lmax && (dmin >> L) >= leaf_min; ++L) {
+                const int c = (int)ceil_div(dmin, 1LL << L);
+                const int d = resolve_depth(m, n, k, c, variant, eb);
+                if (d != prev) cuts.push_back(c);
+                prev = d;
+            }
+            // FP64: every level saves FP64 multiply-adds at little cost, so only the three deepest
+            // depths are timed
+            if (!tc && cuts.size() > 3) cuts.erase(cuts.begin(), cuts.end() - 3);
             if (cuts.size() >= 2) {
                 std::vector<PlanBuilder> cands;
                 for (int c : cuts) cands.push_back(builder(c));

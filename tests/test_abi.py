@@ -53,6 +53,22 @@ def test_fused_depth_is_capped_at_three(lib):
     assert st == swmm.SW_OK and d == 3
 
 
+@pytest.mark.parametrize("m,n,k,want", [(8192, 8192, 8192, 6), (4096, 4096, 4096, 5), (4100, 4100, 4100, 5),
+                                        (4098, 4096, 4096, 4), (4097, 4096, 4096, 3), (2048, 2080, 2064, 4),
+                                        (1040, 1056, 1024, 3)])
+def test_fused_fp64_depth_grows_by_exact_halvings(lib, m, n, k, want):
+    # FP64 Strassen / BDPZ products go past three fused levels by one Table 2 / Alg. 2 level per
+    # exact halving of m, n and k while the fused bottom keeps a smallest side >= 1024; Knuth's
+    # form and FP32 stay at three
+    F = swmm.SW_SCHED_FUSED
+    for a in (swmm.SW_ALGO_WINOGRAD, swmm.SW_ALGO_STRASSEN):
+        assert swmm.sw_mm_depth(m, n, k, 8, a | F, 8) == (swmm.SW_OK, want)
+    assert swmm.sw_mm_depth(m, n, k, 8, swmm.SW_ALGO_WINOGRAD_KNUTH | F, 8) == (swmm.SW_OK, 3)
+    assert swmm.sw_mm_depth(m, n, k, 8, swmm.SW_ALGO_WINOGRAD | F, 4) == (swmm.SW_OK, 3)
+    # the FP64 static default (cutoff <= 0) keeps leaves of more than 128
+    assert swmm.sw_mm_depth(4096, 4096, 4096, 0, swmm.SW_ALGO_WINOGRAD | F, 8) == (swmm.SW_OK, 5)
+
+
 @pytest.mark.parametrize("L", [1, 2, 3])
 def test_workspace_matches_schedule_counts(lib, L):
     n = 16384

@@ -25,6 +25,7 @@ torch = pytest.importorskip("torch")
 
 W, S, K = swmm.SW_ALGO_WINOGRAD, swmm.SW_ALGO_STRASSEN, swmm.SW_ALGO_WINOGRAD_KNUTH
 FUSED, TWO, INPL, ALLOC = swmm.SW_SCHED_FUSED, swmm.SW_SCHED_TWO_TEMP, swmm.SW_SCHED_IN_PLACE, swmm.SW_SCHED_ALLOC
+WT = swmm.SW_LEAF_F64_WTILE
 
 
 @pytest.fixture(scope="module")
@@ -213,8 +214,22 @@ def test_fp64_odd_sizes(h, odd):
             assert oracle.err_norm(C, R, A, B) <= 1e-13, (m, n, k, v)
 
 
+@pytest.mark.parametrize("algo", [W, S])
+@pytest.mark.parametrize("m,n,k,cutoff,L", [(2048, 2048, 2048, 16, 4), (2048, 2080, 2064, 40, 4), (2050, 2048, 2052, 40, 4)])
+def test_fp64_fused_deeper_than_three(h, algo, m, n, k, cutoff, L):
+    # FP64 FUSED past three levels: Table 2 (BDPZ) / Alg. 2 (Strassen) steps above a fused
+    # three-level bottom; with and without the tile-step leaf
+    for leaf in ((0, WT) if algo == W else (0,)):
+        v = algo | FUSED | leaf
+        assert depth(h, m, n, k, cutoff, v, 8) == L
+        Ai, Bi = inputs.pair(m, n, k, "int", seed=8, dtype=np.float64)
+        assert np.array_equal(run(h, Ai, Bi, cutoff, v, dtype=np.float64), oracle.naive_mt(Ai, Bi)), v
+        A, B = inputs.pair(m, n, k, "uniform", seed=9, dtype=np.float64)
+        C = run(h, A, B, cutoff, v, dtype=np.float64)
+        assert oracle.err_norm(C, oracle.naive_mt(A, B), A, B) <= 1e-13, v
+
+
 # ------------------------------------------------------------------ FP64 leaves with a Winograd step per tile
-WT = swmm.SW_LEAF_F64_WTILE
 
 
 @pytest.mark.parametrize("algo,sched", [(W, FUSED), (W, TWO), (W, INPL), (W, ALLOC), (K, FUSED)])
