@@ -26,6 +26,10 @@
  *                                 them (FUSED schedule only)
  *   schedule    SW_SCHED_FUSED    all levels' operand sums in one pass; the 7^L leaf products in
  *                                 one grouped launch whose epilogue adds +-P into the C blocks
+ *                                 (at most 3 levels; FP64 Strassen / BDPZ products go deeper by
+ *                                 Alg. 2 / Table 2 steps above a fused 3-level bottom, one per
+ *                                 exact halving of m, n, k while the bottom's smallest side stays
+ *                                 >= 1024, at most 6 levels)
  *               SW_SCHED_TWO_TEMP Table 2 ("Two Temp Winograd", Sec. 3.3): two temporaries X, Y
  *                                 per level; products written into C quadrants (Winograd only)
  *               SW_SCHED_IN_PLACE Table 3 ("In-Place Winograd", Sec. 3.3): temporaries stored in
@@ -64,7 +68,7 @@
  * runs it once more, so C holds exactly its result; later calls reuse the decision (per handle).
  * That first call therefore runs the product several times and waits for the stream.  Under stream
  * capture, and for SW_SCHED_IN_PLACE (whose runs overwrite A and B), a static default applies
- * instead (FP32: cutoff 8192; FP64: 64), which is also what sw_mm_depth reports for cutoff <= 0.
+ * instead (FP32: cutoff 8192; FP64: 128), which is also what sw_mm_depth reports for cutoff <= 0.
  */
 #ifndef SWMM_H
 #define SWMM_H
