@@ -44,8 +44,9 @@ def parse():
     p.add_argument("--n", type=int, default=8192)
     p.add_argument("--algo", choices=["winograd", "knuth", "strassen", "naive"], default="winograd")
     p.add_argument("--sched", choices=["fused", "two_temp", "in_place", "alloc"], default="fused")
-    p.add_argument("--leaf", choices=["tf32", "bf16x3", "tf32x3"], default="tf32",
-                   help="leaf precision of the profile case (the headline line is TF32)")
+    p.add_argument("--leaf", choices=["tf32", "bf16x3", "tf32x3", "f64", "f64wt"], default="tf32",
+                   help="leaf precision of the profile case (the headline line is TF32; f64 / f64wt: an FP64 "
+                        "product on uniform operands with the plain or the tile-step leaf)")
     p.add_argument("--cutoff", type=int, default=None,
                    help="recursion cutoff (default n / 2: one level); 0 = the library's autotuner")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-oracle sample budget")
@@ -407,9 +408,18 @@ def main():
         return
 
     if args.profile_case:
-        leafbits = {"tf32": swmm.SW_LEAF_TF32, "bf16x3": swmm.SW_LEAF_BF16X3, "tf32x3": swmm.SW_LEAF_TF32X3}[args.leaf]
-        for _ in range(args.warmup + 1):
-            product(variant | leafbits, args.cutoff)
+        if args.leaf in ("f64", "f64wt"):
+            A8, B8 = dA.double(), dB.double()
+            C8 = torch.empty((n, n), dtype=torch.float64, device="cuda")
+            v8 = variant | (swmm.SW_LEAF_F64_WTILE if args.leaf == "f64wt" else 0)
+            for _ in range(args.warmup + 1):
+                swmm.check(h, swmm.sw_dmm(h, p(A8), n, p(B8), n, p(C8), n, n, n, n, args.cutoff, v8, sp))
+            L = swmm.sw_mm_depth(n, n, n, args.cutoff, v8, 8)[1]
+        else:
+            leafbits = {"tf32": swmm.SW_LEAF_TF32, "bf16x3": swmm.SW_LEAF_BF16X3,
+                        "tf32x3": swmm.SW_LEAF_TF32X3}[args.leaf]
+            for _ in range(args.warmup + 1):
+                product(variant | leafbits, args.cutoff)
         swmm.check(h, swmm.sw_sync(h, sp))
         if rank == 0:
             print(json.dumps({"profile_case": args.algo, "schedule": args.sched, "leaf": args.leaf, "n": n, "depth": L}),
