@@ -112,13 +112,13 @@ bool tf32_bt_form() {
     return bt;
 }
 
-// Tile-width override for tuning sweeps (SWMM_TF32_BN = 128 or 256); 0 = the planner's choice.
+// Tile-width override for tuning sweeps (SWMM_TF32_BN = 128, 256 or 512); 0 = the planner's choice.
 int bn_override() {
     static int v = -1;
     if (v < 0) {
         const char* e = getenv("SWMM_TF32_BN");
         v = e ? atoi(e) : 0;
-        if (v != 128 && v != 256) v = 0;
+        if (v != 128 && v != 256 && v != 512) v = 0;
     }
     return v;
 }
@@ -217,7 +217,16 @@ struct Planner {
     // SWMM_NO_PAIR=1 disables it (diagnostics).
     bool pair_ok(int bn) const {
         static const bool off = getenv("SWMM_NO_PAIR") != nullptr;
-        return !off && bn == 256 && !batch && !server && !x3 && eb == 4;
+        return !off && (bn == 256 || (bn == 512 && nmaj && !bf)) && !batch && !server && !x3 && eb == 4;
+    }
+    // Tile width of a TF32 launch over C blocks `cols` wide: 512 (CTA pairs, one accumulator, a
+    // quarter fewer operand bytes per MMA) where the blocks are at least 512 wide and 512-wide tiles
+    // pad no more than 256-wide ones; else 256, or 128 for narrow blocks.
+    int tf32_bn(int cols) const {
+        if (bn_override()) return bn_override() == 512 && !pair_ok(512) ? 256 : bn_override();
+        if (cols <= 128) return 128;
+        if (pair_ok(512) && cols >= 512 && round_up(cols, 512) == round_up(cols, 256)) return 512;
+        return 256;
     }
     // rows of one B-side TMA box: half the tile width for a CTA pair
     int b_box(int bn) const { return pair_ok(bn) ? bn / 2 : bn; }
@@ -501,7 +510,7 @@ struct Planner {
         lf.tile_begin = 0;
         Op o;
         o.kind = OP_GEMM_TF32;
-        o.bn = force_bn ? force_bn : bn_override() ? bn_override() : (c.cols <= 128 ? 128 : 256);
+        o.bn = force_bn ? force_bn : tf32_bn(c.cols);
         lf.kblocks = (int)ceil_div(a.cols, tf32_tile_k());
         lf.tiles_n = (int)ceil_div(c.cols, o.bn);
         o.nmaj = nmaj;
@@ -820,8 +829,9 @@ struct Planner {
     //   [P1 -> C11 := ; +P6 -> C12 := U2 ; +P7 -> C21 := C22 := U3]  (stores, the first writers)
     //   [P5 -> C22 += ; +P3 -> C12 += P5 + P3]   [P2 -> C11 +=]   [P4 -> C21 += sign P4]
     // (4 stores and 4 reduce-adds instead of 4 and 10).  The work layout is explicit: every CTA
-    // pair gets its own item sequence (pairs of positions, so the two accumulators alternate;
-    // stores before adds on every pair; greedy balance), interleaved as item t * units + u.
+    // pair gets its own item sequence (pairs of positions, so the two accumulators alternate, or
+    // single positions with the one accumulator of 512-wide tiles; stores before adds on every
+    // pair; greedy balance), interleaved as item t * units + u.
     // *done = 1 when the op was emitted; 0 to fall back to the plain FUSED order.
     // `o` is the depth-1 grouped-GEMM op with its kind, tile width and operand maps set (TF32 on
     // CTA pairs, or split-BF16 on single CTAs).
@@ -832,7 +842,8 @@ struct Planner {
         if (off || dry) return true;
         const bool pairs = o.pair;
         const int units = !pairs ? sms  // one CTA per SM, all resident
-                                 : o.kind == OP_GEMM_TF32 ? gemm_tf32n_pair_units(sms) : gemm_bf16x3_pair_units(sms);
+                                 : o.kind == OP_GEMM_TF32 ? gemm_tf32n_pair_units(sms, bn) : gemm_bf16x3_pair_units(sms);
+        const int nacc = bn > 256 ? 1 : 2;  // TMEM accumulators: a chain's next step comes nacc items later
         const int tile_m = pairs ? 2 * tf32_tile_m() : tf32_tile_m();
         if (units <= 0) return true;
         struct Emit { int q, mode; float sign; };
@@ -912,13 +923,14 @@ struct Planner {
                 }
                 continue;
             }
-            for (int p = 0; p < npos; p += 2) {
+            for (int p = 0; p < npos; p += nacc) {
                 const int u = least();
                 for (int st = 0; st < ch.len; ++st) {
                     seq[u].push_back({ch.prod[st], pos[p]});
-                    seq[u].push_back(p + 1 < npos ? std::make_pair(ch.prod[st], pos[p + 1]) : std::make_pair(7, 0));
+                    if (nacc == 2)
+                        seq[u].push_back(p + 1 < npos ? std::make_pair(ch.prod[st], pos[p + 1]) : std::make_pair(7, 0));
                 }
-                load[u] += ch.len * (p + 1 < npos ? 2 : 1);
+                load[u] += ch.len * (nacc == 2 && p + 1 < npos ? 2 : 1);
             }
         }
         size_t tmax = 0;
@@ -1043,9 +1055,11 @@ struct Planner {
         // C and reduce-adds only.
         const bool ordered = eb == 4 && L == 1 && !batch && !server;
         if (!ordered) memset0(C);
-        const int bn_o = eb == 8 ? F64_BN
-                                 : force_bn ? force_bn
-                                            : (bn_override() ? bn_override() : (x3 || nb <= 128 ? 128 : 256));
+        const int bn_o = eb == 8                ? F64_BN
+                         : force_bn             ? force_bn
+                         : x3 || (bf && nb <= 128) ? 128
+                         : bf                   ? 256
+                                                : tf32_bn(nb);
         std::vector<int> first_writer(1 << (2 * L), -1), flag_base(1 << (2 * L), -1), flag_cols(1 << (2 * L), 0);
         int nflags = 0;
         // leaves and their Kronecker-product targets

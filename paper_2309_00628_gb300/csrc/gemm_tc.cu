@@ -65,7 +65,13 @@ struct TfCfg {
     static constexpr int NOPS = (MODE == MODE_TF32 || MODE == MODE_TF32N) ? 1 : 2;  // tiles per operand (hi, lo)
     static constexpr int STAGE_BYTES = NOPS * (A_BYTES + B_BYTES);
     static constexpr int STAGES = (4 * 49152) / STAGE_BYTES;         // 192 KB of operand stages
-    static constexpr int TMEM_COLS = 2 * BN;
+    // BN = 512 (TF32 N-major on CTA pairs): a 256 x 512 tile as two N = 256 MMAs per k step into
+    // one 512-column accumulator -- 48 operand bytes per clock and SM at the full MMA rate instead
+    // of 64, at the price of a single accumulator (the epilogue no longer overlaps the next tile)
+    static_assert(BN <= 256 || (BN == 512 && PAIR && MODE == MODE_TF32N), "512-wide tiles: TF32N on CTA pairs");
+    static constexpr int MMA_N = BN > 256 ? 256 : BN;                 // N of one MMA
+    static constexpr int NACC = BN > 256 ? 1 : 2;                     // TMEM accumulators (512 columns)
+    static constexpr int TMEM_COLS = NACC * BN;
     static constexpr int STG_OFF = STAGES * STAGE_BYTES;      // epilogue staging: 4 warps x 2 x 4 KB
     static constexpr int STG_BYTES = 4 * 2 * 4096;
     static constexpr int BAR_OFF = STG_OFF + STG_BYTES;
@@ -74,8 +80,8 @@ struct TfCfg {
     // B MN-major; N = BN, M = 128
     static constexpr uint32_t IDESC =
         TF ? ((1u << 4) | (2u << 7) | (2u << 10) | (BN_MAJOR32 ? (1u << 16) : 0u) |
-              ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24))
-            : ((1u << 4) | (1u << 7) | (1u << 10) | (1u << 16) | ((uint32_t)(BN >> 3) << 17) |
+              ((uint32_t)(MMA_N >> 3) << 17) | ((uint32_t)(TM >> 4) << 24))
+            : ((1u << 4) | (1u << 7) | (1u << 10) | (1u << 16) | ((uint32_t)(MMA_N >> 3) << 17) |
                ((uint32_t)(TM >> 4) << 24));
 };
 
@@ -307,7 +313,10 @@ __global__ void __launch_bounds__(192, 1)
                 const int a_col = __ldg(&L->a_col);
                 // TF32: B^T, rows are N, columns K.  BF16X3 / TF32N: B as stored, rows K, columns N.
                 const int b_row = __ldg(&L->b_row) + (MODE == MODE_TF32 ? ip.tn * BN + (int)rank * Cfg::B_ROWS : 0);
-                const int b_col = __ldg(&L->b_col) + (MODE == MODE_TF32 ? 0 : ip.tn * BN + (int)rank * Cfg::B_ROWS);
+                // a pair's CTA holds half of every MMA's N columns: 128 of each 256 (BN = 512: B chunk
+                // c of rank r is tile column (c / 4) * 256 + r * 128 + (c % 4) * 32)
+                const int b_col = __ldg(&L->b_col) +
+                                  (MODE == MODE_TF32 ? 0 : ip.tn * BN + (int)rank * (Cfg::B_ROWS < 128 ? Cfg::B_ROWS : 128));
                 const int kb_n = __ldg(&L->kblocks);
                 // TMA x coordinates must be 16-byte aligned (4 FP32 / 8 BF16 elements)
                 if (((a_col | b_col) & (Cfg::TF ? 3 : 7)) != 0) {
@@ -349,7 +358,7 @@ __global__ void __launch_bounds__(192, 1)
 #pragma unroll
                             for (int c = 0; c < Cfg::B_ROWS / 32; ++c)  // 32 N-columns x 32 K-rows per box
                                 tma_load_2d_pair(stage_b(stage, 0) + c * 4096, pick_map(maps, gmaps, bm), fb,
-                                                 b_col + c * 32, b_row + kb * Cfg::BK);
+                                                 b_col + (c >> 2) * 256 + (c & 3) * 32, b_row + kb * Cfg::BK);
                         } else {
                             tma_load_2d_pair(stage_b(stage, 0), pick_map(maps, gmaps, bm), fb, b_col + kb * Cfg::BK,
                                              b_row);
@@ -415,8 +424,8 @@ __global__ void __launch_bounds__(192, 1)
                                        : decode_any<Cfg::TM>(leaves, nleaves, ctl, item);
                 const int kb_n = __ldg(&leaves[ip.leaf].kblocks);
                 const uint32_t cont = __ldg(&leaves[ip.leaf].cont) != 0 ? 1u : 0u;  // keep the chain's sum
-                const int acc = local & 1;
-                const uint32_t acc_phase = (local >> 1) & 1;
+                const int acc = local % Cfg::NACC;
+                const uint32_t acc_phase = (local / Cfg::NACC) & 1;
                 if (!mbar_wait(&tempty[acc], acc_phase ^ 1u, err, ERR_WAIT_ACC_FREE)) { ok = false; break; }
                 tc_fence_after();
                 const uint32_t d_tmem = tmem_base + (uint32_t)(acc * BN);
@@ -448,8 +457,16 @@ __global__ void __launch_bounds__(192, 1)
                                                     ? make_sdesc(b_addr + kk * 1024, 4096, 512, SWZ_128B_BASE32B)
                                                     : make_sdesc(b_addr + kk * 32, 16, 1024, SWZ_128B);
                             const uint32_t accum = ((kb | kk) != 0 ? 1u : 0u) | cont;
-                            if (PAIR) mma_tf32_pair(d_tmem, ad, bd, Cfg::IDESC, accum);
-                            else mma_tf32(d_tmem, ad, bd, Cfg::IDESC, accum);
+                            if (PAIR) {
+                                mma_tf32_pair(d_tmem, ad, bd, Cfg::IDESC, accum);
+                                if (BN > 256) {  // second N half: B chunks 4..7 (16 KB on), TMEM columns 256..511
+                                    const uint64_t bd2 =
+                                        make_sdesc(b_addr + kk * 1024 + 16384, 4096, 512, SWZ_128B_BASE32B);
+                                    mma_tf32_pair(d_tmem + Cfg::MMA_N, ad, bd2, Cfg::IDESC, accum);
+                                }
+                            } else {
+                                mma_tf32(d_tmem, ad, bd, Cfg::IDESC, accum);
+                            }
                         }
                     } else {
                         const uint32_t ah = smem_u32(stage_a(stage, 0)), al = smem_u32(stage_a(stage, 1));
@@ -517,8 +534,8 @@ __global__ void __launch_bounds__(192, 1)
             const ItemPos ip = RES ? decode_in_leaf<Cfg::TM>(leaves, __ldcg(&ctl.item_leaf[item]), item)
                                    : decode_any<Cfg::TM>(leaves, nleaves, ctl, item);
             const Leaf* L = &leaves[ip.leaf];
-            const int acc = local & 1;
-            const uint32_t acc_phase = (local >> 1) & 1;
+            const int acc = local % Cfg::NACC;
+            const uint32_t acc_phase = (local / Cfg::NACC) & 1;
             if (!mbar_wait(&tfull[acc], acc_phase, err, ERR_WAIT_ACC)) break;
             tc_fence_after();
             const int tb = __ldg(&L->tgt_begin), tc = __ldg(&L->tgt_count);
@@ -808,10 +825,15 @@ cudaError_t launch_gemm_tf32n(int bn, const MapSet& maps, const CUtensorMap* gma
                               const Target* targets, const CUtensorMap* tmaps, unsigned* flags,
                               int total_items, int* err, int grid, cudaStream_t stream, bool pair,
                               const int* item_leaf, const int* item_tile, int units) {
+    if (pair && bn == 512)
+        return launch_tc_impl<MODE_TF32N, 512, false, true>(maps, gmaps, leaves, nleaves, targets, tmaps, flags,
+                                                            total_items, err, grid, stream, nullptr, item_leaf,
+                                                            item_tile, units);
     if (pair)
         return launch_tc_impl<MODE_TF32N, 256, false, true>(maps, gmaps, leaves, nleaves, targets, tmaps, flags,
                                                             total_items, err, grid, stream, nullptr, item_leaf,
                                                             item_tile, units);
+    if (bn == 512) return cudaErrorInvalidValue;  // 512-wide tiles exist on CTA pairs only
     if (bn == 256)
         return launch_tc_impl<MODE_TF32N, 256>(maps, gmaps, leaves, nleaves, targets, tmaps, flags,
                                                total_items, err, grid, stream, nullptr, item_leaf, item_tile, units);
@@ -819,9 +841,11 @@ cudaError_t launch_gemm_tf32n(int bn, const MapSet& maps, const CUtensorMap* gma
                                            err, grid, stream, nullptr, item_leaf, item_tile, units);
 }
 
-int gemm_tf32n_pair_units(int sms) {
+int gemm_tf32n_pair_units(int sms, int bn) {
     int max_pairs = 0;
-    if (tc_setup<MODE_TF32N, 256, false, true>(&max_pairs) != cudaSuccess || max_pairs <= 0) return 0;
+    const cudaError_t e = bn == 512 ? tc_setup<MODE_TF32N, 512, false, true>(&max_pairs)
+                                    : tc_setup<MODE_TF32N, 256, false, true>(&max_pairs);
+    if (e != cudaSuccess || max_pairs <= 0) return 0;
     return std::min(sms / 2, max_pairs);
 }
 

@@ -35,7 +35,8 @@ cudaError_t launch_gemm_tf32(int bn, const MapSet& maps, const CUtensorMap* gmap
                              int total_items, int* err, int grid, cudaStream_t stream, bool pair = false,
                              const int* item_leaf = nullptr);
 // TF32 leaves with B N-major (k x n as stored; maps from make_map_f32_n, Leaf::b_row = K,
-// Leaf::b_col = N); otherwise as launch_gemm_tf32.
+// Leaf::b_col = N); otherwise as launch_gemm_tf32.  bn = 512 (CTA pairs only): 256 x 512 tiles with
+// one TMEM accumulator.
 // item_tile / units: an explicit work layout (tile row << 16 | column per item, with item_leaf its
 // leaf) planned for exactly `units` persistent units; the launch uses that many (accumulation
 // chains rely on unit u taking items u, u + units, ...).
@@ -43,8 +44,9 @@ cudaError_t launch_gemm_tf32n(int bn, const MapSet& maps, const CUtensorMap* gma
                               const Target* targets, const CUtensorMap* tmaps, unsigned* flags,
                               int total_items, int* err, int grid, cudaStream_t stream, bool pair = false,
                               const int* item_leaf = nullptr, const int* item_tile = nullptr, int units = 0);
-// Persistent units (CTA pairs) of a pair-form N-major TF32 launch on `sms` SMs (0: unavailable).
-int gemm_tf32n_pair_units(int sms);
+// Persistent units (CTA pairs) of a pair-form N-major TF32 launch with tile width bn (256 or
+// 512) on `sms` SMs (0: unavailable).
+int gemm_tf32n_pair_units(int sms, int bn = 256);
 // Resident (serving) form of the TF32 grouped GEMM, BN = 256: runs until ctl.stop, an error, or
 // ctl.idle_ns without newly published items.  nmajor: B maps N-major (as launch_gemm_tf32n), else B^T.
 cudaError_t launch_gemm_tf32_resident(const CUtensorMap* gmaps, const Leaf* leaves, const Target* targets,

@@ -57,8 +57,10 @@ struct Leaf {
     int tiles_n;
     int c_row0, c_col0;  // position of the leaf's tile (0, 0) inside its target blocks
     int tag;             // resident server: completion counter of the leaf's request (-1: none)
-    int cont;            // 1: the tile continues the accumulator of this CTA's tile two items back
-                         //    (an accumulation chain; needs an explicit item table, see ResidentCtl)
+    int cont;            // 1: the tile continues the accumulator of this CTA's last tile that used
+                         //    the same TMEM accumulator (two items back with two accumulators, the
+                         //    previous item with one); an accumulation chain, which needs an
+                         //    explicit item table (see ResidentCtl)
     int pad_[2];
 };
 
