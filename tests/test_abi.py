@@ -119,3 +119,18 @@ def test_argument_errors_without_gpu(lib):
               swmm.SW_ALGO_WINOGRAD_KNUTH):
         assert swmm.sw_mm_workspace_size(256, 256, 256, 32, v | wt, 8) == swmm.sw_mm_workspace_size(256, 256, 256,
                                                                                                     32, v, 8)
+
+
+@pytest.mark.parametrize("n,cutoff,top", [(4096, 256, 1), (4096, 128, 2), (8192, 128, 3)])
+def test_deep_fp64_fused_workspace_is_table2_plus_one_bottom(lib, n, cutoff, top):
+    # a deep FP64 FUSED product holds the Table 2 temporaries X, Y of its top levels (each
+    # (n / 2^l)^2 FP64 at level l) plus the sum slots of one fused three-level bottom at a time
+    v = swmm.SW_ALGO_WINOGRAD | swmm.SW_SCHED_FUSED
+    assert swmm.sw_mm_depth(n, n, n, cutoff, v, 8) == (swmm.SW_OK, 3 + top)
+    st, total = swmm.sw_mm_workspace_size(n, n, n, cutoff, v, 8)
+    assert st == swmm.SW_OK
+    s = n >> top
+    st, bottom = swmm.sw_mm_workspace_size(s, s, s, s // 8, v, 8)
+    assert st == swmm.SW_OK
+    xy = sum(2 * (n >> l) ** 2 * 8 for l in range(1, top + 1))
+    assert total == xy + bottom, (total, xy, bottom)
