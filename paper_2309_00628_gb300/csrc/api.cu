@@ -2613,6 +2613,13 @@ static sw_status host_panels(sw_handle h, const float* A, int lda, const float* 
         }
     }
     cudaEvent_t* ev = h->io_ev.data();  // [0] start, [1 + i] A_i arrived, [1 + npan + i] C_i done, [last] out done
+    // the call is synchronous: on any failure the copies already queued finish before it returns,
+    // so the caller may release its host buffers
+    auto drained = [&](sw_status st) {
+        cudaStreamSynchronize(h->io_in);
+        cudaStreamSynchronize(h->io_out);
+        return st;
+    };
     cudaError_t e = cudaEventRecord(ev[0], s);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(h->io_in, ev[0], 0);
     if (e == cudaSuccess)
@@ -2623,11 +2630,11 @@ static sw_status host_panels(sw_handle h, const float* A, int lda, const float* 
                               cudaMemcpyHostToDevice, h->io_in);
         if (e == cudaSuccess) e = cudaEventRecord(ev[1 + i], h->io_in);
     }
-    if (e != cudaSuccess) return cuda_fail(h, e, "host to device copy");
+    if (e != cudaSuccess) return drained(cuda_fail(h, e, "host to device copy"));
     for (int i = 0; i < npan; ++i) {
         const int r0 = i * mp, hgt = std::min(mp, m - r0);
         e = cudaStreamWaitEvent(s, ev[1 + i], 0);
-        if (e != cudaSuccess) return cuda_fail(h, e, "panel order");
+        if (e != cudaSuccess) return drained(cuda_fail(h, e, "panel order"));
         int cut = cutoff;
         if ((variant & SW_ALGO_MASK) != SW_ALGO_NAIVE) {
             const long long d = 1LL << L;
@@ -2636,17 +2643,17 @@ static sw_status host_panels(sw_handle h, const float* A, int lda, const float* 
         }
         sw_status st = sw_smm(h, dA + r0 * lda2, (int)lda2, dB, (int)ldb2, dC + r0 * ldc2, (int)ldc2, hgt, n, k, cut,
                               variant, s);
-        if (st != SW_OK) return st;
+        if (st != SW_OK) return drained(st);
         e = cudaEventRecord(ev[1 + npan + i], s);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(h->io_out, ev[1 + npan + i], 0);
         if (e == cudaSuccess)
             e = cudaMemcpy2DAsync(C + (size_t)r0 * ldc, (size_t)ldc * 4, dC + r0 * ldc2, ldc2 * 4, (size_t)n * 4, hgt,
                                   cudaMemcpyDeviceToHost, h->io_out);
-        if (e != cudaSuccess) return cuda_fail(h, e, "device to host copy");
+        if (e != cudaSuccess) return drained(cuda_fail(h, e, "device to host copy"));
     }
     e = cudaEventRecord(ev[1 + 2 * npan], h->io_out);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[1 + 2 * npan], 0);
-    if (e != cudaSuccess) return cuda_fail(h, e, "panel order");
+    if (e != cudaSuccess) return drained(cuda_fail(h, e, "panel order"));
     return sw_sync(h, s);
 }
 
@@ -2691,11 +2698,21 @@ sw_status sw_smm_host(sw_handle h, const float* A, int lda, const float* B, int 
     if (m && k) e = cudaMemcpy2DAsync(dA, lda2 * 4, A, (size_t)lda * 4, (size_t)k * 4, m, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && k && n)
         e = cudaMemcpy2DAsync(dB, ldb2 * 4, B, (size_t)ldb * 4, (size_t)n * 4, k, cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return cuda_fail(h, e, "host to device copy");
+    // synchronous call: a failure returns only after the copies already queued have finished
+    if (e != cudaSuccess) {
+        cudaStreamSynchronize(s);
+        return cuda_fail(h, e, "host to device copy");
+    }
     sw_status st = sw_smm(h, dA, (int)lda2, dB, (int)ldb2, dC, (int)ldc2, m, n, k, cutoff, variant, stream);
-    if (st != SW_OK) return st;
+    if (st != SW_OK) {
+        cudaStreamSynchronize(s);
+        return st;
+    }
     if (m && n) e = cudaMemcpy2DAsync(C, (size_t)ldc * 4, dC, ldc2 * 4, (size_t)n * 4, m, cudaMemcpyDeviceToHost, s);
-    if (e != cudaSuccess) return cuda_fail(h, e, "device to host copy");
+    if (e != cudaSuccess) {
+        cudaStreamSynchronize(s);
+        return cuda_fail(h, e, "device to host copy");
+    }
     return sw_sync(h, stream);
 }
 
