@@ -1,0 +1,56 @@
+"""Host-side helpers of bench.py (no GPU): the leaf-flop count behind the roofline, the lookup of
+a profile's DRAM traffic (only for the kernel source it was captured on), the reduction of the
+clock record taken during the timed region, and the config both bench arms share."""
+import hashlib
+import os
+import sys
+import types
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+@pytest.mark.parametrize("n", [256, 4096, 8192])
+@pytest.mark.parametrize("L", [0, 1, 2, 3])
+def test_leaf_flops_is_seven_eighths_per_level(n, L):
+    # 7^L leaves of (n / 2^L)^3 multiply-adds: 2 n^3 (7/8)^L
+    assert bench.leaf_flops(n, L) == pytest.approx(2.0 * n ** 3 * (7 / 8) ** L, rel=1e-15)
+
+
+def test_traffic_is_read_only_for_the_profiled_kernel_source(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    csrc = tmp_path / "paper_2309_00628_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (tmp_path / "profiles").mkdir()
+    (csrc / "k.cu").write_bytes(b"kernel v1")
+    sha = hashlib.sha1(b"kernel v1").hexdigest()[:12]
+    (tmp_path / "profiles" / "w.md").write_text(f"kernel_source_sha1: {sha}\ndram_bytes_per_launch: 2.5e9\n")
+    assert bench.traffic_from_profiles("k.cu", "w") == 2.5e9
+    (csrc / "k.cu").write_bytes(b"kernel v2")  # the kernel changed since the capture: no traffic
+    assert bench.traffic_from_profiles("k.cu", "w") is None
+    assert bench.traffic_from_profiles("k.cu", "missing") is None
+
+
+def test_clock_record_reduction(tmp_path):
+    # nvidia-smi rows: index, sm clock, max sm clock, power, reasons mask, hw_slowdown,
+    # hw_thermal_slowdown, sw_thermal_slowdown, sw_power_cap
+    p = tmp_path / "clocks.csv"
+    p.write_text("0, 2070, 2070, 900.5, 0x4, Not Active, Not Active, Not Active, Active\n"
+                 "0, 1900, 2070, 1300.0, 0x4, Not Active, Not Active, Not Active, Active\n"
+                 "0, 2000, 2070, 1200.0, 0x0, Not Active, Not Active, Not Active, Not Active\n"
+                 "not a record\n")
+    s = bench.ClockSampler(0)
+    s.path = str(p)
+    s.proc = types.SimpleNamespace(terminate=lambda: None, wait=lambda timeout=None: None, kill=lambda: None)
+    assert s.stop() == {"sm_mhz": 2000.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    assert not p.exists()
+
+
+def test_both_arms_share_the_workload_config():
+    args = types.SimpleNamespace(n=8192, algo="winograd", sched="fused")
+    c = bench.workload_config(args, 1)
+    assert c["n"] == 8192 and c["depth"] == 1 and c["algo"] == "winograd" and c["schedule"] == "fused"
+    assert "n=8192" in c["workload"] and "L=1" in c["workload"]
