@@ -158,6 +158,13 @@ sw_status sw_smm_host(sw_handle h, const float *A_host, int lda, const float *B_
                       float *C_host, int ldc, int m, int n, int k, int cutoff, uint32_t variant,
                       void *stream);
 
+/* Self-test of the bounded device waits (failure detection without a GPU fault): launches one
+ * small leaf-GEMM whose only contribution is a reduce-add ordered after a first write that no leaf
+ * makes, so its epilogue's wait on the ordering counter expires after the bound (about 2 s); the
+ * kernel records the expiry, finishes and releases its resources.  Returns what sw_sync reports,
+ * SW_ETIMEOUT when the bound works.  The handle and the CUDA context stay usable.  Synchronous. */
+sw_status sw_selftest_expired_wait(sw_handle h, void *stream);
+
 /* Wait for `stream` and report device-side failures of this handle's kernels: SW_ETIMEOUT if a
  * bounded wait inside a kernel expired, SW_ECUDA if the stream reported a CUDA error.
  * Clears the device error word. */

@@ -2736,6 +2736,66 @@ sw_status sw_sync(sw_handle h, void* stream) {
     return SW_OK;
 }
 
+sw_status sw_selftest_expired_wait(sw_handle h, void* stream) {
+    if (!h) return SW_EINVAL;
+    cudaSetDevice(h->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int n = 256;  // one 256-wide tile column, two 128-row tiles
+    const size_t mat = (size_t)n * n * sizeof(float);
+    // device block: A | B | C | tensor map of C | leaf | target | epoch, finished-CTA count, 2 counters
+    const size_t o_map = 3 * mat, o_leaf = o_map + sizeof(CUtensorMap), o_tgt = o_leaf + sizeof(Leaf),
+                 o_flags = round_up((long long)(o_tgt + sizeof(Target)), 64), total = o_flags + 4 * sizeof(unsigned);
+    char* d = nullptr;
+    if (cudaMalloc(&d, total) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(h, SW_ENOMEM, "self-test buffers");
+    }
+    MapSet maps;
+    memset(&maps, 0, sizeof(maps));
+    CUtensorMap cmap;
+    float* A = reinterpret_cast<float*>(d);
+    float* B = reinterpret_cast<float*>(d + mat);
+    float* C = reinterpret_cast<float*>(d + 2 * mat);
+    if (!make_map_f32(&maps.m[0], A, n, n, n, 32, tf32_tile_m()) || !make_map_f32_n(&maps.m[1], B, n, n, n) ||
+        !make_map_f32(&cmap, C, n, n, n, 32, 32)) {
+        cudaFree(d);
+        return fail(h, SW_ECUDA, "self-test tensor maps");
+    }
+    Leaf lf;
+    memset(&lf, 0, sizeof(lf));
+    lf.tag = -1;
+    lf.a_map = 0;
+    lf.b_map = 1;
+    lf.m = n;
+    lf.n = n;
+    lf.kblocks = n / tf32_tile_k();
+    lf.tiles_n = 1;
+    lf.tgt_count = 1;
+    Target t;
+    memset(&t, 0, sizeof(t));
+    t.c = C;
+    t.ldc = n;
+    t.rows = t.cols = n;
+    t.sign = 1.f;
+    t.mode = TGT_ATOMIC;  // ordered after a first write that no leaf of the launch makes
+    t.vec_ok = 1;
+    t.map = 0;
+    t.flag_base = 0;
+    t.flag_cols = 1;
+    cudaError_t e = cudaMemsetAsync(d, 0, total, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d + o_map, &cmap, sizeof(cmap), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d + o_leaf, &lf, sizeof(lf), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d + o_tgt, &t, sizeof(t), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = launch_gemm_tf32n(256, maps, nullptr, reinterpret_cast<const Leaf*>(d + o_leaf), 1,
+                              reinterpret_cast<const Target*>(d + o_tgt), reinterpret_cast<const CUtensorMap*>(d + o_map),
+                              reinterpret_cast<unsigned*>(d + o_flags), 2, h->d_err, h->sms, s, false);
+    sw_status st = e == cudaSuccess ? sw_sync(h, stream) : cuda_fail(h, e, "self-test launch");
+    cudaStreamSynchronize(s);
+    cudaFree(d);
+    return st;
+}
+
 sw_status sw_profile(sw_handle h, int enable) {
     if (!h) return SW_EINVAL;
     std::lock_guard<std::mutex> lock(h->mu);

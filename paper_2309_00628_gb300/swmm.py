@@ -159,6 +159,15 @@ PROFILE_KINDS = ["gemm_tf32", "gemm_simt", "addsub", "copy_pad", "preadd", "mems
                  "preadd_split"]
 
 
+def sw_selftest_expired_wait(h, stream=None) -> int:
+    """Bounded-wait self-test (see include/swmm.h): SW_ETIMEOUT when a device wait that nothing
+    satisfies ends at its bound."""
+    fn = load().sw_selftest_expired_wait
+    fn.argtypes = [_V, _V]
+    fn.restype = _I
+    return fn(h, stream)
+
+
 def sw_profile(h, enable: bool) -> int:
     return load().sw_profile(h, 1 if enable else 0)
 

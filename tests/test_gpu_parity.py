@@ -618,3 +618,13 @@ def test_max_size_past_2_31_elements_sampled_entries(h, algo, cutoff):
     del dA, dB, dC
     torch.cuda.empty_cache()
     assert np.array_equal(Cs, oracle.naive(Ar, Bc))
+
+
+def test_expired_device_wait_reports_timeout_and_the_handle_stays_usable(h):
+    # failure detection without a fault: a reduce-add whose ordering counter nothing advances
+    # waits until its bound, the kernel records the expiry and finishes, sw_sync reports it
+    assert swmm.sw_selftest_expired_wait(h, None) == swmm.SW_ETIMEOUT
+    assert "expired" in swmm.sw_last_error(h)
+    assert swmm.sw_sync(h, None) == swmm.SW_OK  # the error word was consumed
+    A, B = inputs.pair(300, 260, 520, "int", seed=98, dtype=np.float64, lim=4)
+    assert np.array_equal(run(h, A, B, 200, W | FUSED), oracle.naive(A, B))
