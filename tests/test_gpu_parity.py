@@ -628,3 +628,35 @@ def test_expired_device_wait_reports_timeout_and_the_handle_stays_usable(h):
     assert swmm.sw_sync(h, None) == swmm.SW_OK  # the error word was consumed
     A, B = inputs.pair(300, 260, 520, "int", seed=98, dtype=np.float64, lim=4)
     assert np.array_equal(run(h, A, B, 200, W | FUSED), oracle.naive(A, B))
+
+
+@pytest.mark.parametrize("ldc_pad", [12, 5])
+@pytest.mark.parametrize("variant,cutoff,dtype", [(W | FUSED, 300, np.float32), (W | FUSED, 120, np.float32),
+                                                  (swmm.SW_ALGO_NAIVE, 0, np.float32),
+                                                  (W | FUSED | swmm.SW_LEAF_BF16X3, 300, np.float32),
+                                                  (W | TWO, 200, np.float32), (W | FUSED, 60, np.float64)])
+def test_output_stays_inside_its_view(h, ldc_pad, variant, cutoff, dtype):
+    # canary bands: C is a view inside a larger buffer (rows above and below, columns on both
+    # sides; ldc_pad 12 keeps 16-byte rows, 5 does not); every element outside the view keeps
+    # its sentinel and the view holds the exact product (integer inputs)
+    m, n, k = 520, 600, 460
+    L = depth(h, m, n, k, cutoff, variant, 4 if dtype == np.float32 else 8)
+    assert dtype == np.float64 or exact_int_safe(2, k, L)
+    A, B = inputs.pair(m, n, k, "int", seed=99, dtype=np.float64, lim=2)
+    tdt = torch.float32 if dtype == np.float32 else torch.float64
+    dA = torch.from_numpy(A.astype(dtype)).cuda()
+    dB = torch.from_numpy(B.astype(dtype)).cuda()
+    ldc, top, left, bottom = n + ldc_pad, 3, 4, 5
+    sentinel = -12345.0
+    buf = torch.full((top + m + bottom, ldc), sentinel, dtype=tdt, device="cuda")
+    view = buf[top:top + m, left:left + n]
+    fn = swmm.sw_smm if dtype == np.float32 else swmm.sw_dmm
+    st = fn(h, ctypes.c_void_p(dA.data_ptr()), k, ctypes.c_void_p(dB.data_ptr()), n, ctypes.c_void_p(view.data_ptr()),
+            ldc, m, n, k, cutoff, variant, None)
+    swmm.check(h, st)
+    swmm.check(h, swmm.sw_sync(h, None))
+    out = buf.cpu().numpy().astype(np.float64)
+    inside = np.zeros(out.shape, bool)
+    inside[top:top + m, left:left + n] = True
+    assert np.all(out[~inside] == sentinel)
+    assert np.array_equal(out[top:top + m, left:left + n], oracle.naive(A, B))
