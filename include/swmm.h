@@ -129,7 +129,8 @@ const char *sw_last_error(sw_handle h);
  * without running it.  For SW_SCHED_ALLOC this is the peak of the per-level temporaries
  * (Alg. 3: 4 S + 4 T + 7 P blocks per level, all levels live); for SW_SCHED_TWO_TEMP the
  * X and Y temporaries of every level (Table 2); SW_SCHED_IN_PLACE needs none beyond a
- * padded copy for unaligned sizes; SW_SCHED_FUSED the materialised operand sums. */
+ * padded copy for unaligned sizes; SW_SCHED_FUSED the materialised operand sums (deep FP64
+ * products: those of one fused three-level bottom plus the Table 2 X, Y of the levels above). */
 sw_status sw_mm_workspace_size(int m, int n, int k, int cutoff, uint32_t variant, int elem_bytes,
                                size_t *bytes);
 
@@ -184,8 +185,7 @@ typedef struct {
 /* `count` independent FP32 products (different shapes allowed, any alignment), asynchronous on
  * `stream`.  The tensor-core work of all products runs as ONE persistent grouped launch; the
  * per-product staging (packing operands whose rows are not 16-byte aligned) runs as one batched
- * launch, and
- * depth >= 1 products add their operand-sum passes.  The whole batch is captured once into a CUDA
+ * launch, and depth >= 1 products add their operand-sum passes.  The whole batch is captured once into a CUDA
  * graph and replayed on later calls with the same problem list (same pointers and shapes).
  * Variant: SW_SCHED_FUSED with SW_LEAF_TF32 (other schedules / leaves: SW_EUNSUPPORTED); each
  * product's depth follows `cutoff` as for sw_smm (<= 0: the autotuner picks one cutoff and the tile
