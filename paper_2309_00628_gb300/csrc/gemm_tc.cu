@@ -14,6 +14,8 @@
 //  * BF16X3: each FP32 operand arrives split into bf16 halves hi = bf16(x), lo = bf16(x - hi);
 //    per k-step the kernel issues kind::f16 MMAs hi*hi + hi*lo + lo*hi into one FP32
 //    accumulator.  A K-major, B N-major (as stored, k x n).
+//  * TF32X3: compensated TF32, FP32 halves hi = tf32(x), lo = x - hi; three kind::tf32 MMAs per
+//    k-step (B N-major).
 // Products accumulate in FP32 in tensor memory.
 //
 // CTA = 6 warps, persistent over work items (one item = one BM x BN output tile of one leaf):
@@ -24,7 +26,10 @@
 //               TMA store (first writer) or TMA reduce-add (further contributions) per target;
 //               targets without a tensor map take coalesced row stores / atomics from the same
 //               staging (one 128-byte row run per warp step).
-// Two TMEM accumulators (2 x BN columns) let the epilogue of tile i overlap the MMAs of i+1.
+// With BN <= 256 two TMEM accumulators (2 x BN columns) let the epilogue of tile i overlap the
+// MMAs of i+1.  CTA pairs (cta_group::2) take 256-row tiles; TF32N pairs also run 256 x 512 tiles
+// as two N = 256 MMAs per k-step into one 512-column accumulator (fewer operand bytes per MMA,
+// the epilogue no longer overlapped).
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cstdint>
