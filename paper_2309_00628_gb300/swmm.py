@@ -87,9 +87,10 @@ def load(build_if_missing: bool = False):
     lib.sw_server_submit.argtypes = [_V, _P(sw_request), _P(ctypes.c_uint64)]
     lib.sw_server_wait.argtypes = [_V, ctypes.c_uint64, ctypes.c_int64]
     lib.sw_server_stop.argtypes = [_V]
+    lib.sw_selftest_expired_wait.argtypes = [_V, _V]
     for name in ("sw_create", "sw_destroy", "sw_mm_workspace_size", "sw_mm_depth", "sw_smm", "sw_dmm",
                  "sw_smm_host", "sw_sync", "sw_error_norms", "sw_profile", "sw_profile_read", "sw_server_start",
-                 "sw_server_submit", "sw_server_wait", "sw_server_stop"):
+                 "sw_server_submit", "sw_server_wait", "sw_server_stop", "sw_selftest_expired_wait"):
         getattr(lib, name).restype = _I
     _lib = lib
     return lib
@@ -162,10 +163,7 @@ PROFILE_KINDS = ["gemm_tf32", "gemm_simt", "addsub", "copy_pad", "preadd", "mems
 def sw_selftest_expired_wait(h, stream=None) -> int:
     """Bounded-wait self-test (see include/swmm.h): SW_ETIMEOUT when a device wait that nothing
     satisfies ends at its bound."""
-    fn = load().sw_selftest_expired_wait
-    fn.argtypes = [_V, _V]
-    fn.restype = _I
-    return fn(h, stream)
+    return load().sw_selftest_expired_wait(h, stream)
 
 
 def sw_profile(h, enable: bool) -> int:
