@@ -64,7 +64,7 @@ def _load():
     lib.orc_workspace_elems.restype = ctypes.c_double
     ip = ctypes.POINTER(ctypes.c_int)
     lib.orc_schedule_table.argtypes = [ctypes.c_int, ip]
-    lib.orc_recursive_table.argtypes = [ip, L, dp, dp, dp, L, dp]
+    lib.orc_recursive_table.argtypes = [ip, ctypes.c_int, L, L, L, dp, dp, dp, L, dp]
     lib.orc_recursive_table.restype = ctypes.c_int
     lib.orc_err_norm.argtypes = [L, L, L, dp, L, dp, L, dp, L, dp, L]
     lib.orc_err_norm.restype = ctypes.c_double
@@ -160,17 +160,19 @@ def schedule_table(which: int) -> np.ndarray:
     return out.reshape(22, 5)
 
 
-def run_table(tab, A, B, cutoff: int, trace: bool = False):
-    """Run a (possibly perturbed) 22-step table with in-place rules; square inputs.
+def run_table(tab, A, B, cutoff: int, trace: bool = False, two_temp: bool = False):
+    """Run a (possibly perturbed) 22-step table: with Table 3's rules (in place, square inputs,
+    the default) or, with two_temp=True, Table 2's (temporaries X and Y, any shape).
 
     Raises RuntimeError when the liveness shadow finds a read of a dead value."""
     tab = np.ascontiguousarray(np.asarray(tab, np.int32).reshape(-1))
     A, B = _f64(A).copy(), _f64(B).copy()
-    n = A.shape[0]
-    C = np.zeros((n, n), np.float64)
+    m, k = A.shape
+    n = B.shape[1]
+    C = np.zeros((m, n), np.float64)
     tv = np.full(32, np.nan)
-    rc = _load().orc_recursive_table(tab.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), n, _p(A), _p(B),
-                                     _p(C), cutoff, _p(tv) if trace else None)
+    rc = _load().orc_recursive_table(tab.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), 1 if two_temp else 0,
+                                     m, n, k, _p(A), _p(B), _p(C), cutoff, _p(tv) if trace else None)
     if rc == 1:
         raise ValueError("bad table")
     if rc == 2:

@@ -378,7 +378,7 @@ static const step in_place_table[22] = {
 };
 
 static const step *g_tables[3] = {two_temp_table, in_place_table, NULL};
-static step g_custom_table[22]; /* slot 2: a caller-supplied table (tests plant mistakes here) */
+static step g_custom_table[22]; /* a caller-supplied table (tests plant mistakes here) */
 
 /* Shape of a value: 'a' (m2 x k2), 'b' (k2 x n2) or 'c' (m2 x n2). */
 static char shape_of(int v) {
@@ -435,7 +435,7 @@ static void schedule_level(mat a, mat b, mat c, ctx *x, int top, int which) {
     }
     long m2 = a.rows / 2, k2 = a.cols / 2, n2 = b.cols / 2;
     double *xp = NULL, *yp = NULL;
-    if (which == 0) {
+    if (which == 0 || which == 3) { /* Table 2, or a caller's table under its rules */
         /* X holds A-quadrant sums (m2 x k2) and P1 (m2 x n2): sized for the larger. */
         long xs = m2 * (k2 > n2 ? k2 : n2);
         xp = (double *)calloc((size_t)(xs > 0 ? xs : 1), sizeof(double));
@@ -443,13 +443,14 @@ static void schedule_level(mat a, mat b, mat c, ctx *x, int top, int which) {
     }
     slot[sX] = view(xp, 0, 0, 0); slot[sY] = view(yp, 0, 0, 0);
     holds[sX] = vDEAD; holds[sY] = vDEAD;
-    run_table(g_tables[which], slot, holds, x, top, m2, k2, n2);
+    run_table(which == 3 ? g_custom_table : g_tables[which], slot, holds, x, top, m2, k2, n2);
     free(xp); free(yp);
 }
 
 static void two_temp_level(mat a, mat b, mat c, ctx *x, int top) { schedule_level(a, b, c, x, top, 0); }
 static void in_place_level(mat a, mat b, mat c, ctx *x, int top) { schedule_level(a, b, c, x, top, 1); }
 static void custom_level(mat a, mat b, mat c, ctx *x, int top) { schedule_level(a, b, c, x, top, 2); }
+static void custom_tt_level(mat a, mat b, mat c, ctx *x, int top) { schedule_level(a, b, c, x, top, 3); }
 
 /* Copy table `which` (0 two-temp, 1 in-place) out as 22 x {op, val, dst, v1, v2}. */
 int orc_schedule_table(int which, int *out) {
@@ -462,8 +463,8 @@ int orc_schedule_table(int which, int *out) {
     return 0;
 }
 
-static const level_fn g_levels[6] = {strassen_level, winograd_level, knuth_level, two_temp_level,
-                                     in_place_level, custom_level};
+static const level_fn g_levels[7] = {strassen_level, winograd_level, knuth_level, two_temp_level,
+                                     in_place_level, custom_level, custom_tt_level};
 
 /* ------------------------------------------------------------------------- */
 /* Public recursive entry.  alg: 0 Strassen, 1 Winograd (BDPZ, allocating),   */
@@ -474,7 +475,7 @@ static const level_fn g_levels[6] = {strassen_level, winograd_level, knuth_level
 /* ------------------------------------------------------------------------- */
 int orc_recursive(int alg, long m, long n, long k, double *A, long lda, double *B, long ldb,
                   double *C, long ldc, long cutoff, int mode, double *trace) {
-    if (alg < 0 || alg > 5 || m < 0 || n < 0 || k < 0) return 1;
+    if (alg < 0 || alg > 6 || m < 0 || n < 0 || k < 0) return 1;
     if ((alg == ALG_IN_PLACE || alg == 5) && !(m == n && n == k)) return 1;
     if (cutoff < 1) cutoff = 1;
     ctx x;
@@ -510,10 +511,11 @@ int orc_recursive(int alg, long m, long n, long k, double *A, long lda, double *
 }
 
 /* Run a caller-supplied 22-step table (same encoding as orc_schedule_table) with
- * the in-place rules (square only; operands of sub-products are destroyed).  Lets
- * the tests plant a mistake in a copy of Table 2 or 3 and watch the shadow catch it. */
-int orc_recursive_table(const int *tab, long n, double *A, double *B, double *C, long cutoff,
-                        double *trace) {
+ * the rules of Table 3 (rules 0: in place, square only, operands of sub-products are
+ * destroyed) or of Table 2 (rules 1: the X and Y temporaries, any shape, operands kept).
+ * Lets the tests plant a mistake in a copy of Table 2 or 3 and watch the shadow catch it. */
+int orc_recursive_table(const int *tab, int rules, long m, long n, long k, double *A, double *B,
+                        double *C, long cutoff, double *trace) {
     for (int i = 0; i < 22; ++i) {
         g_custom_table[i].op = tab[5 * i + 0]; g_custom_table[i].val = tab[5 * i + 1];
         g_custom_table[i].dst = tab[5 * i + 2]; g_custom_table[i].v1 = tab[5 * i + 3];
@@ -521,6 +523,8 @@ int orc_recursive_table(const int *tab, long n, double *A, double *B, double *C,
         if (g_custom_table[i].dst < 0 || g_custom_table[i].dst >= NSLOT) return 1;
     }
     g_tables[2] = g_custom_table;
+    if (rules == 1) return orc_recursive(6, m, n, k, A, k, B, n, C, n, cutoff, ORC_PAD, trace);
+    if (!(m == n && n == k)) return 1;
     return orc_recursive(5, n, n, n, A, n, B, n, C, n, cutoff, ORC_PAD, trace);
 }
 

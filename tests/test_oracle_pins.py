@@ -210,11 +210,12 @@ def test_tables_traces_match_bdpz(which):
 def test_real_tables_pass_the_shadow():
     rng = np.random.default_rng(13)
     A, B = _ints(rng, (16, 16)), _ints(rng, (16, 16))
-    for which in (0, 1):
-        tab = oracle.schedule_table(which)
-        if which == 0:
-            continue  # Table 2 needs X/Y, exercised through recursive(TWO_TEMP)
-        assert np.array_equal(oracle.run_table(tab, A, B, 2), _exact_matmul_int(A, B))
+    assert np.array_equal(oracle.run_table(oracle.schedule_table(1), A, B, 2), _exact_matmul_int(A, B))
+    # Table 2 under its own rules (X and Y temporaries), square and rectangular
+    for m, n, k in ((16, 16, 16), (16, 8, 32), (8, 32, 16)):
+        A, B = _ints(rng, (m, k)), _ints(rng, (k, n))
+        assert np.array_equal(oracle.run_table(oracle.schedule_table(0), A, B, 2, two_temp=True),
+                              _exact_matmul_int(A, B))
 
 
 def test_planted_mistakes_are_caught():
@@ -243,6 +244,42 @@ def test_planted_mistakes_are_caught():
     tab = base.copy()
     tab[18, 0] = 0
     assert not np.array_equal(oracle.run_table(tab, A, B, 2), ex)
+
+
+def test_planted_mistakes_in_table2_are_caught():
+    # Table 2 (Sec. 3.3) with X and Y: the shadow (or the exact product) catches a reordered step,
+    # X or Y overwritten while a value in it is still live, and a flipped sign
+    rng = np.random.default_rng(16)
+    A, B = _ints(rng, (8, 16)), _ints(rng, (16, 8))
+    ex = _exact_matmul_int(A, B)
+    base = oracle.schedule_table(0)
+    run = lambda t: oracle.run_table(t, A, B, 2, two_temp=True)
+    caught = 0
+    for i in range(21):  # (a) swap two adjacent steps
+        tab = base.copy()
+        tab[[i, i + 1]] = tab[[i + 1, i]]
+        try:
+            if not np.array_equal(run(tab), ex):
+                caught += 1
+        except RuntimeError:
+            caught += 1
+    assert caught >= 15
+    # (b) S4 = A12 - S2 computed before P6 = S2 T2 reads S2: X is overwritten while S2 is live
+    tab = base.copy()
+    tab[[8, 9]] = tab[[9, 8]]
+    with pytest.raises(RuntimeError):
+        run(tab)
+    # (c) P1 stored in Y instead of X: T2 in Y is still needed by T4 = T2 - B21
+    tab = base.copy()
+    assert tab[11, 1] == 16 and tab[11, 2] == 12  # step 12: P1 -> X
+    tab[11, 2] = 13
+    with pytest.raises(RuntimeError):
+        run(tab)
+    # (d) the sign of U6 = U3 - P4 flipped
+    tab = base.copy()
+    assert tab[19, 1] == 28 and tab[19, 0] == 1
+    tab[19, 0] = 0
+    assert not np.array_equal(run(tab), ex)
 
 
 # --------------------------------------------------------------------------- cutoff (Sec. 3.4)
