@@ -32,6 +32,16 @@ def test_header_declares_entry_points():
         assert s in syms
 
 
+def test_binding_constants_match_the_header():
+    text = open(HEADER).read()
+    defines = dict(re.findall(r"^#define (SW_\w+) (.+)$", text, re.M))
+    for name, val in defines.items():
+        if name in ("SW_PROFILE_KINDS",) or not hasattr(swmm, name):
+            continue
+        assert getattr(swmm, name) == eval(val.replace("u", "").replace("(32 << 20)", "33554432")), name
+    assert swmm.SW_NOALLOC_SCRATCH_BYTES == 32 << 20 and "(32u << 20)" in defines["SW_NOALLOC_SCRATCH_BYTES"]
+
+
 def test_library_exports_every_declared_symbol(lib):
     so = ctypes.CDLL(swmm.library_path())
     missing = [s for s in declared_symbols() if not hasattr(so, s)]

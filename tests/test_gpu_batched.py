@@ -9,6 +9,7 @@ import ctypes
 import numpy as np
 import pytest
 
+import bounds
 import oracle
 from paper_2309_00628_gb300 import inputs, swmm
 
@@ -109,6 +110,7 @@ def test_batched_512_uneven_products(h):
         if i < 6:  # exact oracle rows on a few products
             rows = rng.choice(m, min(m, 4), replace=False)
             R = oracle.naive(A[rows], B)
-            assert np.max(np.abs(C[rows] - R)) / (k * np.max(np.abs(A)) * np.max(np.abs(B))) <= \
-                8 * 2.0 ** -9 / np.sqrt(k) + 2.0 ** -20
+            st, L = swmm.sw_mm_depth(m, n, k, t["cutoff"], swmm.SW_ALGO_WINOGRAD | swmm.SW_SCHED_FUSED, 4)
+            assert st == swmm.SW_OK
+            assert oracle.err_norm(C[rows], R, A, B) <= bounds.tol_tf32(R.size, k, L, A, B)
     assert worst <= 8 * 2.0 ** -9 / np.sqrt(96), worst

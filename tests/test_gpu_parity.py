@@ -3,20 +3,22 @@
 Bars (the normalised error is max|C - C_ref| / (k max|A| max|B|)):
   * integer-valued inputs: bit-exact, on sizes where every partial sum the GPU forms is an
     integer below 2^24 (FP32) -- the bound is computed from the depth and value range;
-  * FP64 path: <= 1e-13;
-  * TF32 path: <= 8 * 2^-9 * 3^L / sqrt(k) + 2^-20.  Each TF32 operand carries a relative error
-    below 2^-10, so a product term errs by < 2^-9 |a||b|; over k random-sign terms the sum's error
-    stays below ~8 sqrt(k) 2^-9 max|a||b| on every element (Hoeffding), i.e. 8 * 2^-9 / sqrt(k)
-    normalised.  One Winograd or Strassen level multiplies the error variance of the worst C
-    quadrant by 18 / 2 = 9 (sum over its products of (#A terms)(#B terms), with k halved), so the
-    RMS error grows by 3 per level.  Every float test also checks the error is far below that of
-    an all-zero result, so a dropped product cannot hide under the bound.
+  * float inputs: the bounds of tests/bounds.py, derived from each leaf kind's arithmetic (TF32
+    truncation, the compensated splits and the FP32 accumulator, FP64 rounding) with the RMS of
+    the product terms, the per-level growth of the worst C quadrant (9 for the Winograd forms,
+    6 for Strassen) and the tail factor of the number of compared elements; FP64 results also
+    meet the 1e-13 bound, split-BF16 results the 2e-6 bound of FP32-equivalent paths.  Every
+    float test also checks the error is far below that of an all-zero result, so a dropped
+    product cannot hide under the bound.
+With SWMM_ERRLOG set, every float comparison appends "test err tol" to that file.
 """
 import ctypes
+import os
 
 import numpy as np
 import pytest
 
+import bounds
 import oracle
 from paper_2309_00628_gb300 import inputs, swmm
 
@@ -38,14 +40,37 @@ def h():
     swmm.sw_destroy(hd)
 
 
-def tol_tf32(k, L):
-    return 8.0 * 2.0 ** -9 * 3.0 ** L / np.sqrt(k) + 2.0 ** -20
+ALGO_NAME = {swmm.SW_ALGO_NAIVE: "naive", W: "winograd", K: "knuth", S: "strassen"}
+
+
+def _algo(variant):
+    return ALGO_NAME[variant & 0xF]
+
+
+def tol_tf32(C, A, B, L, variant=W):
+    return bounds.tol_tf32(np.size(C), A.shape[1], L, A, B, _algo(variant))
+
+
+def tol_bf16x3(C, A, B, L, variant=W):
+    return bounds.tol_bf16x3(np.size(C), A.shape[1], L, A, B, _algo(variant))
+
+
+def tol_tf32x3(C, A, B, L, variant=W):
+    return bounds.tol_tf32x3(np.size(C), A.shape[1], L, A, B, _algo(variant))
+
+
+def tol_fp64(C, A, B, L, variant=W):
+    return bounds.tol_fp64(np.size(C), A.shape[1], L, A, B, _algo(variant))
 
 
 def check_close(C, R, A, B, tol):
     """Normalised error within tol, and far below the error of returning zeros."""
     err = oracle.err_norm(C, R, A, B)
     zero = oracle.err_norm(np.zeros_like(R), R, A, B)
+    log = os.environ.get("SWMM_ERRLOG")
+    if log:
+        with open(log, "a") as f:
+            f.write(f"{os.environ.get('PYTEST_CURRENT_TEST', '?').split(' ')[0]} {err:.3e} {tol:.3e}\n")
     assert err <= tol, (err, tol)
     assert err <= 0.3 * zero, (err, zero)
     return err
@@ -98,7 +123,7 @@ def test_plain_tf32_float_within_bound_and_deterministic(h):
     C2 = run(h, A, B, 0, swmm.SW_ALGO_NAIVE)
     assert np.array_equal(C1, C2)
     R = oracle.naive(A.astype(np.float64), B.astype(np.float64))
-    err = check_close(C1, R, A, B, tol_tf32(k, 0))
+    err = check_close(C1, R, A, B, tol_tf32(C1, A, B, 0, swmm.SW_ALGO_NAIVE))
     assert err > 0  # the tensor core really ran at TF32, not FP32
 
 
@@ -143,7 +168,7 @@ def test_fused_float_within_bound(h, algo, L):
     R = oracle.naive_mt(A.astype(np.float64), B.astype(np.float64))
     C = run(h, A, B, n >> L, algo | FUSED)
     assert depth(h, n, n, n, n >> L, algo | FUSED, 4) == L
-    check_close(C, R, A, B, tol_tf32(n, L))
+    check_close(C, R, A, B, tol_tf32(C, A, B, L, algo))
 
 
 # ------------------------------------------------------------------ materialised schedules
@@ -183,7 +208,7 @@ def test_schedules_float_within_bound(h):
     for sched in (TWO, INPL, ALLOC):
         C = run(h, A, B, 64, W | sched)
         L = depth(h, n, n, n, 64, W | sched, 4)
-        check_close(C, R, A, B, tol_tf32(n, L))
+        check_close(C, R, A, B, tol_tf32(C, A, B, L))
 
 
 # ------------------------------------------------------------------ FP64 path (n = 256, cutoff 32, L = 3)
@@ -201,7 +226,7 @@ def test_fp64_n256_cutoff32(h, algo, sched):
     assert np.array_equal(run(h, Ai, Bi, 32, v, dtype=np.float64), oracle.naive(Ai, Bi))
     A, B = inputs.pair(n, n, n, "uniform", seed=0, dtype=np.float64)
     C = run(h, A, B, 32, v, dtype=np.float64)
-    assert oracle.err_norm(C, oracle.naive(A, B), A, B) <= 1e-13
+    check_close(C, oracle.naive(A, B), A, B, tol_fp64(C, A, B, 0 if algo == swmm.SW_ALGO_NAIVE else 3, v))
 
 
 @pytest.mark.parametrize("odd", [swmm.SW_PAD, swmm.SW_PEEL])
@@ -211,7 +236,7 @@ def test_fp64_odd_sizes(h, odd):
         R = oracle.naive(A, B)
         for v in (W | FUSED, W | TWO, S | ALLOC):
             C = run(h, A, B, 16, v | odd, dtype=np.float64)
-            assert oracle.err_norm(C, R, A, B) <= 1e-13, (m, n, k, v)
+            check_close(C, R, A, B, tol_fp64(C, A, B, depth(h, m, n, k, 16, v | odd, 8), v))
 
 
 @pytest.mark.parametrize("algo", [W, S])
@@ -226,7 +251,7 @@ def test_fp64_fused_deeper_than_three(h, algo, m, n, k, cutoff, L):
         assert np.array_equal(run(h, Ai, Bi, cutoff, v, dtype=np.float64), oracle.naive_mt(Ai, Bi)), v
         A, B = inputs.pair(m, n, k, "uniform", seed=9, dtype=np.float64)
         C = run(h, A, B, cutoff, v, dtype=np.float64)
-        assert oracle.err_norm(C, oracle.naive_mt(A, B), A, B) <= 1e-13, v
+        check_close(C, oracle.naive_mt(A, B), A, B, tol_fp64(C, A, B, L + (1 if leaf else 0), v))
 
 
 # ------------------------------------------------------------------ FP64 leaves with a Winograd step per tile
@@ -242,7 +267,7 @@ def test_fp64_wtile_n256_cutoff32(h, algo, sched):
     assert np.array_equal(run(h, Ai, Bi, 32, v, dtype=np.float64), oracle.naive(Ai, Bi))
     A, B = inputs.pair(n, n, n, "uniform", seed=0, dtype=np.float64)
     C = run(h, A, B, 32, v, dtype=np.float64)
-    assert oracle.err_norm(C, oracle.naive(A, B), A, B) <= 1e-13
+    check_close(C, oracle.naive(A, B), A, B, tol_fp64(C, A, B, 3 + 1, v))  # + the in-tile step
 
 
 @pytest.mark.parametrize("cutoff", [1 << 20, 40])
@@ -257,7 +282,7 @@ def test_fp64_wtile_shapes(h, m, n, k, cutoff):
     for v in (W | FUSED | WT, W | TWO | WT | swmm.SW_PEEL, K | FUSED | WT):
         assert np.array_equal(run(h, Ai, Bi, cutoff, v, dtype=np.float64), Ri), (m, n, k, cutoff, v)
         C = run(h, A, B, cutoff, v, dtype=np.float64)
-        assert oracle.err_norm(C, R, A, B) <= 1e-13, (m, n, k, cutoff, v)
+        check_close(C, R, A, B, tol_fp64(C, A, B, depth(h, m, n, k, cutoff, v, 8) + 1, v))
 
 
 def test_fp64_wtile_is_its_own_leaf(h):
@@ -269,7 +294,8 @@ def test_fp64_wtile_is_its_own_leaf(h):
     C0 = run(h, A, B, 1 << 20, W | FUSED, dtype=np.float64)
     C1 = run(h, A, B, 1 << 20, W | FUSED | WT, dtype=np.float64)
     assert not np.array_equal(C0, C1)
-    assert oracle.err_norm(C0, R, A, B) <= 1e-15 and oracle.err_norm(C1, R, A, B) <= 1e-15
+    check_close(C0, R, A, B, tol_fp64(C0, A, B, 0))
+    check_close(C1, R, A, B, tol_fp64(C1, A, B, 1))
 
 
 # ------------------------------------------------------------------ host entry point, norms, errors
@@ -282,7 +308,7 @@ def test_host_entry_point_matches_device_path(h):
     swmm.check(h, st)
     Cd = run(h, A, B, 256, W | FUSED)
     R = oracle.naive(A.astype(np.float64), B.astype(np.float64))
-    check_close(C.astype(np.float64), R, A, B, tol_tf32(k, 1))
+    check_close(C.astype(np.float64), R, A, B, tol_tf32(C, A, B, 1))
     assert np.max(np.abs(C - Cd)) <= 1e-3
 
 
@@ -307,7 +333,7 @@ def test_host_entry_point_row_panels(h, algo):
         if kind == "int":
             assert np.array_equal(C, R)
         else:
-            check_close(C, R, A, B, tol_tf32(k, L))
+            check_close(C, R, A, B, tol_tf32(C, A, B, L, algo))
 
 
 def test_error_norms_match_numpy(h):
@@ -349,7 +375,7 @@ def test_full_size_sampled_rows(h, L):
     rows = np.random.Generator(np.random.PCG64(99)).choice(n, 8, replace=False)
     R = oracle.naive_mt(A[rows].astype(np.float64), B.astype(np.float64))
     Cr = C[torch.from_numpy(rows).cuda()].cpu().numpy().astype(np.float64)
-    check_close(Cr, R, A, B, tol_tf32(n, L))
+    check_close(Cr, R, A, B, tol_tf32(Cr, A, B, L, v))
 
 
 # ------------------------------------------------------------------ split-BF16 leaves (hi*hi + hi*lo + lo*hi)
@@ -357,10 +383,6 @@ def test_full_size_sampled_rows(h, L):
 # 2^-16 |a b|: each product term errs by < 3 * 2^-16 |a||b|, so the same Hoeffding argument as
 # for TF32 gives 8 * 3 * 2^-16 * 3^L / sqrt(k) (normalised), 40x tighter than TF32.
 BF = swmm.SW_LEAF_BF16X3
-
-
-def tol_bf16x3(k, L):
-    return 8.0 * 3.0 * 2.0 ** -16 * 3.0 ** L / np.sqrt(k) + 2.0 ** -20
 
 
 @pytest.mark.parametrize("m,n,k", [(128, 128, 64), (300, 500, 200), (1000, 1000, 1000), (129, 257, 33)])
@@ -373,16 +395,14 @@ def test_bf16x3_plain_float_far_tighter_than_tf32(h):
     m, n, k = 777, 640, 1500
     A, B = inputs.pair(m, n, k, "uniform", seed=71, dtype=np.float32)
     R = oracle.naive(A.astype(np.float64), B.astype(np.float64))
-    e_bf = check_close(run(h, A, B, 0, swmm.SW_ALGO_NAIVE | BF), R, A, B, tol_bf16x3(k, 0))
-    e_tf = check_close(run(h, A, B, 0, swmm.SW_ALGO_NAIVE), R, A, B, tol_tf32(k, 0))
+    e_bf = check_close(run(h, A, B, 0, swmm.SW_ALGO_NAIVE | BF), R, A, B, tol_bf16x3(R, A, B, 0))
+    e_tf = check_close(run(h, A, B, 0, swmm.SW_ALGO_NAIVE), R, A, B, tol_tf32(R, A, B, 0))
     assert e_bf < e_tf / 16, (e_bf, e_tf)
 
 
-@pytest.mark.parametrize("algo", [W, S])
-@pytest.mark.parametrize("sched", [FUSED, TWO, INPL, ALLOC])
+@pytest.mark.parametrize("algo,sched", [(W, FUSED), (W, TWO), (W, INPL), (W, ALLOC), (S, FUSED), (S, ALLOC)])
 def test_bf16x3_recursive(h, algo, sched):
-    if algo == S and sched in (TWO, INPL):
-        pytest.skip("Tables 2 and 3 are Winograd schedules")
+    # (Tables 2 and 3 are Winograd schedules: Strassen runs FUSED and allocating only)
     n, cutoff = 512, 128  # L = 2
     v = algo | sched | BF
     L = depth(h, n, n, n, cutoff, v, 4)
@@ -391,7 +411,7 @@ def test_bf16x3_recursive(h, algo, sched):
     assert np.array_equal(run(h, Ai, Bi, cutoff, v), oracle.naive(Ai, Bi))
     A, B = inputs.pair(n, n, n, "uniform", seed=73, dtype=np.float32)
     R = oracle.naive(A.astype(np.float64), B.astype(np.float64))
-    check_close(run(h, A, B, cutoff, v), R, A, B, tol_bf16x3(n, L))
+    check_close(run(h, A, B, cutoff, v), R, A, B, min(2e-6, tol_bf16x3(R, A, B, L, algo)))
 
 
 def test_bf16x3_odd_sizes_fused_and_two_temp(h):
@@ -414,8 +434,7 @@ def test_bf16x3_two_temp_n16384_normal_sampled_rows(h):
     rows = np.random.Generator(np.random.PCG64(98)).choice(n, 6, replace=False)
     R = oracle.naive_mt(A[rows].astype(np.float64), B.astype(np.float64))
     Cr = C[torch.from_numpy(rows).cuda()].cpu().numpy().astype(np.float64)
-    err = check_close(Cr, R, A, B, 2e-6)
-    assert err <= tol_bf16x3(n, 2)
+    check_close(Cr, R, A, B, min(2e-6, tol_bf16x3(Cr, A, B, 2)))
     del dA, dB, C
     torch.cuda.empty_cache()
 
@@ -459,8 +478,8 @@ def test_knuth_and_bdpz_errors_agree_by_depth(h):
     A, B = inputs.pair(n, n, n, "uniform", seed=60, dtype=np.float32)
     R = oracle.naive_mt(A.astype(np.float64), B.astype(np.float64))
     for L in (1, 2, 3):
-        ew = check_close(run(h, A, B, n >> L, W | FUSED), R, A, B, tol_tf32(n, L))
-        ek = check_close(run(h, A, B, n >> L, K | FUSED), R, A, B, tol_tf32(n, L))
+        ew = check_close(run(h, A, B, n >> L, W | FUSED), R, A, B, tol_tf32(R, A, B, L, W))
+        ek = check_close(run(h, A, B, n >> L, K | FUSED), R, A, B, tol_tf32(R, A, B, L, K))
         assert 0.5 <= ek / ew <= 2.0, (L, ek, ew)
 
 
@@ -470,8 +489,8 @@ def test_knuth_fp64_matches_oracle_knuth_recursion(h):
     n = 256
     A, B = inputs.pair(n, n, n, "uniform", seed=61, dtype=np.float64)
     C = run(h, A, B, 32, K | FUSED, dtype=np.float64)
-    assert oracle.err_norm(C, oracle.recursive(oracle.KNUTH, A, B, 32), A, B) <= 1e-13
-    assert oracle.err_norm(C, oracle.naive(A, B), A, B) <= 1e-13
+    check_close(C, oracle.recursive(oracle.KNUTH, A, B, 32), A, B, tol_fp64(C, A, B, 3, K))
+    check_close(C, oracle.naive(A, B), A, B, tol_fp64(C, A, B, 3, K))
 
 
 def test_knuth_only_in_fused_schedule(h):
@@ -492,10 +511,6 @@ def test_knuth_only_in_fused_schedule(h):
 X3 = swmm.SW_LEAF_TF32X3
 
 
-def tol_tf32x3(k, L):
-    return 8.0 * 2.0 ** -19 * 3.0 ** L / np.sqrt(k) + 2.0 ** -20
-
-
 @pytest.mark.parametrize("m,n,k", [(128, 128, 64), (300, 500, 200), (1000, 1000, 1000), (129, 257, 33)])
 def test_tf32x3_plain_integers_bit_exact(h, m, n, k):
     A, B = inputs.pair(m, n, k, "int", seed=80, dtype=np.float64)
@@ -509,9 +524,9 @@ def test_tf32x3_plain_float_far_tighter_than_tf32(h):
     m, n, k = 777, 640, 1500
     A, B = inputs.pair(m, n, k, "uniform", seed=81, dtype=np.float32)
     R = oracle.naive(A.astype(np.float64), B.astype(np.float64))
-    e_x3 = check_close(run(h, A, B, 0, swmm.SW_ALGO_NAIVE | X3), R, A, B, tol_tf32x3(k, 0))
-    e_bf = check_close(run(h, A, B, 0, swmm.SW_ALGO_NAIVE | BF), R, A, B, tol_bf16x3(k, 0))
-    e_tf = check_close(run(h, A, B, 0, swmm.SW_ALGO_NAIVE), R, A, B, tol_tf32(k, 0))
+    e_x3 = check_close(run(h, A, B, 0, swmm.SW_ALGO_NAIVE | X3), R, A, B, tol_tf32x3(R, A, B, 0))
+    e_bf = check_close(run(h, A, B, 0, swmm.SW_ALGO_NAIVE | BF), R, A, B, tol_bf16x3(R, A, B, 0))
+    e_tf = check_close(run(h, A, B, 0, swmm.SW_ALGO_NAIVE), R, A, B, tol_tf32(R, A, B, 0))
     assert e_x3 < e_tf / 16 and e_x3 < 4 * e_bf, (e_x3, e_bf, e_tf)
 
 
@@ -526,7 +541,7 @@ def test_tf32x3_recursive(h, algo, sched):
     assert np.array_equal(run(h, Ai, Bi, cutoff, v), oracle.naive(Ai, Bi))
     A, B = inputs.pair(n, n, n, "uniform", seed=83, dtype=np.float32)
     R = oracle.naive(A.astype(np.float64), B.astype(np.float64))
-    check_close(run(h, A, B, cutoff, v), R, A, B, tol_tf32x3(n, L))
+    check_close(run(h, A, B, cutoff, v), R, A, B, tol_tf32x3(R, A, B, L, algo))
 
 
 def test_tf32x3_odd_sizes(h):

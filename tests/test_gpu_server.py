@@ -13,6 +13,7 @@ import threading
 import numpy as np
 import pytest
 
+import bounds
 import oracle
 from paper_2309_00628_gb300 import inputs, swmm
 
@@ -42,8 +43,7 @@ def srv(h):
     swmm.check(h, swmm.sw_server_stop(h))
 
 
-def tol_tf32(k, L):
-    return 8.0 * 2.0 ** -9 * 3.0 ** L / np.sqrt(k) + 2.0 ** -20
+ALGO_NAME = {0: "naive", 1: "strassen", 2: "winograd", 3: "knuth"}
 
 
 def device_problem(m, n, k, dist, seed, eb=4, lim=2):
@@ -106,7 +106,7 @@ def test_server_mix_integers_bit_exact(srv):
 
 
 def test_server_mix_floats(srv, h):
-    """Float inputs: the TF32 bound (FP64: 1e-13), and NAIVE results identical to solo sw_smm."""
+    """Float inputs: the TF32 / FP64 bounds of the parity tests, and NAIVE results identical to solo sw_smm."""
     cases = [(512, 512, 512, 4, 0, N), (1024, 768, 1024, 4, 256, W | FUSED), (2048, 2048, 2048, 4, 1024, S | FUSED),
              (300, 500, 200, 8, 64, W | FUSED), (640, 384, 896, 4, 0, N), (1000, 1000, 1000, 4, 256, W | TWO)]
     probs = []
@@ -127,7 +127,8 @@ def test_server_mix_floats(srv, h):
         st, L = swmm.sw_mm_depth(m, n, k, cutoff, var, eb)
         err = oracle.err_norm(C, R, A, B)
         zero = oracle.err_norm(np.zeros_like(R), R, A, B)
-        tol = 1e-13 if eb == 8 else tol_tf32(k, L)
+        bound = bounds.tol_fp64 if eb == 8 else bounds.tol_tf32
+        tol = bound(C.size, k, L, A, B, ALGO_NAME[var & 0xF])
         assert err <= tol and err <= 0.3 * zero, ((m, n, k, cutoff, hex(var)), err, tol)
         if var == N and eb == 4:
             solo = torch.full_like(dC, float("nan"))
