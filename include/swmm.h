@@ -284,15 +284,19 @@ sw_status sw_profile_read(sw_handle h, int nkinds, int *launches, double *ms);
  * Computes C <- A B (FP32, row-major) with one Strassen-Winograd level in the FUSED schedule and
  * TF32 leaves -- the same arithmetic as sw_smm with SW_ALGO_WINOGRAD | SW_SCHED_FUSED at depth 1.
  * The caller provides A, B and C; every temporary (B^T, the S and T sums, descriptors, the error
- * word) lives in one static device array of SW_NOALLOC_SCRATCH_BYTES, reserved on every GPU that
- * loads the library until the process exits.  A problem fits when
+ * word) lives in one static device array of SW_NOALLOC_SCRATCH_BYTES, which every GPU that loads
+ * this code holds until the process exits.  A problem fits when
  *   4 * (n * ceil4(k) + 4 * ceil(m/2) * kb + 4 * ceil4(ceil(n/2)) * kb) + ~2 KiB <= 32 MiB,
  *   kb = ceil32(ceil(k/2))   (square problems up to n of about 1670);
  * larger problems return SW_EBUDGET without touching memory.
  * Requirements: m, n, k >= 2; A and C 16-byte aligned; lda and ldc multiples of 4 (else SW_EINVAL).
  * The call is synchronous: it waits for `stream` and returns SW_ETIMEOUT if a bounded device wait
- * expired, SW_ECUDA on a CUDA error.  The first call on a device also looks up the array's device
- * address (once per device, with that device current); make that first call before any stream
+ * expired, SW_ECUDA on a CUDA error.  The first call on a device does a one-time set-up with that
+ * device current: it looks up the array's device address and loads the kernels the call uses.
+ * With CUDA's default lazy module loading that set-up is when the array (and the kernels' code)
+ * take their device memory; later calls take none.  A caller that reserves the GPU's memory for
+ * itself should therefore make its first call before reserving (or run with
+ * CUDA_MODULE_LOADING=EAGER, which places them when the context is created), and before any stream
  * capture.  All calls share the one array and overwrite it: calls that overlap on the GPU (other
  * streams, other host threads) race and must be serialised by the caller. */
 #define SW_NOALLOC_SCRATCH_BYTES (32u << 20)

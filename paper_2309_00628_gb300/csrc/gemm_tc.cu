@@ -885,6 +885,11 @@ cudaError_t launch_gemm_bf16x3(int bn, const MapSet& maps, const CUtensorMap* gm
                                             err, grid, stream, nullptr, item_leaf, item_tile, units);
 }
 
+cudaError_t preload_gemm_tf32() {
+    cudaError_t e = tc_setup<MODE_TF32, 128, false, false>(nullptr);
+    return e != cudaSuccess ? e : tc_setup<MODE_TF32, 256, false, false>(nullptr);
+}
+
 int tf32_tile_m() { return TF_BM; }
 int tf32_tile_k() { return TF_BK; }
 int bf16x3_tile_k() { return 64; }

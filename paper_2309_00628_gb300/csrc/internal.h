@@ -52,6 +52,10 @@ int gemm_tf32n_pair_units(int sms, int bn = 256);
 cudaError_t launch_gemm_tf32_resident(const CUtensorMap* gmaps, const Leaf* leaves, const Target* targets,
                                       const CUtensorMap* tmaps, const ResidentCtl& ctl, int* err, int grid,
                                       cudaStream_t stream, bool nmajor);
+// Load the one-CTA, non-resident B^T-form TF32 kernels (tile widths 128 and 256) into device memory
+// now and set their shared-memory attribute; with lazy module loading they would be loaded at
+// their first launch.
+cudaError_t preload_gemm_tf32();
 int tf32_tile_m();
 int tf32_tile_k();
 int bf16x3_tile_k();
@@ -92,6 +96,9 @@ constexpr int F64_BM = 64, F64_BN = 64;
 // out (out_rows x out_cols) <- x^T, zero outside the source extent (src_rows x src_cols).
 cudaError_t launch_transpose_pad(int out_rows, int out_cols, float* out, long long ldo, const float* x,
                                  long long ldx, int src_rows, int src_cols, cudaStream_t s);
+// Load the kernels launch_transpose_pad may launch and the FP32 depth-1 BDPZ operand-sum kernels
+// of launch_preadd (A side, and B side held as B^T; vector and scalar forms) into device memory now.
+cudaError_t preload_transpose_preadd_f32_l1();
 // x (n x n view) <- x^T in place.
 cudaError_t launch_transpose_inplace(int n, float* x, long long ld, cudaStream_t s);
 

@@ -885,6 +885,23 @@ cudaError_t launch_transpose_pad(int out_rows, int out_cols, float* out, long lo
     return cudaGetLastError();
 }
 
+cudaError_t preload_transpose_preadd_f32_l1() {
+    // cudaFuncGetAttributes makes the runtime load a kernel that lazy module loading would
+    // otherwise load at its first launch
+    cudaFuncAttributes fa;
+    const void* fns[] = {
+        reinterpret_cast<const void*>(transpose_pad_kernel), reinterpret_cast<const void*>(transpose64_kernel),
+        reinterpret_cast<const void*>(preadd_kernel<float, 4, 1, 2, false, false>),
+        reinterpret_cast<const void*>(preadd_kernel<float, 4, 1, 2, true, true>),
+        reinterpret_cast<const void*>(preadd_kernel<float, 1, 1, 2, false, false>),
+        reinterpret_cast<const void*>(preadd_kernel<float, 1, 1, 2, true, true>)};
+    for (const void* f : fns) {
+        const cudaError_t e = cudaFuncGetAttributes(&fa, f);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 // In-place transpose of an n x n view: tile pair (bi, bj), bi <= bj, swapped through shared memory.
 __global__ void transpose_inplace_kernel(float* __restrict__ x, long long ld, int n) {
     const int bi = blockIdx.y, bj = blockIdx.x;

@@ -9,8 +9,17 @@
 // the cost of cudaMalloc / cudaFree.  This entry point takes the inputs and the output from the
 // caller and keeps every temporary -- B^T, the operand sums S1..S4 and T1..T4, the leaf and
 // target descriptors and the device error word -- in one file-scope __device__ array of fixed
-// size, reserved when the library is loaded and held on every GPU that loads it until the
-// process exits.
+// size.
+//
+// When the memory is taken: the array lives in this file's CUDA module, and the kernels the call
+// launches live in the library's other modules.  CUDA loads modules and kernels lazily by default
+// (at their first use), so the first call on a device does a one-time set-up with that device
+// current: it resolves the array's device address (which loads the module and places the array
+// in device memory) and loads every kernel the call launches.  From then on the array stays on
+// that device until the process exits and no call takes device memory.  A caller that reserves
+// the GPU's memory for itself should make its first call before reserving (or run with
+// CUDA_MODULE_LOADING=EAGER, which loads everything when the context is created), and before any
+// stream capture.
 //
 // All calls share that array and each call overwrites it.  Calls that overlap on the GPU (two
 // streams, or two host threads) race on it; callers must serialise them.
@@ -34,22 +43,34 @@ constexpr int kMaxDevices = 64;
 // device address is obtained with cudaGetSymbolAddress below and passed to the kernels.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
+__global__ void noalloc_describe(swk::Leaf* leaves, swk::Target* targets, float* C, long long ldc, int m, int n,
+                                 int mb, int kb, int nb, int tiles_n, int tiles_per_leaf, int vec_ok);
+
 std::mutex g_mu;
 unsigned char* g_scratch_ptr[kMaxDevices] = {nullptr};
+int g_sms[kMaxDevices] = {0};
 
-// Device address of the scratch array on the current device; resolved once per device (the
-// device must be current).  Returns nullptr on failure.
-unsigned char* scratch_address(int dev) {
+// One-time set-up of device `dev` (the current device): the scratch array's device address, the
+// SM count, and every kernel the call launches loaded into device memory (so that with lazy
+// module loading no later call takes device memory).  Returns nullptr on failure.
+unsigned char* device_setup(int dev, int* sms) {
     if (dev < 0 || dev >= kMaxDevices) return nullptr;
     std::lock_guard<std::mutex> lock(g_mu);
     if (!g_scratch_ptr[dev]) {
         void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) {
+        cudaFuncAttributes fa;
+        int n = 0;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess ||
+            cudaFuncGetAttributes(&fa, reinterpret_cast<const void*>(noalloc_describe)) != cudaSuccess ||
+            swk::preload_gemm_tf32() != cudaSuccess || swk::preload_transpose_preadd_f32_l1() != cudaSuccess ||
+            cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
             cudaGetLastError();
             return nullptr;
         }
+        g_sms[dev] = n;
         g_scratch_ptr[dev] = static_cast<unsigned char*>(p);
     }
+    *sms = g_sms[dev];
     return g_scratch_ptr[dev];
 }
 
@@ -173,7 +194,8 @@ extern "C" sw_status sw_smm_noalloc(const float* A, int lda, const float* B, int
     if (L.total > kScratchBytes) return SW_EBUDGET;  // the problem does not fit the static scratch
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return SW_ECUDA; }
-    unsigned char* base = scratch_address(dev);
+    int sms = 0;
+    unsigned char* base = device_setup(dev, &sms);
     if (!base) return SW_ECUDA;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     int* err = reinterpret_cast<int*>(base + L.err);
@@ -220,14 +242,14 @@ extern "C" sw_status sw_smm_noalloc(const float* A, int lda, const float* B, int
     if (e == cudaSuccess) e = swk::launch_preadd(4, pa, s);
     if (e == cudaSuccess) e = swk::launch_preadd(4, pb, s);
     if (e == cudaSuccess) e = cudaMemset2DAsync(C, (size_t)ldc * 4, 0, (size_t)n * 4, (size_t)m, s);  // C is summed into
-    int sms = 148;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
         e = swk::launch_gemm_tf32(bn, maps, nullptr, leaves, 7, targets, nullptr, nullptr, 7 * tiles_per_leaf, err,
                                   sms, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    // the error word comes back on the caller's stream (no legacy-stream copy, which would wait for
+    // every other blocking stream of the device)
     int code = 0;
-    if (e == cudaSuccess) e = cudaMemcpy(&code, err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&code, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) { cudaGetLastError(); return SW_ECUDA; }
     return code ? SW_ETIMEOUT : SW_OK;
 }

@@ -18,6 +18,7 @@ SW_ALGO_NAIVE, SW_ALGO_STRASSEN, SW_ALGO_WINOGRAD, SW_ALGO_WINOGRAD_KNUTH = 0x0,
 SW_SCHED_FUSED, SW_SCHED_TWO_TEMP, SW_SCHED_IN_PLACE, SW_SCHED_ALLOC = 0x00, 0x10, 0x20, 0x30
 SW_PAD, SW_PEEL = 0x000, 0x100
 SW_LEAF_TF32, SW_LEAF_BF16X3, SW_LEAF_TF32X3, SW_LEAF_F64_WTILE = 0x0000, 0x1000, 0x2000, 0x3000
+SW_NOALLOC_SCRATCH_BYTES = 32 << 20  # the static device array of sw_smm_noalloc
 
 
 class sw_problem(ctypes.Structure):
