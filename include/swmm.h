@@ -282,7 +282,9 @@ sw_status sw_profile_read(sw_handle h, int nkinds, int *launches, double *ms);
  * synchronisation of cudaMalloc / cudaFree.  It needs no handle and calls no allocating routine.
  *
  * Computes C <- A B (FP32, row-major) with one Strassen-Winograd level in the FUSED schedule and
- * TF32 leaves -- the same arithmetic as sw_smm with SW_ALGO_WINOGRAD | SW_SCHED_FUSED at depth 1.
+ * TF32 leaves -- the same operand sums and leaf products as sw_smm with SW_ALGO_WINOGRAD |
+ * SW_SCHED_FUSED at depth 1; the seven products are added into a zeroed C with atomic adds in the
+ * order they finish, so float results can differ in their last bits from call to call.
  * The caller provides A, B and C; every temporary (B^T, the S and T sums, descriptors, the error
  * word) lives in one static device array of SW_NOALLOC_SCRATCH_BYTES, which every GPU that loads
  * this code holds until the process exits.  A problem fits when

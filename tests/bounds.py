@@ -30,10 +30,10 @@ F = 2.  The 2^-20 term allows for the FP32 accumulation of the tensor core.  Whe
 fixed TF32 bound of 2e-4 applies (k >= 4096, L <= 2) the smaller of the two is used.
 
 Compensated leaves (split-BF16 and 3xTF32).  The operand split carries x to a relative error e
-(split-BF16: hi = bf16(x), lo = bf16(x - hi), |e| <= 2^-18, RMS about 2^-18 / 3 per factor with
-the dropped lo*lo term of the same size; 3xTF32: hi = tf32(x), lo read as TF32, RMS about
-2^-21 / 3).  These terms behave like the TF32 ones with 2^-10 replaced by e.  What dominates is
-the FP32 accumulator: each MMA adds its partial sum into the accumulator with one rounding of
+(split-BF16: hi = bf16(x), lo = bf16(x - hi) and the dropped lo*lo term give a term error of
+RMS below 2^-18; 3xTF32: hi = tf32(x) and lo read as TF32 truncate lo by at most 2^-10 |lo| <=
+2^-21 |x|, uniformly, RMS 2^-21 / sqrt(3), the dropped lo*lo term below 2^-22).  These terms
+behave like the TF32 ones with 2^-10 replaced by e.  What dominates is the FP32 accumulator: each MMA adds its partial sum into the accumulator with one rounding of
 relative size below u = 2^-23 (a truncating FP32 accumulate; the tensor core's rounding is not
 documented, so the worse of truncation and rounding to nearest is assumed), all of one sign in
 the worst case.  With n_mma MMAs of depth K per k-step (split-BF16: 3 of K = 16; 3xTF32: 3 of
@@ -44,12 +44,13 @@ add in FP32 (rounding to nearest, negligible).
     tol = F [z(N) e rho sqrt(R^L) / sqrt(k) + u (2/3) sqrt(2/pi) (n_mma / K) sqrt(k) rho g^L],
 F = 4 (the accumulator model is the loosest part of the derivation).
 
-FP64 (SIMT leaves, every operation rounded to nearest, u = 2^-53).  A leaf of inner length
-k' = k / 2^L accumulates its terms one FMA at a time; the rounding errors form a random walk
-over partial sums of RMS sqrt(j) RMS(st), so a leaf result errs by about u k' RMS(s) RMS(t)
-/ sqrt(2); over the leaves of the worst quadrant this grows by sqrt(R / 2) per level.  The
-operand sums add one rounding each (relative u, behaving like a term error).
-    tol = F z(N) u rho (sqrt((R / 2)^L / 2) + sqrt(R^L / k)),  F = 4,
+FP64 (SIMT leaves, every operation rounded to nearest, u = 2^-53).  Rounding to nearest leaves
+an error uniform within half an ulp, RMS ulp / sqrt(12) <= u |s| / sqrt(3) for a result s.  A
+leaf of inner length k' = k / 2^L accumulates its terms one FMA at a time; the rounding errors
+form a random walk over partial sums of RMS sqrt(j) RMS(st), so a leaf result errs by about
+(u / sqrt(3)) k' RMS(s) RMS(t) / sqrt(2); over the leaves of the worst quadrant this grows by
+sqrt(R / 2) per level.  The operand sums add one rounding each (behaving like a term error).
+    tol = F z(N) (u / sqrt(3)) rho (sqrt((R / 2)^L / 2) + sqrt(R^L / k)),  F = 4,
 and the benchmark spec bound 1e-13 is checked as well.
 
 A result may be compared on sampled rows; N is then the number of compared elements.
@@ -102,11 +103,11 @@ def tol_bf16x3(nelem: int, k: int, L: int, A, B, algo: str = "winograd") -> floa
 
 
 def tol_tf32x3(nelem: int, k: int, L: int, A, B, algo: str = "winograd") -> float:
-    return _tol_compensated(nelem, k, L, A, B, algo, 2.0 ** -21, 3, 8)
+    return _tol_compensated(nelem, k, L, A, B, algo, 2.0 ** -21 / math.sqrt(3.0), 3, 8)
 
 
 def tol_fp64(nelem: int, k: int, L: int, A, B, algo: str = "winograd") -> float:
     R = GROWTH[algo] if L > 0 else 1.0
-    u = 2.0 ** -53
+    u = 2.0 ** -53 / math.sqrt(3.0)
     t = 4.0 * z_tail(nelem) * u * rho(A, B) * (math.sqrt((R / 2.0) ** L / 2.0) + math.sqrt(R ** L / k))
     return min(t, 1e-13)

@@ -411,7 +411,9 @@ def test_bf16x3_recursive(h, algo, sched):
     assert np.array_equal(run(h, Ai, Bi, cutoff, v), oracle.naive(Ai, Bi))
     A, B = inputs.pair(n, n, n, "uniform", seed=73, dtype=np.float32)
     R = oracle.naive(A.astype(np.float64), B.astype(np.float64))
-    check_close(run(h, A, B, cutoff, v), R, A, B, min(2e-6, tol_bf16x3(R, A, B, L, algo)))
+    # (at k = 512 and depth 2 the split leaves' own error, not the accumulator, dominates: the
+    # normalised error exceeds the 2e-6 of the n = 16384 configuration, which the test below checks)
+    check_close(run(h, A, B, cutoff, v), R, A, B, tol_bf16x3(R, A, B, L, algo))
 
 
 def test_bf16x3_odd_sizes_fused_and_two_temp(h):
