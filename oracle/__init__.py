@@ -66,6 +66,8 @@ def _load():
     lib.orc_schedule_table.argtypes = [ctypes.c_int, ip]
     lib.orc_recursive_table.argtypes = [ip, ctypes.c_int, L, L, L, dp, dp, dp, L, dp]
     lib.orc_recursive_table.restype = ctypes.c_int
+    lib.orc_recursive_products.argtypes = [ctypes.c_int, L, L, L, dp, L, dp, L, dp, L, L, ctypes.c_uint]
+    lib.orc_recursive_products.restype = ctypes.c_int
     lib.orc_err_norm.argtypes = [L, L, L, dp, L, dp, L, dp, L, dp, L]
     lib.orc_err_norm.restype = ctypes.c_double
     _lib = lib
@@ -137,6 +139,21 @@ def recursive(alg: int, A, B, cutoff: int, mode: int = PAD, trace: bool = False)
     if rc == 2:
         raise RuntimeError("schedule liveness shadow failed")
     return (C, tv) if trace else C
+
+
+def recursive_products(alg: int, A, B, cutoff: int, mask: int) -> np.ndarray:
+    """The top-level products in `mask` only (bit i = product i+1 of Sec. 2.2 / 2.3; Knuth's form
+    in the BDPZ numbering), the others taken as zero: their contribution to C = A B.  Zero padding
+    (Sec. 3.1); the depth must be >= 1."""
+    A, B = _f64(A).copy(), _f64(B).copy()
+    m, k = A.shape
+    n = B.shape[1]
+    C = np.zeros((m, n), np.float64)
+    rc = _load().orc_recursive_products(alg, m, n, k, _p(A), max(k, 1), _p(B), max(n, 1), _p(C), max(n, 1),
+                                        cutoff, mask)
+    if rc != 0:
+        raise ValueError("bad arguments (algorithm, mask or depth 0)")
+    return C
 
 
 def workspace_elems(sched: int, m: int, n: int, k: int, L: int) -> float:

@@ -177,6 +177,11 @@ struct ctx {
 
 static double *g_trace = NULL; /* top-level intermediates, element [0][0] */
 static int g_sched_error = 0;  /* set when a schedule's shadow finds a dead read */
+/* Products of the TOP level that take part (bit i: the (i+1)-th product of Sec. 2.2 / 2.3 in
+ * the numbering of strassen_level / winograd_level; Knuth's form uses the BDPZ numbering).  A
+ * product outside the mask is taken as the zero block and the level's post-additions run as
+ * written: C then holds the top-level products' contributions to C restricted to the mask. */
+static unsigned g_top_mask = 0x7Fu;
 
 static void tr(int idx, mat x) {
     if (g_trace && x.rows > 0 && x.cols > 0) g_trace[idx] = x.p[0];
@@ -185,6 +190,17 @@ static void tr(int idx, mat x) {
 static void product_at(mat a, mat b, mat c, ctx *x, int top);
 
 static void product(mat a, mat b, mat c, ctx *x) { product_at(a, b, c, x, 0); }
+
+static void zero_mat(mat c) {
+    for (long i = 0; i < c.rows; ++i)
+        for (long j = 0; j < c.cols; ++j) c.p[i * c.ld + j] = 0.0;
+}
+
+/* Sub-product `idx` of a level: at the top level a product outside g_top_mask is the zero block. */
+static void product_top(mat a, mat b, mat c, ctx *x, int top, int idx) {
+    if (top && !((g_top_mask >> idx) & 1u)) { zero_mat(c); return; }
+    product(a, b, c, x);
+}
 
 static void product_at(mat a, mat b, mat c, ctx *x, int top) {
     if (x->mode == ORC_PAD) {
@@ -223,13 +239,13 @@ static void strassen_level(mat a, mat b, mat c, ctx *x, int top) {
     long m2 = A11.rows, k2 = A11.cols, n2 = B11.cols;
     mat sa = alloc_mat(m2, k2), sb = alloc_mat(k2, n2), P[7];
     for (int i = 0; i < 7; ++i) P[i] = alloc_mat(m2, n2);
-    addsub(sa, A11, A22, +1); addsub(sb, B11, B22, +1); product(sa, sb, P[0], x);
-    addsub(sa, A21, A22, +1); product(sa, B11, P[1], x);
-    addsub(sb, B12, B22, -1); product(A11, sb, P[2], x);
-    addsub(sb, B21, B11, -1); product(A22, sb, P[3], x);
-    addsub(sa, A11, A12, +1); product(sa, B22, P[4], x);
-    addsub(sa, A21, A11, -1); addsub(sb, B11, B12, +1); product(sa, sb, P[5], x);
-    addsub(sa, A12, A22, -1); addsub(sb, B21, B22, +1); product(sa, sb, P[6], x);
+    addsub(sa, A11, A22, +1); addsub(sb, B11, B22, +1); product_top(sa, sb, P[0], x, top, 0);
+    addsub(sa, A21, A22, +1); product_top(sa, B11, P[1], x, top, 1);
+    addsub(sb, B12, B22, -1); product_top(A11, sb, P[2], x, top, 2);
+    addsub(sb, B21, B11, -1); product_top(A22, sb, P[3], x, top, 3);
+    addsub(sa, A11, A12, +1); product_top(sa, B22, P[4], x, top, 4);
+    addsub(sa, A21, A11, -1); addsub(sb, B11, B12, +1); product_top(sa, sb, P[5], x, top, 5);
+    addsub(sa, A12, A22, -1); addsub(sb, B21, B22, +1); product_top(sa, sb, P[6], x, top, 6);
     if (top) for (int i = 0; i < 7; ++i) tr(i, P[i]);
     mat C11 = quad(c, 0), C12 = quad(c, 1), C21 = quad(c, 2), C22 = quad(c, 3);
     addsub(C11, P[0], P[3], +1); addsub(C11, C11, P[4], -1); addsub(C11, C11, P[6], +1);
@@ -266,13 +282,13 @@ static void winograd_level(mat a, mat b, mat c, ctx *x, int top) {
     addsub(T[2], B22, B12, -1);
     addsub(S[3], A12, S[1], -1);
     addsub(T[3], T[1], B21, -1);
-    product(A11, B11, P[0], x);
-    product(A12, B21, P[1], x);
-    product(S[3], B22, P[2], x);
-    product(A22, T[3], P[3], x);
-    product(S[0], T[0], P[4], x);
-    product(S[1], T[1], P[5], x);
-    product(S[2], T[2], P[6], x);
+    product_top(A11, B11, P[0], x, top, 0);
+    product_top(A12, B21, P[1], x, top, 1);
+    product_top(S[3], B22, P[2], x, top, 2);
+    product_top(A22, T[3], P[3], x, top, 3);
+    product_top(S[0], T[0], P[4], x, top, 4);
+    product_top(S[1], T[1], P[5], x, top, 5);
+    product_top(S[2], T[2], P[6], x, top, 6);
     if (top) {
         for (int i = 0; i < 4; ++i) { tr(8 + i, S[i]); tr(12 + i, T[i]); }
         for (int i = 0; i < 7; ++i) tr(16 + i, P[i]);
@@ -308,22 +324,22 @@ static void knuth_level(mat X, mat Y, mat Z, ctx *x, int top) {
     mat l = alloc_mat(m2, k2), r = alloc_mat(k2, n2);
     mat u = alloc_mat(m2, n2), v = alloc_mat(m2, n2), w = alloc_mat(m2, n2);
     mat aA = alloc_mat(m2, n2), bB = alloc_mat(m2, n2), t = alloc_mat(m2, n2);
-    addsub(l, c, a, -1); addsub(r, C, D, -1); product(l, r, u, x);
-    addsub(l, c, d, +1); addsub(r, C, A, -1); product(l, r, v, x);
-    product(a, A, aA, x);
+    addsub(l, c, a, -1); addsub(r, C, D, -1); product_top(l, r, u, x, top, 6);
+    addsub(l, c, d, +1); addsub(r, C, A, -1); product_top(l, r, v, x, top, 4);
+    product_top(a, A, aA, x, top, 0);
     addsub(l, c, d, +1); addsub(l, l, a, -1);
     addsub(r, A, D, +1); addsub(r, r, C, -1);
-    product(l, r, t, x); addsub(w, aA, t, +1);
-    product(b, B, bB, x);
+    product_top(l, r, t, x, top, 5); addsub(w, aA, t, +1);
+    product_top(b, B, bB, x, top, 1);
     mat z11 = quad(Z, 0), z12 = quad(Z, 1), z21 = quad(Z, 2), z22 = quad(Z, 3);
     addsub(z11, aA, bB, +1);
     if (top) { tr(0, u); tr(1, v); tr(2, w); tr(3, aA); tr(4, bB); }
     addsub(l, a, b, +1); addsub(l, l, c, -1); addsub(l, l, d, -1);
-    product(l, D, t, x);
+    product_top(l, D, t, x, top, 2);
     if (top) tr(5, t);
     addsub(z12, w, v, +1); addsub(z12, z12, t, +1);
     addsub(r, B, C, +1); addsub(r, r, A, -1); addsub(r, r, D, -1);
-    product(d, r, t, x);
+    product_top(d, r, t, x, top, 3);
     if (top) tr(6, t);
     addsub(z21, w, u, +1); addsub(z21, z21, t, +1);
     addsub(z22, w, u, +1); addsub(z22, z22, v, +1);
@@ -508,6 +524,21 @@ int orc_recursive(int alg, long m, long n, long k, double *A, long lda, double *
     }
     g_trace = NULL;
     return g_sched_error ? 2 : 0;
+}
+
+/* The top-level products in `mask` only (bit i = the (i+1)-th product of the level; Knuth's form
+ * in the BDPZ numbering): C receives their contributions to C, the other products taken as zero
+ * blocks (alg 0 Strassen, 1 Winograd BDPZ, 2 Knuth; PAD; depth >= 1).  Summing the results of
+ * masks that partition the seven products gives the product of orc_recursive, up to the order of
+ * the floating-point additions.  Returns 1 on bad arguments or depth 0. */
+int orc_recursive_products(int alg, long m, long n, long k, double *A, long lda, double *B, long ldb,
+                           double *C, long ldc, long cutoff, unsigned mask) {
+    if (alg < 0 || alg > 2 || (mask & ~0x7Fu) != 0) return 1;
+    if (orc_depth(m, n, k, cutoff < 1 ? 1 : cutoff) < 1) return 1;
+    g_top_mask = mask;
+    int rc = orc_recursive(alg, m, n, k, A, lda, B, ldb, C, ldc, cutoff, ORC_PAD, NULL);
+    g_top_mask = 0x7Fu;
+    return rc;
 }
 
 /* Run a caller-supplied 22-step table (same encoding as orc_schedule_table) with

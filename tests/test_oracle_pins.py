@@ -282,6 +282,50 @@ def test_planted_mistakes_in_table2_are_caught():
     assert not np.array_equal(run(tab), ex)
 
 
+# --------------------------------------------------------------------------- top-level product subsets
+# C's coefficient of each top-level product, read off the paper's combinations:
+# Strassen (Sec. 2.2) C11 = P1+P4-P5+P7, C12 = P3+P5, C21 = P2+P4, C22 = P1+P3-P2+P6;
+# BDPZ (Sec. 2.3) C11 = U1 = P1+P2, C12 = U5 = P1+P6+P5+P3, C21 = U6 = P1+P6+P7-P4,
+# C22 = U7 = P1+P6+P7+P5.  Rows: products P1..P7; columns: C11, C12, C21, C22.
+_COEF = {
+    oracle.STRASSEN: [[1, 0, 0, 1], [0, 0, 1, -1], [0, 1, 0, 1], [1, 0, 1, 0], [-1, 1, 0, 0], [0, 0, 0, 1],
+                      [1, 0, 0, 0]],
+    oracle.WINOGRAD: [[1, 1, 1, 1], [1, 0, 0, 0], [0, 1, 0, 0], [0, 0, -1, 0], [0, 1, 0, 1], [0, 1, 1, 1],
+                      [0, 0, 1, 1]],
+}
+
+
+def test_single_top_products_on_the_worked_2x2():
+    g = _golden()
+    A = np.array(g["A"], float).reshape(2, 2)
+    B = np.array(g["B"], float).reshape(2, 2)
+    for alg, key in ((oracle.STRASSEN, "strassen_P"), (oracle.WINOGRAD, "bdpz_P")):
+        for i, P in enumerate(g[key]):
+            C = oracle.recursive_products(alg, A, B, 1, 1 << i)
+            want = np.array(_COEF[alg][i], float).reshape(2, 2) * P
+            assert np.array_equal(C, want), (alg, i)
+
+
+@pytest.mark.parametrize("alg", [oracle.STRASSEN, oracle.WINOGRAD, oracle.KNUTH])
+@pytest.mark.parametrize("m,n,k,cutoff", [(16, 16, 16, 8), (16, 16, 16, 2), (13, 10, 7, 3), (24, 8, 40, 4)])
+def test_product_subsets_partition_the_product(alg, m, n, k, cutoff):
+    # masks that partition the seven top-level products add up to the exact product, and a union
+    # of disjoint masks is the sum of their results (integers: exact)
+    rng = np.random.default_rng(17)
+    A, B = _ints(rng, (m, k)), _ints(rng, (k, n))
+    ex = _exact_matmul_int(A, B)
+    assert np.array_equal(oracle.recursive_products(alg, A, B, cutoff, 0x7F), oracle.recursive(alg, A, B, cutoff))
+    assert not np.any(oracle.recursive_products(alg, A, B, cutoff, 0))
+    for parts in ([0x7F], [0x0F, 0x70], [0x03, 0x1C, 0x60], [1 << i for i in range(7)]):
+        tot = sum(oracle.recursive_products(alg, A, B, cutoff, msk) for msk in parts)
+        assert np.array_equal(tot, ex), (alg, parts)
+    a = oracle.recursive_products(alg, A, B, cutoff, 0x05)
+    b = oracle.recursive_products(alg, A, B, cutoff, 0x48)
+    assert np.array_equal(a + b, oracle.recursive_products(alg, A, B, cutoff, 0x4D))
+    with pytest.raises(ValueError):  # depth 0 has no top-level products
+        oracle.recursive_products(alg, A, B, 10 ** 6, 0x7F)
+
+
 # --------------------------------------------------------------------------- cutoff (Sec. 3.4)
 def test_cutoff_model_closed_form():
     # lhs <= rhs  <=>  mkn <= 4(mk + kn + mn); for m = n = k tight at n = 12
