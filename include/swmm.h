@@ -147,6 +147,20 @@ sw_status sw_smm(sw_handle h, const float *A, int lda, const float *B, int ldb, 
 sw_status sw_dmm(sw_handle h, const double *A, int lda, const double *B, int ldb, double *C, int ldc,
                  int m, int n, int k, int cutoff, uint32_t variant, void *stream);
 
+/* Part of a product for a split of the top recursion level over several GPUs.  The seven products
+ * of one Strassen or Strassen-Winograd level (Sec. 2.2 P1..P7; Sec. 2.3 P1..P7, Knuth's form in the
+ * same numbering) are independent: a rank computes some of them and the ranks' results are summed.
+ * This call overwrites C (device pointer, elem_bytes 4: FP32 as sw_smm, 8: FP64 as sw_dmm) with the
+ * contributions to A B of the top-level products whose bit is set in product_mask (bit i = product
+ * i + 1), everything below the top level computed as sw_smm / sw_dmm would; C blocks that none of
+ * them reaches are zero.  The results of masks that partition 0x7F add up to A B (exactly on
+ * small-integer inputs).  Needs SW_SCHED_FUSED, a Strassen or Winograd algorithm and a recursion
+ * depth of 1 to 3 (else SW_EUNSUPPORTED); cutoff <= 0 takes the static default (no tuning).
+ * Asynchronous on `stream`.  The summation across GPUs is the caller's (a reduction of C). */
+sw_status sw_mm_products(sw_handle h, int elem_bytes, const void *A, int lda, const void *B, int ldb, void *C,
+                         int ldc, int m, int n, int k, int cutoff, uint32_t variant, uint32_t product_mask,
+                         void *stream);
+
 /* FP32 product with HOST operands: copies A and B to the device, runs sw_smm and copies C back;
  * returns after the work has finished (synchronous).  Pinned host memory gives the fastest
  * copies.  Device buffers come from the handle's workspace.  Large products (n, k >= 1024, at

@@ -85,6 +85,15 @@ sw_status sw_dmm(sw_handle h, const double* A, int lda, const double* B, int ldb
     return do_mm(h, 8, A, lda, B, ldb, C, ldc, m, n, k, cutoff, variant, stream);
 }
 
+sw_status sw_mm_products(sw_handle h, int eb, const void* A, int lda, const void* B, int ldb, void* C, int ldc, int m,
+                         int n, int k, int cutoff, uint32_t variant, uint32_t product_mask, void* stream) {
+    if (!h) return SW_EINVAL;
+    if (eb != 4 && eb != 8) return fail(h, SW_EINVAL, "elem_bytes must be 4 or 8");
+    if ((product_mask & ~0x7Fu) != 0) return fail(h, SW_EINVAL, "product_mask has bits beyond the seven products");
+    if (cutoff <= 0) cutoff = eb == 4 ? 8192 : 128;  // the static default: no tuning for partial products
+    return do_mm(h, eb, A, lda, B, ldb, C, ldc, m, n, k, cutoff, variant, stream, product_mask);
+}
+
 sw_status sw_mm_batched(sw_handle h, int count, const sw_problem* probs, int cutoff, uint32_t variant, void* stream) {
     if (!h) return SW_EINVAL;
     if (count < 0 || (count > 0 && !probs)) return fail(h, SW_EINVAL, "bad problem list");

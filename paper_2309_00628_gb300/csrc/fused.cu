@@ -196,7 +196,9 @@ bool Planner::fused(View A, View B, View C, int L) {
     std::vector<short> slot_a(nleaf, -1), slot_b(nleaf, -1);
     std::vector<int> ar(nleaf), ac(nleaf), br(nleaf), bc(nleaf);
     int na = 0, nbs = 0;
+    auto in_mask = [&](int w) { return ((top_mask >> (w / (nleaf / 7))) & 1u) != 0; };
     for (int w = 0; w < nleaf; ++w) {
+        if (!in_mask(w)) continue;  // a left-out top-level product: no operand slots, no leaf
         bool pa = true, pb = true;
         int r_a = 0, c_a = 0, r_b = 0, c_b = 0;
         for (int l = 0, div = nleaf / 7; l < L; ++l, div /= 7) {
@@ -284,7 +286,7 @@ bool Planner::fused(View A, View B, View C, int L) {
     // path, where the first writer's tiles lead their position group and the waits are short;
     // deeper levels (many leaves queue behind one writer) and the SIMT FP64 leaf keep a zeroed
     // C and reduce-adds only.
-    const bool ordered = eb == 4 && L == 1 && !batch && !server;
+    const bool ordered = eb == 4 && L == 1 && !batch && !server && top_mask == 0x7Fu;
     if (!ordered) memset0(C);
     const int bn_o = eb == 8                ? F64_BN
                      : force_bn             ? force_bn
@@ -299,6 +301,7 @@ bool Planner::fused(View A, View B, View C, int L) {
     const int tm_sz = eb == 4 ? tf32_tile_m() : F64_BM;
     const int bn = bn_o;
     for (int w = 0; w < nleaf; ++w) {
+        if (!in_mask(w)) continue;
         Leaf lf;
         memset(&lf, 0, sizeof(lf));
         lf.tag = -1;

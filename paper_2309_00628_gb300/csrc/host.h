@@ -153,7 +153,7 @@ sw_status ensure_ws(sw_handle h, size_t need);
 // Build the whole plan for one product (planner.cu); server: plan inside a region of the serving arena
 sw_status build_plan(sw_handle h, int eb, const void* A, int lda, const void* B, int ldb, void* C, int ldc, int m,
                      int n, int k, int cutoff, uint32_t variant, bool dry, Plan* plan, char* ws_base = nullptr,
-                     bool server = false);
+                     bool server = false, uint32_t top_mask = 0x7Fu);
 // Plan of a batch of FP32 products in one grouped launch (planner.cu)
 sw_status build_batched_plan(sw_handle h, int count, const sw_problem* probs, int cutoff, uint32_t variant, bool dry,
                              Plan* plan, int bn = 256, bool pair = false);
@@ -171,9 +171,10 @@ sw_status time_plan(sw_handle h, Plan* plan, cudaStream_t s, double* ms);
 sw_status tune(sw_handle h, const std::string& key, const std::vector<PlanBuilder>& cands, cudaStream_t s, int* best,
                double* best_ms);
 bool capturing(cudaStream_t s);
-// One product through the plan cache (and the autotuner for cutoff <= 0): sw_smm / sw_dmm.
+// One product through the plan cache (and the autotuner for cutoff <= 0): sw_smm / sw_dmm; with
+// top_mask != 0x7F only the contributions of those top-level products (sw_mm_products, no tuning).
 sw_status do_mm(sw_handle h, int eb, const void* A, int lda, const void* B, int ldb, void* C, int ldc, int m, int n,
-                int k, int cutoff, uint32_t variant, void* stream);
+                int k, int cutoff, uint32_t variant, void* stream, uint32_t top_mask = 0x7Fu);
 // A validated batch of products: sw_mm_batched.
 sw_status do_batched(sw_handle h, int count, const sw_problem* probs, int cutoff, uint32_t variant, void* stream);
 // Host-operand product in row panels (sw_smm_host).

@@ -409,7 +409,7 @@ int resolve_depth(int m, int n, int k, int cutoff, uint32_t variant, int eb) {
 // the BN = 256 form the resident loop runs, without ordering counters.
 sw_status build_plan(sw_handle h, int eb, const void* A, int lda, const void* B, int ldb, void* C, int ldc,
                             int m, int n, int k, int cutoff, uint32_t variant, bool dry, Plan* plan,
-                            char* ws_base, bool server) {
+                            char* ws_base, bool server, uint32_t top_mask) {
     const uint32_t algo = variant & SW_ALGO_MASK, sched = variant & SW_SCHED_MASK, odd = variant & SW_ODD_MASK;
     if (algo > SW_ALGO_WINOGRAD_KNUTH) return fail(h, SW_EINVAL, "unknown algorithm bits");
     if (sched > SW_SCHED_ALLOC) return fail(h, SW_EINVAL, "unknown schedule bits");
@@ -446,9 +446,12 @@ sw_status build_plan(sw_handle h, int eb, const void* A, int lda, const void* B,
     P.algo = (int)algo;
     P.server = server;
     P.sms = h->sms;
+    P.top_mask = top_mask;
     if (server && eb == 4 && !bf) P.force_bn = 256;
     const int L = resolve_depth(m, n, k, cutoff, variant, eb);
     plan->depth = L;
+    if (top_mask != 0x7Fu && (sched != SW_SCHED_FUSED || algo == SW_ALGO_NAIVE || L < 1 || L > 3))
+        return fail(h, SW_EUNSUPPORTED, "product subsets need a FUSED recursion of depth 1 to 3");
 
     View Av = {(char*)A, lda, m, k}, Bv = {(char*)B, ldb, k, n}, Cv = {(char*)C, ldc, m, n};
     // TF32 leaves read A and write C through TMA (16-byte rows); the SIMT FP64 leaf and the split
@@ -480,6 +483,8 @@ sw_status build_plan(sw_handle h, int eb, const void* A, int lda, const void* B,
         if (!a_ok) { a2 = P.talloc(m, k); P.copy_pad(a2, Av); }
         if (!c_ok) c2 = P.talloc(m, n);
         View b2 = stage_b(Bv, k, n);
+        if (top_mask != 0x7Fu && (L == 0 || algo == SW_ALGO_NAIVE || L > 3 || sched != SW_SCHED_FUSED))
+            return fail(h, SW_EUNSUPPORTED, "product subsets need a FUSED recursion of depth 1 to 3");
         if (L == 0 || algo == SW_ALGO_NAIVE) ok = P.gemm(a2, b2, c2, TGT_STORE);
         else if (L <= 3) ok = P.fused(a2, b2, c2, L);
         else {  // FP64 deeper than three levels: Table 2 (BDPZ) or Alg. 2 (Strassen) steps on top

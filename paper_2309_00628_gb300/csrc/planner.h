@@ -35,6 +35,10 @@ struct Planner {
     Plan* plan;
     std::string err;
     int sched, algo;
+    // Products of the top recursion level that take part (bit i: product i + 1 of Sec. 2.2 / 2.3,
+    // Knuth's form in the BDPZ numbering); the others are left out and C holds the contributions of
+    // the rest (FUSED only).  0x7F: the whole product.
+    uint32_t top_mask = 0x7Fu;
 
     // Batch mode: products append their leaves, targets and operand maps to one grouped launch
     // instead of emitting their own (operand maps then live in global memory).

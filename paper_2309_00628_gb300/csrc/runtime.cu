@@ -294,7 +294,7 @@ bool capturing(cudaStream_t s) {
 }
 
 sw_status do_mm(sw_handle h, int eb, const void* A, int lda, const void* B, int ldb, void* C, int ldc, int m,
-                       int n, int k, int cutoff, uint32_t variant, void* stream) {
+                       int n, int k, int cutoff, uint32_t variant, void* stream, uint32_t top_mask) {
     if (!h) return SW_EINVAL;
     if (m < 0 || n < 0 || k < 0) return fail(h, SW_EINVAL, "negative dimension");
     if ((m && k && !A) || (k && n && !B) || (m && n && !C)) return fail(h, SW_EINVAL, "null matrix pointer");
@@ -305,19 +305,20 @@ sw_status do_mm(sw_handle h, int eb, const void* A, int lda, const void* B, int 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     auto builder = [=](int c) {
         return PlanBuilder([=](bool dry, Plan* p) {
-            return build_plan(h, eb, A, lda, B, ldb, C, ldc, m, n, k, c, variant, dry, p);
+            return build_plan(h, eb, A, lda, B, ldb, C, ldc, m, n, k, c, variant, dry, p, nullptr, false, top_mask);
         });
     };
     auto key_of = [&](int c) {
         char key[256];
-        snprintf(key, sizeof(key), "%d|%p|%d|%p|%d|%p|%d|%d|%d|%d|%d|%u", eb, A, lda, B, ldb, C, ldc, m, n, k, c,
-                 variant);
+        snprintf(key, sizeof(key), "%d|%p|%d|%p|%d|%p|%d|%d|%d|%d|%d|%u|%x", eb, A, lda, B, ldb, C, ldc, m, n, k, c,
+                 variant, top_mask);
         return std::string(key);
     };
     // cutoff <= 0: the autotuner picks the depth on the first call for this shape and variant (not
     // under stream capture, and not for IN_PLACE, whose runs overwrite A and B)
     const uint32_t algo = variant & SW_ALGO_MASK, sched = variant & SW_SCHED_MASK;
-    if (cutoff <= 0 && algo != SW_ALGO_NAIVE && sched != SW_SCHED_IN_PLACE && !capturing(s) && m && n && k) {
+    if (cutoff <= 0 && algo != SW_ALGO_NAIVE && sched != SW_SCHED_IN_PLACE && top_mask == 0x7Fu && !capturing(s) && m &&
+        n && k) {
         char sig[160];
         const int align = (int)((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B) |
                                  reinterpret_cast<uintptr_t>(C)) & 15) | (((lda | ldb | ldc) & 3) << 4);

@@ -89,9 +89,11 @@ def load(build_if_missing: bool = False):
     lib.sw_server_wait.argtypes = [_V, ctypes.c_uint64, ctypes.c_int64]
     lib.sw_server_stop.argtypes = [_V]
     lib.sw_selftest_expired_wait.argtypes = [_V, _V]
+    lib.sw_mm_products.argtypes = [_V, _I, _V, _I, _V, _I, _V, _I, _I, _I, _I, _I, _U, _U, _V]
     for name in ("sw_create", "sw_destroy", "sw_mm_workspace_size", "sw_mm_depth", "sw_smm", "sw_dmm",
                  "sw_smm_host", "sw_sync", "sw_error_norms", "sw_profile", "sw_profile_read", "sw_server_start",
-                 "sw_server_submit", "sw_server_wait", "sw_server_stop", "sw_selftest_expired_wait"):
+                 "sw_server_submit", "sw_server_wait", "sw_server_stop", "sw_selftest_expired_wait",
+                 "sw_mm_products"):
         getattr(lib, name).restype = _I
     _lib = lib
     return lib
@@ -133,6 +135,10 @@ def sw_smm(h, A, lda, B, ldb, C, ldc, m, n, k, cutoff, variant, stream=None) -> 
 
 def sw_dmm(h, A, lda, B, ldb, C, ldc, m, n, k, cutoff, variant, stream=None) -> int:
     return load().sw_dmm(h, A, lda, B, ldb, C, ldc, m, n, k, cutoff, variant, stream)
+
+
+def sw_mm_products(h, elem_bytes, A, lda, B, ldb, C, ldc, m, n, k, cutoff, variant, product_mask, stream=None) -> int:
+    return load().sw_mm_products(h, elem_bytes, A, lda, B, ldb, C, ldc, m, n, k, cutoff, variant, product_mask, stream)
 
 
 def sw_smm_host(h, A, lda, B, ldb, C, ldc, m, n, k, cutoff, variant, stream=None) -> int:
