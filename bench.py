@@ -166,6 +166,24 @@ def leaf_flops(n: int, L: int) -> float:
     return 2.0 * (n >> L) ** 3 * 7 ** L
 
 
+SIZE_CLASSES = ("order <= 1024", "order 2048", "order >= 4096")
+
+
+def size_class(m: int, n: int, k: int) -> str:
+    """Serving size class of a request by the geometric mean of its dimensions."""
+    g = (float(m) * n * k) ** (1.0 / 3.0)
+    return SIZE_CLASSES[0] if g <= 1448 else SIZE_CLASSES[1] if g <= 2896 else SIZE_CLASSES[2]
+
+
+def latency_summary(lat):
+    """Count, p50 and p99 (ms) of a list of latencies in seconds (None fields when empty)."""
+    if not lat:
+        return {"requests": 0, "p50_ms": None, "p99_ms": None}
+    ls = sorted(lat)
+    return {"requests": len(ls), "p50_ms": 1e3 * statistics.median(ls),
+            "p99_ms": 1e3 * ls[min(len(ls) - 1, int(math.ceil(0.99 * len(ls))) - 1)]}
+
+
 def serving_bench(h, swmm, torch, rates, count, share, seed=3):
     """Poisson arrivals of the FP32 / FP64 serving mix through sw_server_*; per rate: achieved
     throughput, p50 / p99 latency (submit to completion, host clock), Freivalds error; once: the
@@ -238,7 +256,12 @@ def serving_bench(h, swmm, torch, rates, count, share, seed=3):
             rows.append({"rate_per_s": rate, "requests": count, "achieved_req_per_s": count / span,
                          "eff_tflops": flops / span / 1e12, "p50_ms": 1e3 * statistics.median(ls),
                          "p99_ms": 1e3 * ls[min(count - 1, int(math.ceil(0.99 * count)) - 1)],
-                         "max_ms": 1e3 * ls[-1]})
+                         "max_ms": 1e3 * ls[-1],
+                         "by_dtype": {name: latency_summary([lat[i] for i, r in enumerate(reqs) if r[3] == eb])
+                                      for name, eb in (("fp32", 4), ("fp64", 8))},
+                         "by_size": {name: latency_summary([lat[i] for i, r in enumerate(reqs)
+                                                            if size_class(*r[:3]) == name])
+                                     for name in SIZE_CLASSES}})
         # accuracy of the last rate's results: Freivalds with random signs, normalised like the
         # element-wise metric; then each request alone (sw_smm / sw_dmm) against its served result
         gx = torch.Generator(device="cuda")
@@ -569,6 +592,32 @@ def main():
             tot, _, _, _ = timed(v, c, ks, W)
             depth_rows.append({"variant": lab, "ms": tot / ks, "eff_tflops": flop / (tot / ks / 1e3) / 1e12,
                                "err": row_err(v, c)})
+        # the same sweep at n = 4096 (config 2's smaller size): its own seeded inputs and oracle rows
+        n5 = n // 2
+        A5, B5 = inputs.pair(n5, n5, n5, "uniform", seed=0, dtype=np.float32)
+        dA5, dB5 = torch.from_numpy(A5).cuda(), torch.from_numpy(B5).cuda()
+        dC5 = torch.empty((n5, n5), dtype=torch.float32, device="cuda")
+        sel5 = np.sort(np.random.Generator(np.random.PCG64(10)).choice(n5, 16, replace=False))
+        R5 = oracle.naive_mt(A5[sel5].astype(np.float64), B5.astype(np.float64), oracle.max_threads())
+        scale5 = n5 * float(np.max(np.abs(A5))) * float(np.max(np.abs(B5)))
+        idx5 = torch.from_numpy(sel5).cuda()
+        depth_rows5 = []
+        for lab, v, c in [("plain L0", swmm.SW_ALGO_NAIVE, 0)] + [
+                (f"winograd L{l}", swmm.SW_ALGO_WINOGRAD | swmm.SW_SCHED_FUSED, n5 >> l) for l in (1, 2, 3)]:
+            run5 = lambda: swmm.check(h, swmm.sw_smm(h, p(dA5), n5, p(dB5), n5, p(dC5), n5, n5, n5, n5, c, v, sp))
+            for _ in range(W):
+                run5()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(ks):
+                run5()
+            e1.record(stream)
+            swmm.check(h, swmm.sw_sync(h, sp))
+            ms5 = e0.elapsed_time(e1) / ks
+            err5 = float(np.max(np.abs(dC5[idx5].double().cpu().numpy() - R5)) / scale5)
+            depth_rows5.append({"variant": lab, "ms": ms5, "eff_tflops": 2.0 * n5 ** 3 / (ms5 / 1e3) / 1e12,
+                                "err": err5})
+        del dA5, dB5, dC5
         bf_rows = []
         X3 = swmm.SW_LEAF_TF32X3
         for lab, v, c in (("plain L0", swmm.SW_ALGO_NAIVE | BF, 0),
@@ -697,7 +746,8 @@ def main():
         tuned = {"cutoff": tune["cutoff"], "depth": swmm.sw_mm_depth(n, n, n, tune["cutoff"], variant, 4)[1],
                  "candidates": tune["candidates"], "ms": tot / ks, "eff_tflops": flop / (tot / ks / 1e3) / 1e12}
         extra = {"autotuned_winograd_n8192": tuned,
-                 "depth_sweep_n8192_tf32": depth_rows, "fp32_accuracy_leaves_n8192": bf_rows,
+                 "depth_sweep_n8192_tf32": depth_rows, "depth_sweep_n4096_tf32": depth_rows5,
+                 "fp32_accuracy_leaves_n8192": bf_rows,
                  "n16384_tf32": big,
                  "fp32_accuracy_n16384_normal_bf16x3": cfg3,
                  "workspace_bytes_n16384_L2_bf16x3": ws,

@@ -54,3 +54,13 @@ def test_both_arms_share_the_workload_config():
     c = bench.workload_config(args, 1)
     assert c["n"] == 8192 and c["depth"] == 1 and c["algo"] == "winograd" and c["schedule"] == "fused"
     assert "n=8192" in c["workload"] and "L=1" in c["workload"]
+
+
+def test_serving_latency_summaries():
+    import bench
+    assert bench.size_class(512, 512, 512) == bench.SIZE_CLASSES[0]
+    assert bench.size_class(2048, 2048, 2048) == bench.SIZE_CLASSES[1]
+    assert bench.size_class(8192, 1024, 8192) == bench.SIZE_CLASSES[2]
+    s = bench.latency_summary([0.004, 0.001, 0.002, 0.003])
+    assert s["requests"] == 4 and s["p50_ms"] == 2.5 and s["p99_ms"] == 4.0
+    assert bench.latency_summary([])["p50_ms"] is None
