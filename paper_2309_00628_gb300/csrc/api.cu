@@ -131,25 +131,6 @@ sw_status sw_smm_host(sw_handle h, const float* A, int lda, const float* B, int 
         return fail(h, SW_EINVAL, "bad host operand");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const long long lda2 = round_up(std::max(k, 1), 4), ldb2 = round_up(std::max(n, 1), 4), ldc2 = ldb2;
-    const size_t ba = (size_t)round_up((long long)m * lda2 * 4, 256), bb = (size_t)round_up((long long)k * ldb2 * 4, 256),
-                 bc = (size_t)round_up((long long)m * ldc2 * 4, 256);
-    {
-        std::lock_guard<std::mutex> lock(h->mu);
-        cudaSetDevice(h->device);
-        if (ba + bb + bc > h->io_bytes) {
-            flush_plans(h);
-            if (h->io) { cudaDeviceSynchronize(); cudaFree(h->io); h->io = nullptr; h->io_bytes = 0; }
-            if (cudaMalloc(&h->io, ba + bb + bc) != cudaSuccess) {
-                cudaGetLastError();
-                return fail(h, SW_ENOMEM, "host-path buffers");
-            }
-            h->io_bytes = ba + bb + bc;
-        }
-    }
-    float* dA = reinterpret_cast<float*>(h->io);
-    float* dB = reinterpret_cast<float*>(h->io + ba);
-    float* dC = reinterpret_cast<float*>(h->io + ba + bb);
-    cudaError_t e = cudaSuccess;
     // large FUSED / naive products with a given cutoff: A and C move in row panels so the copies
     // overlap the panel products and each other (the link is duplex)
     const uint32_t algo = variant & SW_ALGO_MASK, sched = variant & SW_SCHED_MASK;
@@ -157,10 +138,36 @@ sw_status sw_smm_host(sw_handle h, const float* A, int lda, const float* B, int 
     const long long unit = 256LL << L;  // panel height granularity: whole 256-row tiles per block
     const int P = 4;
     const long long mp = round_up(ceil_div(m, P), unit);
-    if ((cutoff > 0 || algo == SW_ALGO_NAIVE) && (algo == SW_ALGO_NAIVE || sched == SW_SCHED_FUSED) &&
-        n >= 1024 && k >= 1024 && m >= 2 * mp && (long long)m * n + (long long)k * n + (long long)m * k >= (16LL << 20))
+    const bool panels = (cutoff > 0 || algo == SW_ALGO_NAIVE) && (algo == SW_ALGO_NAIVE || sched == SW_SCHED_FUSED) &&
+                        n >= 1024 && k >= 1024 && m >= 2 * mp &&
+                        (long long)m * n + (long long)k * n + (long long)m * k >= (16LL << 20);
+    // the panels share one pass of B's operand sums (FUSED, TF32 leaves read N-major)
+    const bool share_b = panels && algo != SW_ALGO_NAIVE && L >= 1 && L <= 3 &&
+                         (variant & SW_LEAF_MASK) == SW_LEAF_TF32 && !tf32_bt_form();
+    const size_t ba = (size_t)round_up((long long)m * lda2 * 4, 256), bb = (size_t)round_up((long long)k * ldb2 * 4, 256),
+                 bc = (size_t)round_up((long long)m * ldc2 * 4, 256),
+                 bs = share_b ? (size_t)round_up(fused_b_sum_elems((int)algo, k, n, L) * 4, 256) : 0;
+    {
+        std::lock_guard<std::mutex> lock(h->mu);
+        cudaSetDevice(h->device);
+        if (ba + bb + bc + bs > h->io_bytes) {
+            flush_plans(h);
+            if (h->io) { cudaDeviceSynchronize(); cudaFree(h->io); h->io = nullptr; h->io_bytes = 0; }
+            if (cudaMalloc(&h->io, ba + bb + bc + bs) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(h, SW_ENOMEM, "host-path buffers");
+            }
+            h->io_bytes = ba + bb + bc + bs;
+        }
+    }
+    float* dA = reinterpret_cast<float*>(h->io);
+    float* dB = reinterpret_cast<float*>(h->io + ba);
+    float* dC = reinterpret_cast<float*>(h->io + ba + bb);
+    char* dS = share_b ? h->io + ba + bb + bc : nullptr;
+    cudaError_t e = cudaSuccess;
+    if (panels)
         return host_panels(h, A, lda, B, ldb, C, ldc, m, n, k, cutoff, variant, L, (int)mp, dA, lda2, dB, ldb2, dC,
-                           ldc2, s);
+                           ldc2, dS, s);
     if (m && k) e = cudaMemcpy2DAsync(dA, lda2 * 4, A, (size_t)lda * 4, (size_t)k * 4, m, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && k && n)
         e = cudaMemcpy2DAsync(dB, ldb2 * 4, B, (size_t)ldb * 4, (size_t)n * 4, k, cudaMemcpyHostToDevice, s);

@@ -226,8 +226,11 @@ bool Planner::fused(View A, View B, View C, int L) {
     View SA = split_sums ? View{nullptr, kb, na * mb, kb} : talloc(std::max(na, 1) * mb, kb);
     SA.rows = na * mb;
     SA.ld = kb;
+    const bool share_b = b_sums_mode != 0 && eb == 4 && !bf && !x3 && !bt;
     View SB = split_sums ? View{nullptr, nb, nbs * kb, nb}
-                         : bt ? talloc(std::max(nbs, 1) * nb, kb) : talloc(std::max(nbs, 1) * kb, nb);
+              : share_b  ? View{b_sums, nb, nbs * kb, nb}
+              : bt       ? talloc(std::max(nbs, 1) * nb, kb)
+                         : talloc(std::max(nbs, 1) * kb, nb);
     SB.rows = bt ? nbs * nb : nbs * kb;
     SB.ld = bt ? kb : nb;
     // split-BF16 leaves: (hi, lo) halves of A, B and the S / T sums (sized in the dry run too)
@@ -273,6 +276,11 @@ bool Planner::fused(View A, View B, View C, int L) {
         pa.pre_b = pb.pre;
         pa.sout_b = pb.sout;
         push(pa);
+    } else if (share_b && b_sums_mode == 1) {  // only the shared B-side sums
+        if (nbs > 0) push(pb);
+        return true;
+    } else if (share_b) {                       // B-side sums already in b_sums
+        if (na > 0) push(pa);
     } else if (na > 0 && nbs > 0 && eb == 4) {
         pa.pre_b = pb.pre;
         pa.pre_two = true;
@@ -530,6 +538,25 @@ bool Planner::batched(const sw_problem* probs, int count, const std::vector<int>
     batch = false;  // the combined op itself is emitted normally
     emit_grouped(o, bleaves, btargets, 0);
     return true;
+}
+
+// Elements of the B-side operand sums of a FUSED FP32 product with TF32 leaves at depth L (the
+// slot stack fused() writes: one (k/2^L rounded to the k-block) x (n/2^L rounded to 4) slot per
+// leaf whose B operand is a sum).
+long long fused_b_sum_elems(int algo, int k, int n, int L) {
+    const Planner::ProdTab& T = Planner::table(algo);
+    const long long s = 1LL << L;
+    const long long kb = round_up(ceil_div(k, s), tf32_tile_k()), nb = round_up(ceil_div(n, s), 4);
+    int nleaf = 1;
+    for (int i = 0; i < L; ++i) nleaf *= 7;
+    long long nbs = 0;
+    for (int w = 0; w < nleaf; ++w) {
+        bool pure = true;
+        for (int l = 0, div = nleaf / 7; l < L; ++l, div /= 7)
+            if (T.pure_b_q[(w / div) % 7] < 0) pure = false;
+        if (!pure) ++nbs;
+    }
+    return nbs * kb * nb;
 }
 
 }  // namespace swh

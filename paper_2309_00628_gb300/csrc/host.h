@@ -25,6 +25,9 @@
 #include <unordered_map>
 #include <vector>
 
+#include <set>
+#include <tuple>
+
 #include "../../include/swmm.h"
 #include "internal.h"
 #include "plan.h"
@@ -54,7 +57,7 @@ int bn_override();
 // ------------------------------------------------------------------ plan
 enum OpKind {
     OP_GEMM_TF32, OP_GEMM_SIMT, OP_ADDSUB, OP_COPY_PAD, OP_PREADD, OP_MEMSET, OP_TRANSPOSE, OP_TRANSPOSE_SQ,
-    OP_SPLIT, OP_GEMM_BF16X3, OP_BATCH_COPY, OP_SPLIT_TF32, OP_GEMM_TF32X3, OP_PREADD_SPLIT
+    OP_SPLIT, OP_GEMM_BF16X3, OP_BATCH_COPY, OP_SPLIT_TF32, OP_GEMM_TF32X3, OP_PREADD_SPLIT, OP_ADDSUB2
 };
 
 struct Op {
@@ -85,6 +88,7 @@ struct Op {
     bool wtile = false;     // OP_GEMM_SIMT (FP64): one Winograd step inside every 64 x 64 tile
     PreaddSplitOut sout;    // OP_PREADD_SPLIT: bf16 halves of A and of its sums (sout_b: of B)
     PreaddSplitOut sout_b;
+    AddJob job_a, job_b;    // OP_ADDSUB2: two block additions in one launch
 };
 
 struct Plan {
@@ -102,6 +106,8 @@ struct Plan {
     }
 };
 
+// Elements of the B-side operand sums of a FUSED FP32 product with TF32 leaves at depth L (fused.cu).
+long long fused_b_sum_elems(int algo, int k, int n, int L);
 // Recursion depth of a product (the Sec. 3.4 cutoff rule, capped for the FUSED schedule).
 int resolve_depth(int m, int n, int k, int cutoff, uint32_t variant, int eb);
 
@@ -153,7 +159,8 @@ sw_status ensure_ws(sw_handle h, size_t need);
 // Build the whole plan for one product (planner.cu); server: plan inside a region of the serving arena
 sw_status build_plan(sw_handle h, int eb, const void* A, int lda, const void* B, int ldb, void* C, int ldc, int m,
                      int n, int k, int cutoff, uint32_t variant, bool dry, Plan* plan, char* ws_base = nullptr,
-                     bool server = false, uint32_t top_mask = 0x7Fu);
+                     bool server = false, uint32_t top_mask = 0x7Fu, int b_sums_mode = 0,
+                     char* b_sums = nullptr);
 // Plan of a batch of FP32 products in one grouped launch (planner.cu)
 sw_status build_batched_plan(sw_handle h, int count, const sw_problem* probs, int cutoff, uint32_t variant, bool dry,
                              Plan* plan, int bn = 256, bool pair = false);
@@ -174,12 +181,14 @@ bool capturing(cudaStream_t s);
 // One product through the plan cache (and the autotuner for cutoff <= 0): sw_smm / sw_dmm; with
 // top_mask != 0x7F only the contributions of those top-level products (sw_mm_products, no tuning).
 sw_status do_mm(sw_handle h, int eb, const void* A, int lda, const void* B, int ldb, void* C, int ldc, int m, int n,
-                int k, int cutoff, uint32_t variant, void* stream, uint32_t top_mask = 0x7Fu);
+                int k, int cutoff, uint32_t variant, void* stream, uint32_t top_mask = 0x7Fu, int b_sums_mode = 0,
+                char* b_sums = nullptr);
 // A validated batch of products: sw_mm_batched.
 sw_status do_batched(sw_handle h, int count, const sw_problem* probs, int cutoff, uint32_t variant, void* stream);
-// Host-operand product in row panels (sw_smm_host).
+// Host-operand product in row panels (sw_smm_host); dS: room for B's operand sums, computed once
+// and shared by the panels (nullptr: each panel computes its own).
 sw_status host_panels(sw_handle h, const float* A, int lda, const float* B, int ldb, float* C, int ldc, int m, int n,
                       int k, int cutoff, uint32_t variant, int L, int mp, float* dA, long long lda2, float* dB,
-                      long long ldb2, float* dC, long long ldc2, cudaStream_t s);
+                      long long ldb2, float* dC, long long ldc2, char* dS, cudaStream_t s);
 
 }  // namespace swh

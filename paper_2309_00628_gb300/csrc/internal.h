@@ -106,6 +106,19 @@ cudaError_t launch_transpose_inplace(int n, float* x, long long ld, cudaStream_t
 cudaError_t launch_addsub(int elem_bytes, int rows, int cols, void* z, long long ldz, const void* x, long long ldx,
                           const void* y, long long ldy, float sy, cudaStream_t stream);
 
+// Two independent elementwise jobs z = x + sy * y (FP32 or FP64 per elem_bytes) in one launch.
+struct AddJob {
+    int rows, cols;
+    void* z;
+    long long ldz;
+    const void* x;
+    long long ldx;
+    const void* y;
+    long long ldy;
+    float sy;
+};
+cudaError_t launch_addsub2(int elem_bytes, const AddJob& a, const AddJob& b, cudaStream_t stream);
+
 // Z = X (strided 2-D copy with zero fill outside the source extent).
 cudaError_t launch_copy_pad(int elem_bytes, int rows, int cols, void* z, long long ldz, const void* x,
                             long long ldx, int src_rows, int src_cols, cudaStream_t stream);

@@ -73,6 +73,70 @@ cudaError_t launch_addsub(int elem_bytes, int rows, int cols, void* z, long long
     return cudaGetLastError();
 }
 
+// Two independent elementwise jobs z = x + sy * y in one launch: blocks [0, grid_a) take job a.
+template <typename T>
+__device__ __forceinline__ void addsub_job(const AddJob& j, int block, int nblocks) {
+    const long long total = (long long)j.rows * j.cols;
+    T* z = static_cast<T*>(j.z);
+    const T* x = static_cast<const T*>(j.x);
+    const T* y = static_cast<const T*>(j.y);
+    const T sy = (T)j.sy;
+    for (long long e = block * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)nblocks * blockDim.x) {
+        const int i = (int)(e / j.cols), c = (int)(e - (long long)i * j.cols);
+        z[i * j.ldz + c] = x[i * j.ldx + c] + sy * y[i * j.ldy + c];
+    }
+}
+
+__device__ __forceinline__ void addsub4_job(const AddJob& j, int block, int nblocks) {
+    const int c4 = j.cols / 4;
+    const long long total = (long long)j.rows * c4;
+    float4* z = static_cast<float4*>(j.z);
+    const float4* x = static_cast<const float4*>(j.x);
+    const float4* y = static_cast<const float4*>(j.y);
+    const long long ldz = j.ldz / 4, ldx = j.ldx / 4, ldy = j.ldy / 4;
+    for (long long e = block * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)nblocks * blockDim.x) {
+        const int i = (int)(e / c4), c = (int)(e - (long long)i * c4);
+        const float4 a = x[i * ldx + c], b = y[i * ldy + c];
+        z[i * ldz + c] = make_float4(a.x + j.sy * b.x, a.y + j.sy * b.y, a.z + j.sy * b.z, a.w + j.sy * b.w);
+    }
+}
+
+template <typename T, bool V4>
+__global__ void __launch_bounds__(256) addsub2_kernel(const AddJob a, const AddJob b, int grid_a) {
+    const bool first = (int)blockIdx.x < grid_a;
+    const int blk = first ? (int)blockIdx.x : (int)blockIdx.x - grid_a;
+    const int nb = first ? grid_a : (int)gridDim.x - grid_a;
+    if (V4) addsub4_job(first ? a : b, blk, nb);
+    else addsub_job<T>(first ? a : b, blk, nb);
+}
+
+cudaError_t launch_addsub2(int elem_bytes, const AddJob& a, const AddJob& b, cudaStream_t stream) {
+    const long long wa = (long long)std::max(a.rows, 0) * std::max(a.cols, 0);
+    const long long wb = (long long)std::max(b.rows, 0) * std::max(b.cols, 0);
+    if (wa == 0 || wb == 0) {  // one job alone
+        const AddJob& j = wa ? a : b;
+        return launch_addsub(elem_bytes, j.rows, j.cols, j.z, j.ldz, j.x, j.ldx, j.y, j.ldy, j.sy, stream);
+    }
+    auto v4 = [](const AddJob& j) {
+        return ((j.cols | j.ldz | j.ldx | j.ldy) & 3) == 0 &&
+               ((reinterpret_cast<uintptr_t>(j.z) | reinterpret_cast<uintptr_t>(j.x) |
+                 reinterpret_cast<uintptr_t>(j.y)) & 15) == 0;
+    };
+    const bool vec = elem_bytes == 4 && v4(a) && v4(b);
+    const int per = vec ? 4 : 1;
+    const int g = grid_for((wa + wb) / per, 256);
+    const int ga = std::max(1, std::min(g - 1, (int)((g * wa + (wa + wb) / 2) / (wa + wb))));
+    if (g < 2) {
+        cudaError_t e = launch_addsub(elem_bytes, a.rows, a.cols, a.z, a.ldz, a.x, a.ldx, a.y, a.ldy, a.sy, stream);
+        return e != cudaSuccess ? e : launch_addsub(elem_bytes, b.rows, b.cols, b.z, b.ldz, b.x, b.ldx, b.y, b.ldy,
+                                                    b.sy, stream);
+    }
+    if (elem_bytes == 8) addsub2_kernel<double, false><<<g, 256, 0, stream>>>(a, b, ga);
+    else if (vec) addsub2_kernel<float, true><<<g, 256, 0, stream>>>(a, b, ga);
+    else addsub2_kernel<float, false><<<g, 256, 0, stream>>>(a, b, ga);
+    return cudaGetLastError();
+}
+
 template <typename T>
 __global__ void copy_pad_kernel(int rows, int cols, T* __restrict__ z, long long ldz, const T* __restrict__ x,
                                 long long ldx, int src_rows, int src_cols) {

@@ -86,36 +86,47 @@ int bn_override() {
 }
 
 // One leaf product c (=|+=) a b on the tensor cores (FP32: b as stored, or as B^T in bt
-// storage) or, for FP64,
-// on the SIMT kernel.
-bool Planner::gemm(View a, View b, View c, int mode) {
-    if (c.rows <= 0 || c.cols <= 0) return true;
+// storage) or, for FP64, on the SIMT kernel.
+bool Planner::gemm(View a, View b, View c, int mode) { return leaf_to(a, b, {Dest{c, 1.f, mode}}); }
+bool Planner::gemm_split(View a, View b, View c, int mode) { return gemm_split_to(a, b, {Dest{c, 1.f, mode}}); }
+bool Planner::simt(View a, View b, View c, int mode) { return simt_to(a, b, {Dest{c, 1.f, mode}}); }
+
+bool Planner::leaf_to(View a, View b, std::vector<Dest> d) {
+    // a block's first write stores, later ones add (the plan's launches run in order)
+    for (Dest& x : d)
+        if (x.mode < 0) x.mode = written.insert(std::make_tuple(x.c.p, x.c.rows, x.c.cols)).second ? TGT_STORE : TGT_ADD;
+    if (eb == 8) return simt_to(a, b, d);
+    if (bf || x3) return gemm_split_to(a, b, d);
+    return gemm_to(a, b, d);
+}
+
+// TF32 leaf on the tensor cores, one launch, the product added into every destination.
+bool Planner::gemm_to(View a, View b, const std::vector<Dest>& d) {
+    const int rows = d[0].c.rows, cols = d[0].c.cols;
+    if (rows <= 0 || cols <= 0) return true;
     if (a.cols == 0) {
-        if (mode == TGT_STORE) memset0(c);
+        for (const Dest& x : d)
+            if (x.mode == TGT_STORE) memset0(x.c);
         return true;
     }
-    if (eb == 8) {
-        if (dry) return true;
-        return simt(a, b, c, mode);
-    }
-    if (bf || x3) return gemm_split(a, b, c, mode);
     if (dry) return true;
-    Target t = make_target(c, 1.f, mode, target_map(c));
+    std::vector<Target> tv;
+    for (const Dest& x : d) tv.push_back(make_target(x.c, x.sign, x.mode, target_map(x.c)));
     Leaf lf;
     memset(&lf, 0, sizeof(lf));
     lf.tag = -1;
     lf.a_map = 0;
     lf.b_map = 1;
-    lf.m = c.rows;
-    lf.n = c.cols;
+    lf.m = rows;
+    lf.n = cols;
     lf.tgt_begin = 0;
-    lf.tgt_count = 1;
+    lf.tgt_count = (int)tv.size();
     lf.tile_begin = 0;
     Op o;
     o.kind = OP_GEMM_TF32;
-    o.bn = force_bn ? force_bn : tf32_bn(c.cols);
+    o.bn = force_bn ? force_bn : tf32_bn(cols);
     lf.kblocks = (int)ceil_div(a.cols, tf32_tile_k());
-    lf.tiles_n = (int)ceil_div(c.cols, o.bn);
+    lf.tiles_n = (int)ceil_div(cols, o.bn);
     o.nmaj = nmaj;
     if (!make_map_f32(&o.maps.m[0], a.p, a.rows, a.cols, a.ld, 32, tf32_tile_m()) ||
         !(nmaj ? make_map_f32_n(&o.maps.m[1], b.p, b.rows, b.cols, b.ld)
@@ -123,9 +134,8 @@ bool Planner::gemm(View a, View b, View c, int mode) {
         err = "tensor map encoding failed (alignment?)";
         return false;
     }
-    o.items = (int)(ceil_div(c.rows, tf32_tile_m()) * lf.tiles_n);
+    o.items = (int)(ceil_div(rows, tf32_tile_m()) * lf.tiles_n);
     std::vector<Leaf> lv(1, lf);
-    std::vector<Target> tv(1, t);
     if (pair_ok(o.bn)) to_pair(o, lv);
     emit_grouped(o, lv, tv, 0);
     return true;
@@ -134,27 +144,35 @@ bool Planner::gemm(View a, View b, View c, int mode) {
 // Split leaf (split-BF16 or compensated TF32): both operands split into (hi, lo) halves in
 // workspace (released once the launch is queued: later ops run after it on the same stream),
 // then one launch.
-bool Planner::gemm_split(View a, View b, View c, int mode) {
+bool Planner::gemm_split_to(View a, View b, const std::vector<Dest>& d) {
+    const int rows = d[0].c.rows, cols = d[0].c.cols;
+    if (rows <= 0 || cols <= 0) return true;
+    if (a.cols == 0) {
+        for (const Dest& x : d)
+            if (x.mode == TGT_STORE) memset0(x.c);
+        return true;
+    }
     const size_t mark = ws_top;
     View ah, al, bh, bl;
     split(a, ah, al);
     split(b, bh, bl);
     bool ok = true;
     if (!dry) {
-        Target t = make_target(c, 1.f, mode, target_map(c));
+        std::vector<Target> tv;
+        for (const Dest& x : d) tv.push_back(make_target(x.c, x.sign, x.mode, target_map(x.c)));
         Leaf lf;
         memset(&lf, 0, sizeof(lf));
         lf.tag = -1;
         lf.a_map = 0;
         lf.b_map = 1;
-        lf.m = c.rows;
-        lf.n = c.cols;
-        lf.tgt_count = 1;
+        lf.m = rows;
+        lf.n = cols;
+        lf.tgt_count = (int)tv.size();
         Op o;
         o.kind = x3 ? OP_GEMM_TF32X3 : OP_GEMM_BF16X3;
-        o.bn = bn_override() ? bn_override() : (x3 || c.cols <= 128 ? 128 : 256);
+        o.bn = bn_override() ? bn_override() : (x3 || cols <= 128 ? 128 : 256);
         lf.kblocks = (int)ceil_div(a.cols, x3 ? tf32_tile_k() : bf16x3_tile_k());
-        lf.tiles_n = (int)ceil_div(c.cols, o.bn);
+        lf.tiles_n = (int)ceil_div(cols, o.bn);
         if (x3)
             ok = make_map_f32(&o.maps.m[0], ah.p, ah.rows, ah.cols, ah.ld, 32, tf32_tile_m()) &&
                  make_map_f32(&o.maps.m[1], al.p, al.rows, al.cols, al.ld, 32, tf32_tile_m()) &&
@@ -166,14 +184,14 @@ bool Planner::gemm_split(View a, View b, View c, int mode) {
                  make_map_bf16(&o.maps.m[2], bh.p, bh.rows, bh.cols, bh.ld, 64) &&
                  make_map_bf16(&o.maps.m[3], bl.p, bl.rows, bl.cols, bl.ld, 64);
         if (!ok) err = "split-leaf tensor map encoding failed";
-        o.items = (int)(ceil_div(c.rows, tf32_tile_m()) * lf.tiles_n);
+        o.items = (int)(ceil_div(rows, tf32_tile_m()) * lf.tiles_n);
         if (!x3 && pair_ok(o.bn)) {  // 256-row tiles on CTA pairs
-            o.items = (int)(ceil_div(c.rows, 2 * tf32_tile_m()) * lf.tiles_n);
+            o.items = (int)(ceil_div(rows, 2 * tf32_tile_m()) * lf.tiles_n);
             o.pair = true;
         }
         o.nleaves = 1;
         o.leaves_off = put_blob(&lf, sizeof(lf));
-        o.targets_off = put_blob(&t, sizeof(t));
+        o.targets_off = put_blob(tv.data(), tv.size() * sizeof(Target));
         flush_tmaps(o);
         push(o);
     }
@@ -181,35 +199,38 @@ bool Planner::gemm_split(View a, View b, View c, int mode) {
     return ok;
 }
 
-// SIMT product c (=|+=) a b with b in logical orientation (k x n).
-bool Planner::simt(View a, View b, View c, int mode) {
-    if (c.rows <= 0 || c.cols <= 0) return true;
+// SIMT product (FP64 leaves; FP32 thin fix-ups) with b in logical orientation (k x n).
+bool Planner::simt_to(View a, View b, const std::vector<Dest>& d) {
+    const int rows = d[0].c.rows, cols = d[0].c.cols;
+    if (rows <= 0 || cols <= 0) return true;
     if (a.cols == 0) {
-        if (mode == TGT_STORE) memset0(c);
+        for (const Dest& x : d)
+            if (x.mode == TGT_STORE) memset0(x.c);
         return true;
     }
     if (dry) return true;
-    Target t = make_target(c, 1.f, mode);
+    std::vector<Target> tv;
+    for (const Dest& x : d) tv.push_back(make_target(x.c, x.sign, x.mode));
     Leaf lf;
     memset(&lf, 0, sizeof(lf));
     lf.tag = -1;
     lf.a_map = 0;
     lf.b_map = 1;
-    lf.m = c.rows;
-    lf.n = c.cols;
+    lf.m = rows;
+    lf.n = cols;
     lf.kblocks = a.cols;
-    lf.tiles_n = (int)ceil_div(c.cols, F64_BN);
-    lf.tgt_count = 1;
+    lf.tiles_n = (int)ceil_div(cols, F64_BN);
+    lf.tgt_count = (int)tv.size();
     Op o;
     o.kind = OP_GEMM_SIMT;
     o.eb = eb;
     o.wtile = wtile && eb == 8;
     MatRef refs[2] = {{a.p, a.ld, a.rows, a.cols}, {b.p, b.ld, b.rows, b.cols}};
     o.refs_off = put_blob(refs, sizeof(refs));
-    o.items = (int)(ceil_div(c.rows, F64_BM) * lf.tiles_n);
+    o.items = (int)(ceil_div(rows, F64_BM) * lf.tiles_n);
     o.nleaves = 1;
     o.leaves_off = put_blob(&lf, sizeof(lf));
-    o.targets_off = put_blob(&t, sizeof(t));
+    o.targets_off = put_blob(tv.data(), tv.size() * sizeof(Target));
     push(o);
     return true;
 }
@@ -225,7 +246,17 @@ bool Planner::product(View a, View b, View c, int L) {
         ws_top = mark;
         return ok;
     }
-    if (sched == SW_SCHED_TWO_TEMP || (fused_below > 0 && algo == SW_ALGO_WINOGRAD)) return two_temp(a, b, c, L);
+    if (fused_below > 0 && algo == SW_ALGO_WINOGRAD) return two_temp(a, b, c, L);
+    if (sched == SW_SCHED_TWO_TEMP) {
+        // Table 2 step by step down to one level above the leaves; that last level folds its
+        // post-additions into the leaf epilogues (deeper folding multiplies the C blocks every leaf
+        // launch writes: measured slower at depth 2).  The product overwrites c, so none of its
+        // blocks counts as written yet.
+        static const bool literal = getenv("SWMM_TWO_TEMP_LITERAL") != nullptr;  // diagnostics
+        if (literal || L > 1) return two_temp(a, b, c, L);
+        written.clear();
+        return two_temp_folded(a, b, {Dest{c, 1.f, -1}}, L);
+    }
     if (sched == SW_SCHED_IN_PLACE) return in_place(a, b, c, L);
     return algo == SW_ALGO_STRASSEN ? alloc_strassen(a, b, c, L) : alloc_winograd(a, b, c, L);
 }
@@ -336,6 +367,46 @@ bool Planner::two_temp(View a, View b, View c, int L) {
     return ok;
 }
 
+// Table 2 (Sec. 3.3) with the post-additions folded into the products' epilogues.  The sums take
+// the table's steps and order on X (A-quadrant sums) and Y (B-quadrant sums), two sum steps per
+// launch where the table has two in a row; each product adds sign * P straight into the C blocks
+// its U-chain terms reach (BDPZ coefficients, Sec. 2.3), the block's first write storing, so steps
+// 13-17, 20 and 22 need no launch of their own and P1 no longer occupies X.  `d` is where this
+// product goes: the quadrant destinations of the level above, its sign folded in (at the top, C
+// itself).  Footprint per level: X (m/2 x k/2) and Y (k/2 x n/2).
+bool Planner::two_temp_folded(View a, View b, const std::vector<Dest>& d, int L) {
+    if (L == 0) return leaf_to(a, b, d);
+    View A11 = quad(a, 0), A12 = quad(a, 1), A21 = quad(a, 2), A22 = quad(a, 3);
+    View B11 = quadB(b, 0), B12 = quadB(b, 1), B21 = quadB(b, 2), B22 = quadB(b, 3);
+    const int m2 = A11.rows, k2 = A11.cols, n2 = d[0].c.cols / 2;
+    const ProdTab& T = table(SW_ALGO_WINOGRAD);
+    // destinations of product p: every (quadrant, sign) it feeds, within every block of `d`
+    auto dest = [&](int p) {
+        std::vector<Dest> r;
+        for (int t = 0; t < T.ntgt[p]; ++t)
+            for (const Dest& x : d) r.push_back(Dest{quad(x.c, T.tgt[p][t].q), x.sign * (float)T.tgt[p][t].s, -1});
+        return r;
+    };
+    const size_t mark = ws_top;
+    View X = talloc(m2, k2);
+    View Y = tallocB(k2, n2);
+    bool ok = true;
+    add2(X, A11, A21, -1, Y, B22, B12, -1);         //  1,  2  S3 -> X, T3 -> Y
+    ok &= two_temp_folded(X, Y, dest(6), L - 1);    //  3      P7 = S3 T3
+    add2(X, A21, A22, +1, Y, B12, B11, -1);         //  4,  5  S1 -> X, T1 -> Y
+    ok &= two_temp_folded(X, Y, dest(4), L - 1);    //  6      P5 = S1 T1
+    add2(X, X, A11, -1, Y, B22, Y, -1);             //  7,  8  S2 -> X, T2 -> Y
+    ok &= two_temp_folded(X, Y, dest(5), L - 1);    //  9      P6 = S2 T2
+    add(X, A12, X, -1);                             // 10      S4 -> X
+    ok &= two_temp_folded(X, B22, dest(2), L - 1);  // 11      P3 = S4 B22
+    ok &= two_temp_folded(A11, B11, dest(0), L - 1);// 12      P1 = A11 B11 (13-17 in its epilogues)
+    add(Y, Y, B21, -1);                             // 18      T4 -> Y
+    ok &= two_temp_folded(A22, Y, dest(3), L - 1);  // 19      P4 = A22 T4 (20: U6 = U3 - P4)
+    ok &= two_temp_folded(A12, B21, dest(1), L - 1);// 21      P2 = A12 B21 (22: U1 = P1 + P2)
+    ws_top = mark;
+    return ok;
+}
+
 // Table 3 (Sec. 3.3): temporaries stored in the quadrants of A, B and C.  Sub-products
 // recurse in place too, so each one may overwrite its two operand blocks; the table's
 // order never reads a block after such a product consumed it.  Square only: the C22
@@ -409,7 +480,7 @@ int resolve_depth(int m, int n, int k, int cutoff, uint32_t variant, int eb) {
 // the BN = 256 form the resident loop runs, without ordering counters.
 sw_status build_plan(sw_handle h, int eb, const void* A, int lda, const void* B, int ldb, void* C, int ldc,
                             int m, int n, int k, int cutoff, uint32_t variant, bool dry, Plan* plan,
-                            char* ws_base, bool server, uint32_t top_mask) {
+                            char* ws_base, bool server, uint32_t top_mask, int b_sums_mode, char* b_sums) {
     const uint32_t algo = variant & SW_ALGO_MASK, sched = variant & SW_SCHED_MASK, odd = variant & SW_ODD_MASK;
     if (algo > SW_ALGO_WINOGRAD_KNUTH) return fail(h, SW_EINVAL, "unknown algorithm bits");
     if (sched > SW_SCHED_ALLOC) return fail(h, SW_EINVAL, "unknown schedule bits");
@@ -447,6 +518,8 @@ sw_status build_plan(sw_handle h, int eb, const void* A, int lda, const void* B,
     P.server = server;
     P.sms = h->sms;
     P.top_mask = top_mask;
+    P.b_sums_mode = b_sums_mode;
+    P.b_sums = b_sums;
     if (server && eb == 4 && !bf) P.force_bn = 256;
     const int L = resolve_depth(m, n, k, cutoff, variant, eb);
     plan->depth = L;

@@ -39,6 +39,11 @@ struct Planner {
     // Knuth's form in the BDPZ numbering); the others are left out and C holds the contributions of
     // the rest (FUSED only).  0x7F: the whole product.
     uint32_t top_mask = 0x7Fu;
+    // B-side operand sums shared by products with the same B (the row panels of one product; FUSED,
+    // TF32 leaves): 0 computed by the product itself; 1 only the B-side sums, written to b_sums (no
+    // product); 2 read from b_sums (no B-side pass).
+    int b_sums_mode = 0;
+    char* b_sums = nullptr;
 
     // Batch mode: products append their leaves, targets and operand maps to one grouped launch
     // instead of emitting their own (operand maps then live in global memory).
@@ -176,6 +181,16 @@ struct Planner {
         o.y = y.p;
         o.ldy = y.ld;
         o.sy = sy;
+        push(o);
+    }
+
+    // two independent block additions (z1 = x1 + s1 y1, z2 = x2 + s2 y2) in one launch
+    void add2(View z1, View x1, View y1, float s1, View z2, View x2, View y2, float s2) {
+        Op o;
+        o.kind = OP_ADDSUB2;
+        o.eb = eb;
+        o.job_a = {z1.rows, z1.cols, z1.p, z1.ld, x1.p, x1.ld, y1.p, y1.ld, s1};
+        o.job_b = {z2.rows, z2.cols, z2.p, z2.ld, x2.p, x2.ld, y2.p, y2.ld, s2};
         push(o);
     }
 
@@ -319,10 +334,25 @@ struct Planner {
     }
 
     // ---------------------------------------------------------- leaves and materialised schedules (planner.cu)
+    // A destination of a leaf product: block c receives sign * P (mode TGT_STORE: the block's first
+    // write; TGT_ADD / TGT_ATOMIC: added; -1: decided by `written`).  All destinations of one leaf
+    // have the product's shape.
+    struct Dest { View c; float sign; int mode; };
+    // leaf blocks of C already written by the plan (its launches run in order on one stream)
+    std::set<std::tuple<const char*, int, int>> written;
     // One leaf product c (=|+=) a b: tensor cores (FP32), split leaves, or the SIMT kernel (FP64).
     bool gemm(View a, View b, View c, int mode);
     bool gemm_split(View a, View b, View c, int mode);
     bool simt(View a, View b, View c, int mode);
+    // The same with several destinations (mode -1 resolved against `written`).
+    bool leaf_to(View a, View b, std::vector<Dest> d);
+    bool gemm_to(View a, View b, const std::vector<Dest>& d);
+    bool gemm_split_to(View a, View b, const std::vector<Dest>& d);
+    bool simt_to(View a, View b, const std::vector<Dest>& d);
+    // Table 2 with its post-additions (steps 13-17, 20, 22) folded into the epilogues of the
+    // products: each product adds +-P into the C blocks it feeds (used for the level just above
+    // the leaves; SWMM_TWO_TEMP_LITERAL=1: the table's steps one by one, for comparison).
+    bool two_temp_folded(View a, View b, const std::vector<Dest>& d, int L);
     // c <- a b at depth L with the plan's schedule: Alg. 2 / Alg. 3 with fresh temporaries, Table 2
     // (two temporaries per level) or Table 3 (temporaries in A, B and C).
     bool product(View a, View b, View c, int L);

@@ -55,7 +55,8 @@ sw_status run_ops(sw_handle h, Plan* plan, cudaStream_t s, size_t first, size_t 
     for (size_t oi = first; oi < last && oi < plan->ops.size(); ++oi) {
         Op& o = plan->ops[oi];
         cudaError_t e = cudaSuccess;
-        sw_handle_s::ProfRec rec = {(int)o.kind, nullptr, nullptr};
+        // (a paired block addition is profiled as a block addition)
+        sw_handle_s::ProfRec rec = {o.kind == OP_ADDSUB2 ? (int)OP_ADDSUB : (int)o.kind, nullptr, nullptr};
         if (h->prof) {
             rec.e0 = prof_event(h);
             rec.e1 = prof_event(h);
@@ -131,6 +132,9 @@ sw_status run_ops(sw_handle h, Plan* plan, cudaStream_t s, size_t first, size_t 
                 break;
             case OP_PREADD:
                 e = o.pre_two ? launch_preadd2(o.pre, o.pre_b, s) : launch_preadd(o.eb, o.pre, s);
+                break;
+            case OP_ADDSUB2:
+                e = launch_addsub2(o.eb, o.job_a, o.job_b, s);
                 break;
             case OP_PREADD_SPLIT:
                 e = launch_preadd_split(o.pre, o.sout, o.pre_b, o.sout_b, s);
@@ -294,7 +298,8 @@ bool capturing(cudaStream_t s) {
 }
 
 sw_status do_mm(sw_handle h, int eb, const void* A, int lda, const void* B, int ldb, void* C, int ldc, int m,
-                       int n, int k, int cutoff, uint32_t variant, void* stream, uint32_t top_mask) {
+                       int n, int k, int cutoff, uint32_t variant, void* stream, uint32_t top_mask, int b_sums_mode,
+                       char* b_sums) {
     if (!h) return SW_EINVAL;
     if (m < 0 || n < 0 || k < 0) return fail(h, SW_EINVAL, "negative dimension");
     if ((m && k && !A) || (k && n && !B) || (m && n && !C)) return fail(h, SW_EINVAL, "null matrix pointer");
@@ -305,20 +310,21 @@ sw_status do_mm(sw_handle h, int eb, const void* A, int lda, const void* B, int 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     auto builder = [=](int c) {
         return PlanBuilder([=](bool dry, Plan* p) {
-            return build_plan(h, eb, A, lda, B, ldb, C, ldc, m, n, k, c, variant, dry, p, nullptr, false, top_mask);
+            return build_plan(h, eb, A, lda, B, ldb, C, ldc, m, n, k, c, variant, dry, p, nullptr, false, top_mask,
+                              b_sums_mode, b_sums);
         });
     };
     auto key_of = [&](int c) {
         char key[256];
-        snprintf(key, sizeof(key), "%d|%p|%d|%p|%d|%p|%d|%d|%d|%d|%d|%u|%x", eb, A, lda, B, ldb, C, ldc, m, n, k, c,
-                 variant, top_mask);
+        snprintf(key, sizeof(key), "%d|%p|%d|%p|%d|%p|%d|%d|%d|%d|%d|%u|%x|%d|%p", eb, A, lda, B, ldb, C, ldc, m, n, k,
+                 c, variant, top_mask, b_sums_mode, (void*)b_sums);
         return std::string(key);
     };
     // cutoff <= 0: the autotuner picks the depth on the first call for this shape and variant (not
     // under stream capture, and not for IN_PLACE, whose runs overwrite A and B)
     const uint32_t algo = variant & SW_ALGO_MASK, sched = variant & SW_SCHED_MASK;
-    if (cutoff <= 0 && algo != SW_ALGO_NAIVE && sched != SW_SCHED_IN_PLACE && top_mask == 0x7Fu && !capturing(s) && m &&
-        n && k) {
+    if (cutoff <= 0 && algo != SW_ALGO_NAIVE && sched != SW_SCHED_IN_PLACE && top_mask == 0x7Fu && b_sums_mode == 0 &&
+        !capturing(s) && m && n && k) {
         char sig[160];
         const int align = (int)((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B) |
                                  reinterpret_cast<uintptr_t>(C)) & 15) | (((lda | ldb | ldc) & 3) << 4);
@@ -435,7 +441,7 @@ sw_status do_batched(sw_handle h, int count, const sw_problem* probs, int cutoff
 // while later panels still arrive and compute.  Row panels keep every copy one contiguous run.
 sw_status host_panels(sw_handle h, const float* A, int lda, const float* B, int ldb, float* C, int ldc, int m,
                              int n, int k, int cutoff, uint32_t variant, int L, int mp, float* dA, long long lda2,
-                             float* dB, long long ldb2, float* dC, long long ldc2, cudaStream_t s) {
+                             float* dB, long long ldb2, float* dC, long long ldc2, char* dS, cudaStream_t s) {
     const int npan = (int)ceil_div(m, mp);
     {
         std::lock_guard<std::mutex> lock(h->mu);
@@ -444,14 +450,15 @@ sw_status host_panels(sw_handle h, const float* A, int lda, const float* B, int 
             return cuda_fail(h, cudaGetLastError(), "copy stream");
         if (!h->io_out && cudaStreamCreateWithFlags(&h->io_out, cudaStreamNonBlocking) != cudaSuccess)
             return cuda_fail(h, cudaGetLastError(), "copy stream");
-        while ((int)h->io_ev.size() < 2 * npan + 2) {
+        while ((int)h->io_ev.size() < 2 * npan + 3) {
             cudaEvent_t ev;
             if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess)
                 return cuda_fail(h, cudaGetLastError(), "copy event");
             h->io_ev.push_back(ev);
         }
     }
-    cudaEvent_t* ev = h->io_ev.data();  // [0] start, [1 + i] A_i arrived, [1 + npan + i] C_i done, [last] out done
+    // [0] start, [1 + i] A_i arrived, [1 + npan + i] C_i done, [1 + 2 npan] out done, [2 + 2 npan] B arrived
+    cudaEvent_t* ev = h->io_ev.data();
     // the call is synchronous: on any failure the copies already queued finish before it returns,
     // so the caller may release its host buffers
     auto drained = [&](sw_status st) {
@@ -463,6 +470,7 @@ sw_status host_panels(sw_handle h, const float* A, int lda, const float* B, int 
     if (e == cudaSuccess) e = cudaStreamWaitEvent(h->io_in, ev[0], 0);
     if (e == cudaSuccess)
         e = cudaMemcpy2DAsync(dB, ldb2 * 4, B, (size_t)ldb * 4, (size_t)n * 4, k, cudaMemcpyHostToDevice, h->io_in);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[2 + 2 * npan], h->io_in);
     for (int i = 0; i < npan && e == cudaSuccess; ++i) {
         const int r0 = i * mp, hgt = std::min(mp, m - r0);
         e = cudaMemcpy2DAsync(dA + r0 * lda2, lda2 * 4, A + (size_t)r0 * lda, (size_t)lda * 4, (size_t)k * 4, hgt,
@@ -470,18 +478,30 @@ sw_status host_panels(sw_handle h, const float* A, int lda, const float* B, int 
         if (e == cudaSuccess) e = cudaEventRecord(ev[1 + i], h->io_in);
     }
     if (e != cudaSuccess) return drained(cuda_fail(h, e, "host to device copy"));
+    // B's operand sums once for all panels at the whole product's depth, as soon as B has arrived
+    const int cut_l = (int)std::min(std::min(ceil_div(mp, 1LL << L), ceil_div(n, 1LL << L)), ceil_div(k, 1LL << L));
+    if (dS && (cut_l < 2 || resolve_depth(std::min(mp, m), n, k, cut_l, variant, 4) != L)) dS = nullptr;
+    if (dS) {
+        e = cudaStreamWaitEvent(s, ev[2 + 2 * npan], 0);
+        if (e != cudaSuccess) return drained(cuda_fail(h, e, "panel order"));
+        sw_status st = do_mm(h, 4, dA, (int)lda2, dB, (int)ldb2, dC, (int)ldc2, std::min(mp, m), n, k, cut_l, variant, s,
+                             0x7Fu, 1, dS);
+        if (st != SW_OK) return drained(st);
+    }
     for (int i = 0; i < npan; ++i) {
         const int r0 = i * mp, hgt = std::min(mp, m - r0);
         e = cudaStreamWaitEvent(s, ev[1 + i], 0);
         if (e != cudaSuccess) return drained(cuda_fail(h, e, "panel order"));
         int cut = cutoff;
+        bool shared = false;  // this panel reads the shared B-side sums
         if ((variant & SW_ALGO_MASK) != SW_ALGO_NAIVE) {
             const long long d = 1LL << L;
             cut = (int)std::min(std::min(ceil_div(hgt, d), ceil_div(n, d)), ceil_div(k, d));
             if (cut < 2 || resolve_depth(hgt, n, k, cut, variant, 4) != L) cut = cutoff;  // low last panel
+            else shared = dS != nullptr;
         }
-        sw_status st = sw_smm(h, dA + r0 * lda2, (int)lda2, dB, (int)ldb2, dC + r0 * ldc2, (int)ldc2, hgt, n, k, cut,
-                              variant, s);
+        sw_status st = do_mm(h, 4, dA + r0 * lda2, (int)lda2, dB, (int)ldb2, dC + r0 * ldc2, (int)ldc2, hgt, n, k, cut,
+                             variant, s, 0x7Fu, shared ? 2 : 0, shared ? dS : nullptr);
         if (st != SW_OK) return drained(st);
         e = cudaEventRecord(ev[1 + npan + i], s);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(h->io_out, ev[1 + npan + i], 0);
