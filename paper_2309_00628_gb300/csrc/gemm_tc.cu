@@ -521,6 +521,7 @@ __global__ void __launch_bounds__(192, 1)
         uint8_t* stg = base + Cfg::STG_OFF + (warp - 2) * 8192;  // two 4 KB swizzled buffers
         int local = 0, chunk_ctr = 0;
         bool issued_bulk = false;
+        bool last_mixed = false;  // the last TMA group read both staging buffers (a mixed-sign chunk)
         int rslot = 0;
         uint32_t rph = 0;
         for (int item = RES ? -1 : unit;; item += RES ? 0 : nunits, ++local) {
@@ -581,14 +582,21 @@ __global__ void __launch_bounds__(192, 1)
                     const bool mixed = has_pos && has_neg;
                     uint8_t* bpos;
                     uint8_t* bneg;
-                    if (mixed) {
+                    // a buffer is rewritten only once every TMA group that reads it has read it: with
+                    // one buffer per chunk the group before last, after a mixed chunk (which reads
+                    // both) all of them
+                    if (mixed || last_mixed) {
                         if (lane == 0) bulk_wait_read<0>();
+                    } else {
+                        if (lane == 0) bulk_wait_read<1>();
+                    }
+                    if (mixed) {
                         bpos = stg;
                         bneg = stg + 4096;
                     } else {
-                        if (lane == 0) bulk_wait_read<1>();
                         bpos = bneg = stg + (chunk_ctr & 1) * 4096;
                     }
+                    last_mixed = mixed;
                     __syncwarp();
                     // row `lane` of the chunk; 16-byte piece j sits at piece j ^ (row & 7)
                     const uint32_t row_off = (uint32_t)lane * 128u;
