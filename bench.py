@@ -745,7 +745,16 @@ def main():
         tot, _, _, _ = timed(swmm.SW_ALGO_WINOGRAD | swmm.SW_SCHED_FUSED, 0, ks, W)
         tuned = {"cutoff": tune["cutoff"], "depth": swmm.sw_mm_depth(n, n, n, tune["cutoff"], variant, 4)[1],
                  "candidates": tune["candidates"], "ms": tot / ks, "eff_tflops": flop / (tot / ks / 1e3) / 1e12}
-        extra = {"autotuned_winograd_n8192": tuned,
+        # Winograd and the plain product in alternating blocks (the power cap drifts over a long
+        # timed region, so back-to-back blocks compare the two under the same conditions)
+        alt = {"winograd_ms": [], "plain_ms": []}
+        for _ in range(5):
+            for key, v, c in (("winograd_ms", variant, args.cutoff), ("plain_ms", swmm.SW_ALGO_NAIVE, 0)):
+                tot, _, _, _ = timed(v, c, 20, 2)
+                alt[key].append(tot / 20)
+        alt["speedup_per_round"] = [p_ / w_ for w_, p_ in zip(alt["winograd_ms"], alt["plain_ms"])]
+        alt["speedup"] = sum(alt["plain_ms"]) / sum(alt["winograd_ms"])
+        extra = {"autotuned_winograd_n8192": tuned, "alternating_vs_plain_n8192": alt,
                  "depth_sweep_n8192_tf32": depth_rows, "depth_sweep_n4096_tf32": depth_rows5,
                  "fp32_accuracy_leaves_n8192": bf_rows,
                  "n16384_tf32": big,
