@@ -300,7 +300,7 @@ bool Planner::fused(View A, View B, View C, int L) {
                      : force_bn             ? force_bn
                      : x3 || (bf && nb <= 128) ? 128
                      : bf                   ? 256
-                                            : tf32_bn(nb);
+                                            : tf32_bn(nb, kb <= 2048);
     std::vector<int> first_writer(1 << (2 * L), -1), flag_base(1 << (2 * L), -1), flag_cols(1 << (2 * L), 0);
     int nflags = 0;
     // leaves and their Kronecker-product targets

@@ -124,7 +124,7 @@ bool Planner::gemm_to(View a, View b, const std::vector<Dest>& d) {
     lf.tile_begin = 0;
     Op o;
     o.kind = OP_GEMM_TF32;
-    o.bn = force_bn ? force_bn : tf32_bn(cols);
+    o.bn = force_bn ? force_bn : tf32_bn(cols, d.size() > 1 && a.cols <= 2048);
     lf.kblocks = (int)ceil_div(a.cols, tf32_tile_k());
     lf.tiles_n = (int)ceil_div(cols, o.bn);
     o.nmaj = nmaj;

@@ -62,11 +62,16 @@ struct Planner {
     }
     // Tile width of a TF32 launch over C blocks `cols` wide: 512 (CTA pairs, one accumulator, a
     // quarter fewer operand bytes per MMA) where the blocks are at least 512 wide and 512-wide tiles
-    // pad no more than 256-wide ones; else 256, or 128 for narrow blocks.
-    int tf32_bn(int cols) const {
+    // pad no more than 256-wide ones; else 256, or 128 for narrow blocks.  `shallow`: the leaves'
+    // inner dimension is at most 2048 and each tile feeds several C blocks (recursive leaves), so
+    // the one accumulator of a 512-wide tile would expose an epilogue as long as a good part of
+    // the tile's MMA work: 256-wide tiles with two accumulators instead (n = 8192: Winograd L2
+    // 1.770 -> 1.728 ms, L3 3.985 -> 3.760, Strassen L2 1.637 -> 1.573; with 4096-deep leaves
+    // 512-wide tiles stay ahead, n = 16384 L2 10.41 vs 10.96 ms).
+    int tf32_bn(int cols, bool shallow = false) const {
         if (bn_override()) return bn_override() == 512 && !pair_ok(512) ? 256 : bn_override();
         if (cols <= 128) return 128;
-        if (pair_ok(512) && cols >= 512 && round_up(cols, 512) == round_up(cols, 256)) return 512;
+        if (!shallow && pair_ok(512) && cols >= 512 && round_up(cols, 512) == round_up(cols, 256)) return 512;
         return 256;
     }
     // rows of one B-side TMA box: half the tile width for a CTA pair
