@@ -294,13 +294,24 @@ bool Planner::fused(View A, View B, View C, int L) {
     // path, where the first writer's tiles lead their position group and the waits are short;
     // deeper levels (many leaves queue behind one writer) and the SIMT FP64 leaf keep a zeroed
     // C and reduce-adds only.
-    const bool ordered = eb == 4 && L == 1 && !batch && !server && top_mask == 0x7Fu;
-    if (!ordered) memset0(C);
     const int bn_o = eb == 8                ? F64_BN
                      : force_bn             ? force_bn
                      : x3 || (bf && nb <= 128) ? 128
                      : bf                   ? 256
                                             : tf32_bn(nb, kb <= 2048);
+    // Ordered stores pay off only while every unit starts on a first writer's work: a product with
+    // fewer first-writer jobs than units leaves the other units waiting for those stores (n = 4096,
+    // depth 1: 32 store jobs for 76 CTA pairs), so it zeroes C and reduce-adds everything instead.
+    bool ordered = eb == 4 && L == 1 && !batch && !server && top_mask == 0x7Fu;
+    if (ordered) {
+        const bool pr = !bf && !x3 && pair_ok(bn_o);
+        const long long tm_rows = pr ? 2LL * tf32_tile_m() : tf32_tile_m();
+        const long long positions = ceil_div(mb, tm_rows) * ceil_div(nb, bn_o);
+        const long long store_jobs = ceil_div(positions, bn_o > 256 ? 1 : 2);
+        const int units = pr ? gemm_tf32n_pair_units(sms, bn_o) : sms;
+        if (units > 0 && store_jobs < units) ordered = false;
+    }
+    if (!ordered) memset0(C);
     std::vector<int> first_writer(1 << (2 * L), -1), flag_base(1 << (2 * L), -1), flag_cols(1 << (2 * L), 0);
     int nflags = 0;
     // leaves and their Kronecker-product targets
