@@ -33,8 +33,9 @@ Compensated leaves (split-BF16 and 3xTF32).  The operand split carries x to a re
 (split-BF16: hi = bf16(x), lo = bf16(x - hi) and the dropped lo*lo term give a term error of
 RMS below 2^-18; 3xTF32: hi = tf32(x) and lo read as TF32 truncate lo by at most 2^-10 |lo| <=
 2^-21 |x|, uniformly, RMS 2^-21 / sqrt(3), the dropped lo*lo term below 2^-22).  These terms
-behave like the TF32 ones with 2^-10 replaced by e.  What dominates is the FP32 accumulator: each MMA adds its partial sum into the accumulator with one rounding of
-relative size below u = 2^-23 (a truncating FP32 accumulate; the tensor core's rounding is not
+behave like the TF32 ones with 2^-10 replaced by e.  What dominates is the FP32 accumulator:
+each MMA adds its partial sum into the accumulator with one rounding of relative size below
+u = 2^-23 (a truncating FP32 accumulate; the tensor core's rounding is not
 documented, so the worse of truncation and rounding to nearest is assumed), all of one sign in
 the worst case.  With n_mma MMAs of depth K per k-step (split-BF16: 3 of K = 16; 3xTF32: 3 of
 K = 8) the accumulated error is u n_mma sum_j |D_j| with |D_j| ~ sqrt(2/pi) sqrt(K j) RMS(ab),

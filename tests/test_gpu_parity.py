@@ -575,10 +575,12 @@ def test_ordered_depth1_graph_replay_integers_bit_exact(h, leaf):
     # a depth-1 product whose C blocks take a store then reduce-adds (ordering counters) captured
     # once into a CUDA graph and replayed on new data in the same buffers: every replay orders its
     # adds after its own stores (the launch epoch lives on the device, not in the captured args)
-    m = n = k = 1536
+    # (large enough that the product keeps its ordered stores: at least one store job per unit)
+    m, n, k = 8192, 8192, 1024
     cutoff = 1000
     v = W | FUSED | leaf
     assert depth(h, m, n, k, cutoff, v, 4) == 1
+    rows = np.sort(np.random.Generator(np.random.PCG64(94)).choice(m, 24, replace=False))
     dA = torch.zeros((m, k), dtype=torch.float32, device="cuda")
     dB = torch.zeros((k, n), dtype=torch.float32, device="cuda")
     dC = torch.zeros((m, n), dtype=torch.float32, device="cuda")
@@ -601,8 +603,38 @@ def test_ordered_depth1_graph_replay_integers_bit_exact(h, leaf):
         g.replay()
         torch.cuda.synchronize()
         swmm.check(h, swmm.sw_sync(h, None))
-        assert np.array_equal(dC.cpu().numpy().astype(np.float64), oracle.naive_mt(A, B)), seed
+        got = dC[torch.from_numpy(rows).cuda()].cpu().numpy().astype(np.float64)
+        assert np.array_equal(got, oracle.naive_mt(A[rows], B)), seed
+        assert not torch.isnan(dC).any()
 
+
+
+@pytest.mark.parametrize("leaf", [swmm.SW_LEAF_TF32, swmm.SW_LEAF_BF16X3])
+@pytest.mark.parametrize("algo", [W, K])
+@pytest.mark.parametrize("m,n,k,ordered", [(8192, 8192, 1024, True), (8192, 8192, 8192, True),
+                                           (2048, 2048, 2048, False), (1500, 1000, 700, False)])
+def test_depth1_ordered_and_unordered_paths_integers_bit_exact(h, leaf, algo, m, n, k, ordered):
+    # depth-1 products with enough first-writer jobs for every unit keep ordered stores and
+    # accumulation chains (no zeroing of C); smaller ones zero C and reduce-add every product
+    # (TF32 n = 8192, k = 1024: 256-wide tiles, two accumulators; k = 8192: 512-wide, one)
+    cutoff = min(m, n, k) - 1
+    v = algo | FUSED | leaf
+    assert depth(h, m, n, k, cutoff, v, 4) == 1
+    lim = 4 if k <= 4096 else 2
+    assert exact_int_safe(lim, k, 1)
+    A, B = inputs.pair(m, n, k, "int", seed=95, dtype=np.float64, lim=lim)
+    dA, dB = torch.from_numpy(A.astype(np.float32)).cuda(), torch.from_numpy(B.astype(np.float32)).cuda()
+    dC = torch.full((m, n), float("nan"), device="cuda")
+    swmm.check(h, swmm.sw_profile(h, True))
+    swmm.sw_profile_read(h)
+    swmm.mm(h, dA, dB, cutoff, v, out=dC, sync=True)
+    _, prof = swmm.sw_profile_read(h)
+    swmm.check(h, swmm.sw_profile(h, False))
+    assert (prof["memset"][0] == 0) == ordered, prof["memset"]
+    rows = np.sort(np.random.Generator(np.random.PCG64(96)).choice(m, 16, replace=False))
+    got = dC[torch.from_numpy(rows).cuda()].cpu().numpy().astype(np.float64)
+    assert np.array_equal(got, oracle.naive_mt(A[rows], B))
+    assert not torch.isnan(dC).any()
 
 
 @pytest.mark.parametrize("algo,cutoff", [(W, 23200), (swmm.SW_ALGO_NAIVE, 0)])
