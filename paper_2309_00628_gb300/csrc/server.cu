@@ -22,7 +22,11 @@ using namespace swh;
 // the SMs the resident kernel leaves free.
 namespace {
 
-constexpr int SRV_SIDE = 4;                   // side streams
+constexpr int SRV_SIDE = 4;                   // side streams: [0, SRV_SIDE / 2) high priority, the rest low
+// A request whose work is estimated below this many milliseconds (TF32 leaves at ~900 TFLOP/s, FP64
+// at ~1.5 TFLOP/s) runs on a high-priority side stream, so that its blocks take the SMs before
+// pending blocks of long requests (the FP64 n = 8192 products take half a second each).
+constexpr double SRV_SHORT_MS = 2.0;
 constexpr unsigned SRV_MAX_ITEMS = 1u << 21;  // published tiles per generation
 constexpr int SRV_MAX_LEAVES = 1 << 16;
 constexpr int SRV_MAX_TARGETS = 1 << 18;
@@ -77,7 +81,7 @@ struct Server {
     std::vector<int> free_slots;
     std::vector<cudaEvent_t> ev_pool;
     Arena arena, blobs;
-    int side_rr = 0;
+    int side_rr[2] = {0, 0};  // round robin within the high- / low-priority side streams
     unsigned n_items = 0;
     int n_leaves = 0, n_targets = 0, n_maps = 0, n_tmaps = 0;
     bool res_launched = false;
@@ -197,8 +201,12 @@ sw_status Server::init(sw_handle h, const sw_server_cfg* c, std::string* msg) {
     if (cudaStreamCreateWithFlags(&res_stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&ctl_stream, cudaStreamNonBlocking) != cudaSuccess)
         return oom("streams");
-    for (auto& s : side)
-        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return oom("streams");
+    int prio_low = 0, prio_high = 0;
+    if (cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high) != cudaSuccess) return oom("stream priorities");
+    for (int i = 0; i < SRV_SIDE; ++i)
+        if (cudaStreamCreateWithPriority(&side[i], cudaStreamNonBlocking, i < SRV_SIDE / 2 ? prio_high : prio_low) !=
+            cudaSuccess)
+            return oom("streams");
     if (cudaEventCreateWithFlags(&res_ev, cudaEventDisableTiming) != cudaSuccess) return oom("events");
     for (int i = cfg.max_inflight - 1; i >= 0; --i) free_slots.push_back(i);
     return SW_OK;
@@ -306,8 +314,10 @@ void Server::start(ServerReq* r) {
     r->plan.owns_blob = false;
     if (st != SW_OK) { complete(r, st, shadow.last_error); return; }
     if (r->plan.ws_need > r->need) { complete(r, SW_ECUDA, "serving: workspace grew after sizing"); return; }
-    cudaStream_t s = side[side_rr];
-    side_rr = (side_rr + 1) % SRV_SIDE;
+    const double work_ms = 2.0 * (double)q.m * q.n * q.k / (q.elem_bytes == 8 ? 1.5e9 : 9e11);
+    const int cls = work_ms < SRV_SHORT_MS ? 0 : 1;
+    cudaStream_t s = side[cls * (SRV_SIDE / 2) + side_rr[cls]];
+    side_rr[cls] = (side_rr[cls] + 1) % (SRV_SIDE / 2);
     if (!r->plan.blob.empty()) {
         const size_t nb = (size_t)round_up((long long)r->plan.blob.size(), 256);
         size_t off = 0;
