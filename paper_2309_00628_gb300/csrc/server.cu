@@ -290,7 +290,7 @@ void Server::reset_generation() {
 
 sw_status Server::launch_resident() {
     set_mapped(32, 0u);
-    ResidentCtl c;
+    ResidentCtl c = {};
     c.next = ctl_d;
     c.published = mapped_d;
     c.stop = mapped_d + 32;
