@@ -64,6 +64,9 @@ def parse():
     p.add_argument("--profile-batched", type=int, default=0, metavar="COUNT",
                    help="only the first COUNT products of the batched workload: one tuning call, then "
                         "--warmup + 1 more batched calls (for ncu captures)")
+    p.add_argument("--batched-cutoff", type=int, default=0,
+                   help="cutoff of the --profile-batched calls (0: the autotuner; 1073741824: no recursion, "
+                        "the default grouped-launch form, no tuning launches)")
     return p.parse_args()
 
 
@@ -422,11 +425,13 @@ def main():
             probs.append(swmm.sw_problem(tA.data_ptr(), k, tB.data_ptr(), nn, tC.data_ptr(), nn, m, nn, k))
         arr = (swmm.sw_problem * len(probs))(*probs)
         vb = swmm.SW_ALGO_WINOGRAD | swmm.SW_SCHED_FUSED
-        for _ in range(args.warmup + 2):  # the first call tunes (4 candidates, 2 timed runs each)
-            swmm.check(h, swmm.sw_mm_batched(h, len(probs), arr, 0, vb, sp))
+        for _ in range(args.warmup + 2):  # cutoff 0: the first call tunes (5 candidates, 2 timed runs each)
+            swmm.check(h, swmm.sw_mm_batched(h, len(probs), arr, args.batched_cutoff, vb, sp))
         swmm.check(h, swmm.sw_sync(h, sp))
         if rank == 0:
-            print(json.dumps({"profile_batched": len(probs), "autotuner": swmm.sw_last_tuning(h)[1]}), flush=True)
+            tune = swmm.sw_last_tuning(h)
+            print(json.dumps({"profile_batched": len(probs), "autotuner": tune[1] if tune[0] == swmm.SW_OK else None}),
+                  flush=True)
         swmm.sw_destroy(h)
         return
 

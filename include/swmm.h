@@ -209,7 +209,9 @@ sw_status sw_mm_batched(sw_handle h, int count, const sw_problem *probs, int cut
 
 /* The autotuner's last decision on this handle (a call with cutoff <= 0 that had to tune): the
  * chosen cutoff (1 << 30: no recursion), the grouped GEMM's tile width and CTA-pair flag (batched
- * calls; 0 for single products), the winner's device time in ms and the number of candidates timed.
+ * calls; 0 for single products: 0 one CTA per tile, 1 CTA pairs, 2 CTA pairs whose GEMM launch
+ * also runs the copies that pack operands with rows not 16-byte aligned), the winner's device time
+ * in ms and the number of candidates timed.
  * Any pointer may be NULL.  SW_EINVAL if nothing has been tuned on the handle. */
 sw_status sw_last_tuning(sw_handle h, int *cutoff, int *tile_n, int *cta_pair, double *ms, int *candidates);
 

@@ -472,8 +472,10 @@ bool Planner::fused(View A, View B, View C, int L) {
 // Many independent products in one grouped launch: one batched copy launch packs the A and B
 // operands whose rows are not 16-byte aligned (bt storage: a batched transpose launch writes
 // every B^T instead), the depth >= 1 products add their operand-sum passes, and all leaves of
-// all products go into a single persistent GEMM launch (longest k first).  C needs no
-// staging: unaligned or ragged C blocks take the per-thread epilogue.
+// all products go into a single persistent GEMM launch (longest k first).  With pack_in_gemm (no
+// recursion, CTA pairs) that launch runs the packing copies itself, in product order, and each
+// leaf's loads wait for its operands' jobs.  C needs no staging: unaligned or ragged C blocks take
+// the per-thread epilogue.
 bool Planner::batched(const sw_problem* probs, int count, const std::vector<int>& depth) {
     batch = true;
     force_bn = batch_bn == 128 ? 128 : 256;
@@ -483,6 +485,7 @@ bool Planner::batched(const sw_problem* probs, int count, const std::vector<int>
     std::vector<CopyJob> packs, trans;
     int pack_tiles = 0, trans_tiles = 0;
     std::vector<View> As(count), Bs(count), Cs(count);
+    std::vector<int> ajob(count, -1), bjob(count, -1);  // pack job of each product's A / B
     auto job = [](View src, View dst, int& tiles) {
         CopyJob j;
         j.x = src.p; j.ldx = src.ld; j.out = dst.p; j.ldo = dst.ld;
@@ -498,12 +501,14 @@ bool Planner::batched(const sw_problem* probs, int count, const std::vector<int>
         if (q.m == 0 || q.n == 0 || q.k == 0) { As[i] = a; Bs[i] = b; Cs[i] = c; continue; }
         if (!vec_ok(a)) {
             View a2 = talloc(q.m, q.k);
+            ajob[i] = (int)packs.size();
             packs.push_back(job(a, a2, pack_tiles));
             a = a2;
         }
         if (nmaj) {  // B read as stored: packed only when its rows are not 16-byte aligned
             if (!vec_ok(b)) {
                 View b2 = talloc(q.k, q.n);
+                bjob[i] = (int)packs.size();
                 packs.push_back(job(b, b2, pack_tiles));
                 b = b2;
             }
@@ -516,8 +521,13 @@ bool Planner::batched(const sw_problem* probs, int count, const std::vector<int>
         Bs[i] = b;
         Cs[i] = c;
     }
+    bool depth0 = true;
+    for (int i = 0; i < count; ++i) depth0 &= depth[i] == 0;
+    const bool in_gemm = pack_in_gemm && batch_pair && nmaj && depth0 && !packs.empty();
+    for (size_t j = 0; j < packs.size(); ++j)  // tile counts, for the in-launch form's counters
+        packs[j].pad_ = (j + 1 < packs.size() ? packs[j + 1].tile_begin : pack_tiles) - packs[j].tile_begin;
     if (!dry) {
-        for (int t = 0; t < 2; ++t) {
+        for (int t = in_gemm ? 1 : 0; t < 2; ++t) {
             std::vector<CopyJob>& jobs = t == 0 ? packs : trans;
             if (jobs.empty()) continue;
             Op o;
@@ -534,8 +544,13 @@ bool Planner::batched(const sw_problem* probs, int count, const std::vector<int>
         if (q.m == 0 || q.n == 0) continue;
         View c = Cs[i];
         if (q.k == 0) { memset0(c); continue; }
+        const size_t nl = bleaves.size();
         const bool ok = depth[i] == 0 ? gemm(As[i], Bs[i], c, TGT_STORE) : fused(As[i], Bs[i], c, depth[i]);
         if (!ok) return false;
+        for (size_t l = nl; l < bleaves.size(); ++l) {
+            bleaves[l].a_job = in_gemm ? ajob[i] : -1;
+            bleaves[l].b_job = in_gemm ? bjob[i] : -1;
+        }
     }
     if (dry || bleaves.empty()) return true;
     Op o;
@@ -546,8 +561,14 @@ bool Planner::batched(const sw_problem* probs, int count, const std::vector<int>
     o.ngmaps = (int)bmaps.size();
     o.gmaps_off = put_blob(bmaps.data(), bmaps.size() * sizeof(CUtensorMap));
     if (batch_pair && nmaj && o.bn == 256) to_pair(o, bleaves);  // B maps do not depend on the width
+    if (in_gemm) {
+        o.pack = true;
+        o.njobs = (int)packs.size();
+        o.tiles = pack_tiles;
+        o.jobs_off = put_blob(packs.data(), packs.size() * sizeof(CopyJob));
+    }
     batch = false;  // the combined op itself is emitted normally
-    emit_grouped(o, bleaves, btargets, 0);
+    emit_grouped(o, bleaves, btargets, in_gemm ? (int)packs.size() : 0);  // in_gemm: one counter per job
     return true;
 }
 

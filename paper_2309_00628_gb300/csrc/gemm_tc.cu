@@ -18,7 +18,8 @@
 //    k-step (B N-major).
 // Products accumulate in FP32 in tensor memory.
 //
-// CTA = 6 warps, persistent over work items (one item = one BM x BN output tile of one leaf):
+// CTA = 6 warps (10 when the launch packs operands: warps 6..9 copy them), persistent over work
+// items (one item = one BM x BN output tile of one leaf):
 //   warp 0      TMA producer: the A tile(s) and B tile(s) of one k-block per stage
 //   warp 1      TMEM allocator + MMA issuer (one thread)
 //   warps 2..5  epilogue: tcgen05.ld 32 columns at a time; each warp stages its 32 x 32 chunk
@@ -52,7 +53,10 @@ constexpr int TF_GROUP_M = 24;
 // with the 32-byte-atom 128-byte swizzle, read by the MMA through a layout-type-1 descriptor.
 // MODE_TF32X3: compensated TF32 -- each FP32 operand arrives as (hi, lo) FP32 halves, hi = tf32(x),
 // lo = x - hi; per k-step three MMAs lo*hi + hi*lo + hi*hi (A K-major, B N-major as in TF32N).
-constexpr int MODE_TF32 = 0, MODE_BF16X3 = 1, MODE_TF32N = 2, MODE_TF32X3 = 3;
+// MODE_TF32N_PACK: TF32N on CTA pairs whose launch also packs operands (batched products whose
+// rows are not 16-byte aligned): four more warps per CTA copy the launch's pack jobs, tile by
+// tile in job order, while the tiles of earlier products run.
+constexpr int MODE_TF32 = 0, MODE_BF16X3 = 1, MODE_TF32N = 2, MODE_TF32X3 = 3, MODE_TF32N_PACK = 4;
 constexpr uint32_t SWZ_128B_BASE32B = 1;  // descriptor layout: 128-byte swizzle, 32-byte atoms
 
 // PAIR: the TF32 form for a CTA pair (cta_group::2): one 256 x BN tile per pair, each CTA holding
@@ -61,13 +65,15 @@ constexpr uint32_t SWZ_128B_BASE32B = 1;  // descriptor layout: 128-byte swizzle
 template <int MODE, int BN, bool PAIR = false>
 struct TfCfg {
     static constexpr bool TF = MODE != MODE_BF16X3;                  // a TF32 form
-    static constexpr bool BN_MAJOR32 = MODE == MODE_TF32N || MODE == MODE_TF32X3;  // B N-major, 32-bit
+    static constexpr bool NMAJ = MODE == MODE_TF32N || MODE == MODE_TF32N_PACK;  // TF32 with B N-major
+    static constexpr bool PACK = MODE == MODE_TF32N_PACK;
+    static constexpr bool BN_MAJOR32 = NMAJ || MODE == MODE_TF32X3;  // B N-major, 32-bit
     static constexpr int BK = TF ? 32 : 64;                          // elements per 128-byte row
     static constexpr int TM = PAIR ? 2 * TF_BM : TF_BM;              // tile rows per work item
     static constexpr int B_ROWS = PAIR ? BN / 2 : BN;                // B rows held by one CTA
     static constexpr int A_BYTES = TF_BM * 128;                      // one A tile (16 KB)
     static constexpr int B_BYTES = B_ROWS * 128;                     // one B tile
-    static constexpr int NOPS = (MODE == MODE_TF32 || MODE == MODE_TF32N) ? 1 : 2;  // tiles per operand (hi, lo)
+    static constexpr int NOPS = (MODE == MODE_TF32 || NMAJ) ? 1 : 2;  // tiles per operand (hi, lo)
     static constexpr int STAGE_BYTES = NOPS * (A_BYTES + B_BYTES);
     static constexpr int STAGES = (4 * 49152) / STAGE_BYTES;         // 192 KB of operand stages
     // BN = 512 (TF32 N-major on CTA pairs): a 256 x 512 tile as two N = 256 MMAs per k step into
@@ -77,6 +83,8 @@ struct TfCfg {
     static constexpr int MMA_N = BN > 256 ? 256 : BN;                 // N of one MMA
     static constexpr int NACC = BN > 256 ? 1 : 2;                     // TMEM accumulators (512 columns)
     static constexpr int TMEM_COLS = NACC * BN;
+    static constexpr int PACK_WARPS = 4;
+    static constexpr int THREADS = PACK ? 192 + 32 * PACK_WARPS : 192;  // warps 6..: the packing warps
     static constexpr int STG_OFF = STAGES * STAGE_BYTES;      // epilogue staging: 4 warps x 2 x 4 KB
     static constexpr int STG_BYTES = 4 * 2 * 4096;
     static constexpr int BAR_OFF = STG_OFF + STG_BYTES;
@@ -213,13 +221,14 @@ __device__ __forceinline__ void store_chunk32(const Target& t, int row_w, int co
 }
 
 template <int MODE, int BN, bool RES, bool PAIR>
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(TfCfg<MODE, BN, PAIR>::THREADS, 1)
     gemm_tc_kernel(const __grid_constant__ MapSet maps, const CUtensorMap* __restrict__ gmaps,
                      const Leaf* __restrict__ leaves, int nleaves, const Target* __restrict__ targets,
                      const CUtensorMap* __restrict__ tmaps, unsigned* __restrict__ flags,
                      int total_items, int* err, const ResidentCtl ctl) {
     static_assert(!PAIR || (MODE != MODE_TF32X3 && !RES), "CTA pairs: TF32 / split-BF16, non-resident only");
     using Cfg = TfCfg<MODE, BN, PAIR>;
+    static_assert(!Cfg::PACK || (PAIR && !RES && BN == 256), "packing launches: 256 x 256 CTA-pair tiles");
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw_addr = smem_u32(smem_raw);
     const uint32_t base_addr = (raw_addr + 1023u) & ~1023u;
@@ -323,6 +332,13 @@ __global__ void __launch_bounds__(192, 1)
                 const int b_col = __ldg(&L->b_col) +
                                   (MODE == MODE_TF32 ? 0 : ip.tn * BN + (int)rank * (Cfg::B_ROWS < 128 ? Cfg::B_ROWS : 128));
                 const int kb_n = __ldg(&L->kblocks);
+                if (Cfg::PACK) {  // operands packed in this launch: their tiles are complete first
+                    const int ja = __ldg(&L->a_job), jb = __ldg(&L->b_job);
+                    if (ja >= 0) ok &= wait_counter(ctr + ja, epoch * (unsigned)ctl.pack_jobs[ja].pad_, err, ERR_ORDER);
+                    if (jb >= 0) ok &= wait_counter(ctr + jb, epoch * (unsigned)ctl.pack_jobs[jb].pad_, err, ERR_ORDER);
+                    fence_async_global();  // the packing warps' stores -> this CTA's TMA loads
+                    if (!ok) break;
+                }
                 // TMA x coordinates must be 16-byte aligned (4 FP32 / 8 BF16 elements)
                 if (((a_col | b_col) & (Cfg::TF ? 3 : 7)) != 0) {
                     set_error(err, ERR_ALIGN);
@@ -359,7 +375,7 @@ __global__ void __launch_bounds__(192, 1)
                         }
                         tma_load_2d_pair(stage_a(stage, 0), pick_map(maps, gmaps, am), fb, a_col + kb * Cfg::BK,
                                          a_row);
-                        if (MODE == MODE_TF32N) {
+                        if (Cfg::NMAJ) {
 #pragma unroll
                             for (int c = 0; c < Cfg::B_ROWS / 32; ++c)  // 32 N-columns x 32 K-rows per box
                                 tma_load_2d_pair(stage_b(stage, 0) + c * 4096, pick_map(maps, gmaps, bm), fb,
@@ -404,6 +420,74 @@ __global__ void __launch_bounds__(192, 1)
             for (int i = 0; i < min(issued, Cfg::STAGES); ++i) {
                 if (--s < 0) { s = Cfg::STAGES - 1; ph ^= 1u; }
                 mbar_wait(PAIR ? &empty[s] : &full[s], ph, err, ERR_WAIT_DRAIN);
+            }
+        }
+    } else if (Cfg::PACK && warp >= 6) {
+        // ------------------------------------------------------------ operand packing
+        // Every packing warp of the launch takes chunks of PCH consecutive pack tiles, round robin
+        // in job order (the launch's item order, so the tiles the first items wait for come first),
+        // walking the jobs forward as its tile index grows.  A 64 x 64 tile in two passes of 32
+        // rows x 64 columns (lane = column c0 + lane and c0 + lane + 32: 128-byte runs), all 64
+        // loads of a pass before its stores.  After a chunk its stores are fenced for the async
+        // proxy (TMA reads them) and lane 0 counts its tiles on their jobs' counters.
+        constexpr int PCH = 8;
+        const int gw = (int)blockIdx.x * Cfg::PACK_WARPS + (warp - 6), nw = (int)gridDim.x * Cfg::PACK_WARPS;
+        int lo = 0;
+        CopyJob J;
+        J.tile_begin = -1;
+        for (int t0 = gw * PCH; t0 < ctl.pack_tiles; t0 += nw * PCH) {
+            const int t1 = min(t0 + PCH, ctl.pack_tiles);
+            int first_job = -1, n_first = 0;  // the job whose tiles this chunk has done, and how many
+#pragma unroll 1
+            for (int t = t0; t < t1; ++t) {
+                while (lo + 1 < ctl.pack_njobs && __ldg(&ctl.pack_jobs[lo + 1].tile_begin) <= t) {
+                    ++lo;
+                    if (first_job >= 0 && lo != first_job) {  // count what is done so far
+                        fence_async_global();
+                        __syncwarp();
+                        if (lane == 0) {
+                            __threadfence();
+                            red_release_add_u32(ctr + first_job, (unsigned)n_first);
+                        }
+                        first_job = -1;
+                        n_first = 0;
+                    }
+                }
+                if (J.tile_begin != __ldg(&ctl.pack_jobs[lo].tile_begin)) J = ctl.pack_jobs[lo];  // increasing
+                if (first_job < 0) first_job = lo;
+                const int lt = t - J.tile_begin;
+                const int tiles_c = (J.out_cols + 63) / 64;
+                const int r0 = (lt / tiles_c) * 64, c0 = (lt % tiles_c) * 64 + lane;
+                const float* x = static_cast<const float*>(J.x);
+                float* out = static_cast<float*>(J.out);
+#pragma unroll 1
+                for (int half = 0; half < 2; ++half) {
+                    const int rb = r0 + half * 32;
+                    float v[2][32];
+#pragma unroll
+                    for (int p = 0; p < 32; ++p)
+#pragma unroll
+                        for (int u = 0; u < 2; ++u) {
+                            const int r = rb + p, c = c0 + 32 * u;
+                            v[u][p] = (r < J.src_rows && c < J.src_cols) ? __ldcs(x + (long long)r * J.ldx + c) : 0.f;
+                        }
+#pragma unroll
+                    for (int p = 0; p < 32; ++p)
+#pragma unroll
+                        for (int u = 0; u < 2; ++u) {
+                            const int r = rb + p, c = c0 + 32 * u;
+                            if (r < J.out_rows && c < J.out_cols) out[(long long)r * J.ldo + c] = v[u][p];
+                        }
+                }
+                ++n_first;
+            }
+            if (first_job >= 0) {
+                fence_async_global();
+                __syncwarp();
+                if (lane == 0) {
+                    __threadfence();
+                    red_release_add_u32(ctr + first_job, (unsigned)n_first);
+                }
             }
         }
     } else if (warp == 1) {
@@ -458,7 +542,7 @@ __global__ void __launch_bounds__(192, 1)
                             const uint64_t ad = make_sdesc(a_addr + kk * 32, 16, 1024, SWZ_128B);
                             // TF32N: 8 K-rows of 128 bytes per step, read as two 4-row groups
                             // 512 bytes apart; 32-column chunks 4 KB apart
-                            const uint64_t bd = MODE == MODE_TF32N
+                            const uint64_t bd = Cfg::NMAJ
                                                     ? make_sdesc(b_addr + kk * 1024, 4096, 512, SWZ_128B_BASE32B)
                                                     : make_sdesc(b_addr + kk * 32, 16, 1024, SWZ_128B);
                             const uint32_t accum = ((kb | kk) != 0 ? 1u : 0u) | cont;
@@ -744,7 +828,7 @@ static cudaError_t tc_setup(int* pairs_out) {
             at[0].val.clusterDim.y = 1;
             at[0].val.clusterDim.z = 1;
             q.gridDim = dim3(2 * 1024, 1, 1);
-            q.blockDim = dim3(192, 1, 1);
+            q.blockDim = dim3(Cfg::THREADS, 1, 1);
             q.dynamicSmemBytes = Cfg::SMEM_BYTES;
             q.attrs = at;
             q.numAttrs = 1;
@@ -763,7 +847,8 @@ static cudaError_t launch_tc_impl(const MapSet& maps, const CUtensorMap* gmaps, 
                                   const Target* targets, const CUtensorMap* tmaps, unsigned* flags,
                                   int total_items, int* err, int grid, cudaStream_t stream,
                                   const ResidentCtl* ctl = nullptr, const int* item_leaf = nullptr,
-                                  const int* item_tile = nullptr, int units = 0) {
+                                  const int* item_tile = nullptr, int units = 0, const CopyJob* pack_jobs = nullptr,
+                                  int pack_njobs = 0, int pack_tiles = 0) {
     using Cfg = TfCfg<MODE, BN, PAIR>;
     static_assert(Cfg::SMEM_BYTES <= 232448, "shared memory budget");
     auto kern = gemm_tc_kernel<MODE, BN, RES, PAIR>;
@@ -780,6 +865,9 @@ static cudaError_t launch_tc_impl(const MapSet& maps, const CUtensorMap* gmaps, 
         c.item_leaf = item_leaf;  // optional item -> leaf table (nullptr: binary search)
         c.item_tile = item_tile;  // optional explicit layout, planned for `units` units
         c.units = units;
+        c.pack_jobs = pack_jobs;
+        c.pack_njobs = pack_njobs;
+        c.pack_tiles = pack_tiles;
         if (PAIR) grid = std::min(grid / 2, max_pairs);
         if (grid > total_items) grid = total_items;
         if (grid < 1) grid = 1;
@@ -793,7 +881,7 @@ static cudaError_t launch_tc_impl(const MapSet& maps, const CUtensorMap* gmaps, 
         at[0].val.clusterDim.y = 1;
         at[0].val.clusterDim.z = 1;
         cfg.gridDim = dim3(2 * grid, 1, 1);
-        cfg.blockDim = dim3(192, 1, 1);
+        cfg.blockDim = dim3(Cfg::THREADS, 1, 1);
         cfg.dynamicSmemBytes = Cfg::SMEM_BYTES;
         cfg.stream = stream;
         cfg.attrs = at;
@@ -803,7 +891,7 @@ static cudaError_t launch_tc_impl(const MapSet& maps, const CUtensorMap* gmaps, 
         if (e != cudaSuccess) return e;
         return cudaGetLastError();
     }
-    kern<<<grid, 192, Cfg::SMEM_BYTES, stream>>>(maps, gmaps, leaves, nleaves, targets, tmaps, flags,
+    kern<<<grid, Cfg::THREADS, Cfg::SMEM_BYTES, stream>>>(maps, gmaps, leaves, nleaves, targets, tmaps, flags,
                                                  total_items, err, c);
     return cudaGetLastError();
 }
@@ -852,6 +940,18 @@ cudaError_t launch_gemm_tf32n(int bn, const MapSet& maps, const CUtensorMap* gma
                                                total_items, err, grid, stream, nullptr, item_leaf, item_tile, units);
     return launch_tc_impl<MODE_TF32N, 128>(maps, gmaps, leaves, nleaves, targets, tmaps, flags, total_items,
                                            err, grid, stream, nullptr, item_leaf, item_tile, units);
+}
+
+cudaError_t launch_gemm_tf32n_pack(const CUtensorMap* gmaps, const Leaf* leaves, int nleaves, const Target* targets,
+                                   const CUtensorMap* tmaps, unsigned* flags, int total_items, int* err, int grid,
+                                   cudaStream_t stream, const int* item_leaf, const CopyJob* jobs, int njobs,
+                                   int pack_tiles) {
+    if (!flags || !jobs || njobs <= 0) return cudaErrorInvalidValue;  // the jobs' counters live in flags
+    MapSet none;
+    memset(&none, 0, sizeof(none));
+    return launch_tc_impl<MODE_TF32N_PACK, 256, false, true>(none, gmaps, leaves, nleaves, targets, tmaps, flags,
+                                                             total_items, err, grid, stream, nullptr, item_leaf,
+                                                             nullptr, 0, jobs, njobs, pack_tiles);
 }
 
 int gemm_tf32n_pair_units(int sms, int bn) {

@@ -71,6 +71,7 @@ struct Op {
     size_t item_tile_off = 0;
     int units = 0;               // the layout's persistent units
     bool nmaj = false;           // TF32 GEMM reading B N-major (launch_gemm_tf32n)
+    bool pack = false;           // batched TF32N pair GEMM that also runs the pack jobs at jobs_off
     size_t item_leaf_off = 0;
     size_t leaves_off = 0, targets_off = 0, refs_off = 0, tmaps_off = 0, flags_off = 0;
     int ngmaps = 0, njobs = 0, tiles = 0, transpose = 0;
@@ -163,7 +164,7 @@ sw_status build_plan(sw_handle h, int eb, const void* A, int lda, const void* B,
                      char* b_sums = nullptr);
 // Plan of a batch of FP32 products in one grouped launch (planner.cu)
 sw_status build_batched_plan(sw_handle h, int count, const sw_problem* probs, int cutoff, uint32_t variant, bool dry,
-                             Plan* plan, int bn = 256, bool pair = false);
+                             Plan* plan, int bn = 256, bool pair = false, bool pack = false);
 // Launch ops [first, last) of a plan on `s`.
 sw_status run_ops(sw_handle h, Plan* plan, cudaStream_t s, size_t first, size_t last);
 sw_status run_plan(sw_handle h, Plan* plan, cudaStream_t s);

@@ -34,6 +34,13 @@ cudaError_t launch_gemm_tf32(int bn, const MapSet& maps, const CUtensorMap* gmap
                              const Target* targets, const CUtensorMap* tmaps, unsigned* flags,
                              int total_items, int* err, int grid, cudaStream_t stream, bool pair = false,
                              const int* item_leaf = nullptr);
+// The batched TF32N CTA-pair launch that also packs operands: jobs[0..njobs) (CopyJob::pad_ = its
+// tile count of BCOPY_TILE x BCOPY_TILE, tile_begin its first tile of pack_tiles) write the packed
+// copies its leaves' maps read; flags holds the launch epoch and one counter per job.
+cudaError_t launch_gemm_tf32n_pack(const CUtensorMap* gmaps, const Leaf* leaves, int nleaves, const Target* targets,
+                                   const CUtensorMap* tmaps, unsigned* flags, int total_items, int* err, int grid,
+                                   cudaStream_t stream, const int* item_leaf, const CopyJob* jobs, int njobs,
+                                   int pack_tiles);
 // TF32 leaves with B N-major (k x n as stored; maps from make_map_f32_n, Leaf::b_row = K,
 // Leaf::b_col = N); otherwise as launch_gemm_tf32.  bn = 512 (CTA pairs only): 256 x 512 tiles with
 // one TMEM accumulator.
@@ -165,7 +172,7 @@ struct CopyJob {
     void* out;
     long long ldo;
     int src_rows, src_cols, out_rows, out_cols;
-    int tile_begin, pad_;
+    int tile_begin, pad_;  // pad_: the job's tile count where a GEMM launch packs (else unused)
 };
 cudaError_t launch_batched_copy(const CopyJob* jobs, int njobs, int total_tiles, int transpose, cudaStream_t s);
 

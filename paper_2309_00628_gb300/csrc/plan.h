@@ -61,8 +61,12 @@ struct Leaf {
                          //    the same TMEM accumulator (two items back with two accumulators, the
                          //    previous item with one); an accumulation chain, which needs an
                          //    explicit item table (see ResidentCtl)
-    int pad_[2];
+    int a_job, b_job;    // launches that pack operands themselves (ResidentCtl::pack_jobs): the
+                         // jobs writing this leaf's A / B, whose tiles must be complete before its
+                         // loads (-1: none); read by no other launch
 };
+
+struct CopyJob;
 
 // Work source of the resident (serving) form of the grouped GEMM: items are published by the
 // host while the kernel runs.  `published` and `stop` live in host-mapped memory; each CTA claims
@@ -80,6 +84,11 @@ struct ResidentCtl {
     // (CTAs, or CTA pairs) so that unit u processes items u, u + units, ... in order.
     const int* item_tile;
     int units;
+    // Non-resident batched launches may also pack operands: extra warps copy the tiles of
+    // pack_jobs (CopyJob::pad_ = the job's tile count) and count each finished tile on the job's
+    // ordering counter, which a leaf's producer waits for (Leaf::a_job / b_job).
+    const CopyJob* pack_jobs;
+    int pack_njobs, pack_tiles;
 };
 
 }  // namespace swk

@@ -625,10 +625,11 @@ sw_status build_plan(sw_handle h, int eb, const void* A, int lda, const void* B,
 }
 
 sw_status build_batched_plan(sw_handle h, int count, const sw_problem* probs, int cutoff, uint32_t variant,
-                                    bool dry, Plan* plan, int bn, bool pair) {
+                                    bool dry, Plan* plan, int bn, bool pair, bool pack) {
     Planner P;
     P.batch_bn = bn;
     P.batch_pair = pair;
+    P.pack_in_gemm = pack;
     P.eb = 4;
     P.bf = false;
     P.nmaj = !tf32_bt_form();

@@ -53,6 +53,9 @@ struct Planner {
     int sms = 0;              // SMs of the device (explicit work layouts are planned for its units)
     int batch_bn = 256;       // batched launch: tile width of the grouped GEMM (128 or 256)
     bool batch_pair = false;  // batched launch: CTA-pair form (256 x 256 tiles; N-major B only)
+    // batched launch in the CTA-pair form, no recursion: the GEMM launch runs the packing copies
+    // itself (each leaf's loads wait for its operands' pack jobs) instead of a copy launch before it
+    bool pack_in_gemm = false;
     // The CTA-pair GEMM (cta_group::2; TF32 and split-BF16 leaves) serves single products with
     // 256-wide tiles; batched and serving launches keep the one-CTA form unless told otherwise.
     // SWMM_NO_PAIR=1 disables it (diagnostics).

@@ -1,6 +1,9 @@
 // runtime.cu -- the handle's workspace, plan execution (eager or through a captured CUDA graph),
 // the plan cache, the autotuner (cutoff <= 0), single and batched products, and the host-operand
 // row-panel pipeline.
+#include <cstdlib>
+#include <cstring>
+
 #include "host.h"
 
 namespace swh {
@@ -73,10 +76,14 @@ sw_status run_ops(sw_handle h, Plan* plan, cudaStream_t s, size_t first, size_t 
                 const int* il = (o.has_item_leaf || o.has_layout) ? reinterpret_cast<const int*>(blob + o.item_leaf_off)
                                                                   : nullptr;
                 const int* it = o.has_layout ? reinterpret_cast<const int*>(blob + o.item_tile_off) : nullptr;
-                e = o.nmaj ? launch_gemm_tf32n(o.bn, o.maps, gm, lv, o.nleaves, tv, tm, fl, o.items, h->d_err, h->sms,
-                                               s, o.pair, il, it, o.units)
-                           : launch_gemm_tf32(o.bn, o.maps, gm, lv, o.nleaves, tv, tm, fl, o.items, h->d_err,
-                                              h->sms, s, o.pair, il);
+                if (o.pack)
+                    e = launch_gemm_tf32n_pack(gm, lv, o.nleaves, tv, tm, fl, o.items, h->d_err, h->sms, s, il,
+                                               reinterpret_cast<const CopyJob*>(blob + o.jobs_off), o.njobs, o.tiles);
+                else
+                    e = o.nmaj ? launch_gemm_tf32n(o.bn, o.maps, gm, lv, o.nleaves, tv, tm, fl, o.items, h->d_err,
+                                                   h->sms, s, o.pair, il, it, o.units)
+                               : launch_gemm_tf32(o.bn, o.maps, gm, lv, o.nleaves, tv, tm, fl, o.items, h->d_err,
+                                                  h->sms, s, o.pair, il);
             }
                 break;
             case OP_GEMM_SIMT:
@@ -384,18 +391,26 @@ sw_status do_batched(sw_handle h, int count, const sw_problem* probs, int cutoff
     // plan key: the problem list's bytes
     std::string key = "B|" + std::to_string(count) + "|" + std::to_string(cutoff) + "|" + std::to_string(variant) + "|";
     key.append(reinterpret_cast<const char*>(probs), sizeof(sw_problem) * (size_t)count);
-    struct Cfg { int bn, pair, cutoff; };
+    struct Cfg { int bn, pair, cutoff; };  // pair 2: CTA pairs packing operands inside the GEMM launch
     auto builder = [=](Cfg c) {
         return PlanBuilder([=](bool dry, Plan* p) {
-            return build_batched_plan(h, count, probs, c.cutoff, variant, dry, p, c.bn, c.pair != 0);
+            return build_batched_plan(h, count, probs, c.cutoff, variant, dry, p, c.bn, c.pair != 0, c.pair == 2);
         });
     };
     auto key_of = [&](Cfg c) {
         return key + "|" + std::to_string(c.bn) + "|" + std::to_string(c.pair) + "|" + std::to_string(c.cutoff);
     };
-    Cfg cfg = {256, 0, cutoff};
+    // a given cutoff: CTA pairs, packing inside the GEMM launch where no product recurses (the
+    // autotuner's pick on the uneven 512-product workload); SWMM_BATCH_FORM = cta | pair | pack
+    // selects a form (diagnostics and tests)
+    static const int form = [] {
+        const char* e = getenv("SWMM_BATCH_FORM");
+        return !e ? 2 : !strcmp(e, "cta") ? 0 : !strcmp(e, "pair") ? 1 : 2;
+    }();
+    Cfg cfg = {256, tf32_bt_form() ? 0 : form, cutoff};
     // cutoff <= 0: the autotuner times the grouped launch's tile shape (128- or 256-wide tiles on one
-    // CTA, 256 x 256 tiles on CTA pairs) and the recursion cutoff on this problem list, once
+    // CTA, 256 x 256 tiles on CTA pairs, with the packing copies before the GEMM launch or inside it)
+    // and the recursion cutoff on this problem list, once
     if (cutoff <= 0 && !capturing(s)) {
         auto t = h->tuned.find(key);
         if (t != h->tuned.end()) {
@@ -406,6 +421,7 @@ sw_status do_batched(sw_handle h, int count, const sw_problem* probs, int cutoff
             if (!tf32_bt_form()) {     // CTA pairs need N-major B
                 cs.push_back({256, 1, none});
                 cs.push_back({256, 1, 2048});
+                cs.push_back({256, 2, none});
             }
             std::vector<PlanBuilder> cands;
             for (const Cfg& c : cs) cands.push_back(builder(c));

@@ -66,6 +66,49 @@ def test_batched_integers_bit_exact(h, cutoff):
         assert np.array_equal(C, oracle.naive(A.astype(np.float64), B.astype(np.float64))), (m, n, k, cutoff)
 
 
+_FORM_SCRIPT = r"""
+import sys
+import numpy as np, torch
+sys.path[:0] = [sys.argv[1], sys.argv[1] + "/tests"]
+import oracle
+from paper_2309_00628_gb300 import inputs, swmm
+from test_gpu_batched import SHAPES, make_batch, run_batch
+swmm.load()
+h = swmm.sw_create(0)
+for cutoff in (100000, 128):
+    probs, host, keep = make_batch(SHAPES, "int", seed=5, lim=2, pad_lda=True)
+    run_batch(h, probs, cutoff)
+    for (A, B), (dA, dB, dC), (m, n, k) in zip(host, keep, SHAPES):
+        if m and n:
+            C = dC[:m, :n].double().cpu().numpy()
+            assert np.array_equal(C, oracle.naive(A.astype(np.float64), B.astype(np.float64))), (m, n, k, cutoff)
+    run_batch(h, probs, cutoff)  # the captured graph once more: the in-launch pack counters advance
+    for (A, B), (dA, dB, dC), (m, n, k) in zip(host, keep, SHAPES):
+        if m and n:
+            assert np.array_equal(dC[:m, :n].double().cpu().numpy(),
+                                  oracle.naive(A.astype(np.float64), B.astype(np.float64))), (m, n, k, cutoff)
+swmm.sw_destroy(h)
+print("forms ok")
+"""
+
+
+@pytest.mark.parametrize("form", ["cta", "pair", "pack"])
+def test_batched_forms_integers_bit_exact(form):
+    # each form of the grouped launch (one CTA per tile; CTA pairs with a packing launch before
+    # the GEMM; CTA pairs packing inside the GEMM launch), selected per process, on integer batches
+    # with unaligned leading dimensions, flat (cutoff 100000) and recursive (cutoff 128)
+    import os
+    import subprocess
+    import sys
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, SWMM_BATCH_FORM=form)
+    r = subprocess.run([sys.executable, "-c", _FORM_SCRIPT, root], env=env, capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode == 0 and "forms ok" in r.stdout, r.stdout[-2000:] + r.stderr[-2000:]
+
+
 def test_batched_equals_solo_runs_and_replays(h):
     shapes = [(300, 500, 200), (129, 257, 33), (700, 700, 700), (97, 131, 203)]
     probs, host, keep = make_batch(shapes, "uniform", seed=10)
@@ -99,7 +142,7 @@ def test_batched_512_uneven_products(h):
     # the first call with cutoff 0 timed the grouped launch's shapes and cutoffs on this list
     st, t = swmm.sw_last_tuning(h)
     assert st == swmm.SW_OK
-    assert t["candidates"] == 4 and t["tile_n"] in (128, 256) and t["cta_pair"] in (0, 1) and t["ms"] > 0, t
+    assert t["candidates"] == 5 and t["tile_n"] in (128, 256) and t["cta_pair"] in (0, 1, 2) and t["ms"] > 0, t
     rng = np.random.Generator(np.random.PCG64(3))
     worst = 0.0
     for i, ((dA, dB, dC), (m, n, k)) in enumerate(zip(keep, shapes)):
