@@ -19,7 +19,10 @@ using namespace swh;
 // arrays of the resident kernel, which claims the published tiles one by one on its share of the
 // SMs; the request is complete when its counter reaches 4 per tile (one per epilogue warp).
 // Other plans (FP64, split-BF16 leaves, padded or peeled shapes) run whole on a side stream with
-// the SMs the resident kernel leaves free.
+// the SMs the resident kernel leaves free.  When the descriptor arrays are full the kernel is asked
+// to exit once it has claimed every published tile, and a new generation starts after it has; the
+// host thread never waits for that (the kernel may be queued behind long side-stream blocks), so
+// other requests keep starting and completing meanwhile.
 namespace {
 
 constexpr int SRV_SIDE = 4;                   // side streams: [0, SRV_SIDE / 2) high priority, the rest low
@@ -35,7 +38,8 @@ constexpr int SRV_MAX_TMAPS = 1 << 16;  // target tensor maps
 constexpr size_t SRV_BLOB_BYTES = 256u << 20;
 constexpr size_t SRV_ALIGN = 1024;
 
-enum ReqState { RQ_QUEUED = 0, RQ_PRE = 1, RQ_PUBLISHED = 2, RQ_DONE = 3 };
+// RQ_LAUNCH: planned, its ops being enqueued by the launcher thread; RQ_LFAIL: that failed.
+enum ReqState { RQ_QUEUED = 0, RQ_PRE = 1, RQ_PUBLISHED = 2, RQ_DONE = 3, RQ_LAUNCH = 4, RQ_LFAIL = 5 };
 
 struct ServerReq {
     uint64_t ticket = 0;
@@ -48,8 +52,11 @@ struct ServerReq {
     unsigned items = 0;   // resident tiles
     int state = RQ_QUEUED;
     cudaEvent_t ev = nullptr;
+    cudaStream_t stream = nullptr;  // its side stream
     sw_status status = SW_OK;
     std::string msg;
+    sw_status launch_status = SW_OK;  // set by the launcher thread
+    std::string launch_msg;
 };
 
 // The resident kernel's descriptors for one appended GEMM (indices already rebased).
@@ -64,6 +71,18 @@ struct AppendSet {
 
 struct Server {
     sw_handle_s shadow;  // planning errors and side-stream launches (grid: the SMs left free)
+    // Long requests' ops are enqueued by a launcher thread: a deep FP64 plan holds thousands of
+    // kernels, a launch into a full stream queue blocks until the GPU drains it, and this thread
+    // must keep starting and completing the other requests meanwhile.
+    sw_handle_s shadow_l;  // the launcher's copy of `shadow`
+    std::thread launcher;
+    std::mutex lmu;  // guards lq, lquit, lbusy
+    std::condition_variable lcv, lcv_idle;
+    std::deque<ServerReq*> lq;
+    bool lquit = false;
+    int lbusy = 0;
+    void launch_loop();
+    void launcher_drop_and_wait(std::vector<ServerReq*>* dropped);
     sw_server_cfg cfg{};
     int device = 0, sms = 0;
     std::thread thr;
@@ -85,6 +104,7 @@ struct Server {
     unsigned n_items = 0;
     int n_leaves = 0, n_targets = 0, n_maps = 0, n_tmaps = 0;
     bool res_launched = false;
+    bool stopping = false;  // the resident kernel was asked to exit (a new generation follows)
     // device memory
     char* arena_mem = nullptr;
     char* blob_mem = nullptr;
@@ -193,16 +213,20 @@ sw_status Server::init(sw_handle h, const sw_server_cfg* c, std::string* msg) {
     if (cudaMalloc(&ctl_d, ctl_bytes()) != cudaSuccess) return oom("the control words");
     if (cudaMemset(ctl_d, 0, ctl_bytes()) != cudaSuccess) return oom("the control words");
     shadow.d_err = err_d();
+    shadow_l.device = device;
+    shadow_l.sms = shadow.sms;
+    shadow_l.d_err = shadow.d_err;
     if (cudaHostAlloc(&poll_h, ctl_bytes(), cudaHostAllocDefault) != cudaSuccess) return oom("the poll buffer");
     if (cudaHostAlloc(&mapped_h, 256, cudaHostAllocMapped) != cudaSuccess) return oom("the mapped words");
     memset(mapped_h, 0, 256);
     if (cudaHostGetDevicePointer(reinterpret_cast<void**>(&mapped_d), mapped_h, 0) != cudaSuccess)
         return oom("the mapped words (device view)");
-    if (cudaStreamCreateWithFlags(&res_stream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&ctl_stream, cudaStreamNonBlocking) != cudaSuccess)
-        return oom("streams");
     int prio_low = 0, prio_high = 0;
     if (cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high) != cudaSuccess) return oom("stream priorities");
+    // the resident kernel's CTAs take SMs ahead of pending blocks of long side-stream work
+    if (cudaStreamCreateWithPriority(&res_stream, cudaStreamNonBlocking, prio_high) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&ctl_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return oom("streams");
     for (int i = 0; i < SRV_SIDE; ++i)
         if (cudaStreamCreateWithPriority(&side[i], cudaStreamNonBlocking, i < SRV_SIDE / 2 ? prio_high : prio_low) !=
             cudaSuccess)
@@ -254,6 +278,8 @@ void Server::complete(ServerReq* r, sw_status st, const std::string& msg) {
 
 // Fail every admitted request once no work of theirs can still be in flight.
 void Server::fail_all(sw_status st, const std::string& msg) {
+    std::vector<ServerReq*> dropped;  // never launched: completed below with the rest
+    launcher_drop_and_wait(&dropped);
     if (res_launched) {
         set_mapped(32, 1u);
         cudaEventSynchronize(res_ev);
@@ -318,6 +344,7 @@ void Server::start(ServerReq* r) {
     const int cls = work_ms < SRV_SHORT_MS ? 0 : 1;
     cudaStream_t s = side[cls * (SRV_SIDE / 2) + side_rr[cls]];
     side_rr[cls] = (side_rr[cls] + 1) % (SRV_SIDE / 2);
+    r->stream = s;
     if (!r->plan.blob.empty()) {
         const size_t nb = (size_t)round_up((long long)r->plan.blob.size(), 256);
         size_t off = 0;
@@ -325,19 +352,75 @@ void Server::start(ServerReq* r) {
         r->blob_off = off;
         r->blob_bytes = nb;
         r->plan.d_blob = blob_mem + off;
-        cudaMemcpyAsync(r->plan.d_blob, r->plan.blob.data(), r->plan.blob.size(), cudaMemcpyHostToDevice, s);
     }
     r->resident = resident_form(r->plan);
+    r->ev = take_event();
+    if (cls == 1) {  // long: the launcher thread enqueues it
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            r->state = RQ_LAUNCH;
+        }
+        {
+            std::lock_guard<std::mutex> lk(lmu);
+            lq.push_back(r);
+        }
+        lcv.notify_one();
+        return;
+    }
+    if (r->blob_bytes)
+        cudaMemcpyAsync(r->plan.d_blob, r->plan.blob.data(), r->plan.blob.size(), cudaMemcpyHostToDevice, s);
     st = run_ops(&shadow, &r->plan, s, 0, r->plan.ops.size() - (r->resident ? 1 : 0));
     if (st != SW_OK) {
         cudaStreamSynchronize(s);
         complete(r, st, shadow.last_error);
         return;
     }
-    r->ev = take_event();
     cudaEventRecord(r->ev, s);
     std::lock_guard<std::mutex> lk(mu);
     r->state = RQ_PRE;
+}
+
+// The launcher thread: enqueue a long request's ops (all but a resident GEMM) on its side stream,
+// record its event and hand it back in RQ_PRE (RQ_LFAIL if a launch failed).
+void Server::launch_loop() {
+    cudaSetDevice(device);
+    for (;;) {
+        ServerReq* r = nullptr;
+        {
+            std::unique_lock<std::mutex> lk(lmu);
+            lcv.wait(lk, [&] { return lquit || !lq.empty(); });
+            if (lq.empty()) break;
+            r = lq.front();
+            lq.pop_front();
+            ++lbusy;
+        }
+        if (r->blob_bytes)
+            cudaMemcpyAsync(r->plan.d_blob, r->plan.blob.data(), r->plan.blob.size(), cudaMemcpyHostToDevice,
+                            r->stream);
+        shadow_l.last_error.clear();
+        const sw_status st = run_ops(&shadow_l, &r->plan, r->stream, 0, r->plan.ops.size() - (r->resident ? 1 : 0));
+        if (st != SW_OK) cudaStreamSynchronize(r->stream);
+        else cudaEventRecord(r->ev, r->stream);
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            r->launch_status = st;
+            r->launch_msg = shadow_l.last_error;
+            r->state = st == SW_OK ? RQ_PRE : RQ_LFAIL;
+        }
+        {
+            std::lock_guard<std::mutex> lk(lmu);
+            --lbusy;
+        }
+        lcv_idle.notify_all();
+    }
+}
+
+// Take back the requests still waiting for the launcher and wait until it is idle.
+void Server::launcher_drop_and_wait(std::vector<ServerReq*>* dropped) {
+    std::unique_lock<std::mutex> lk(lmu);
+    for (ServerReq* r : lq) dropped->push_back(r);
+    lq.clear();
+    lcv_idle.wait(lk, [&] { return lbusy == 0; });
 }
 
 // Append the request's final GEMM to the resident descriptor arrays (fresh 128-byte lines, so
@@ -404,17 +487,22 @@ bool Server::append(ServerReq* r, bool* fits) {
 
 // One pass of the loop over admitted requests; returns whether anything moved.
 bool Server::step() {
-    std::vector<ServerReq*> ready, published;
-    for (ServerReq* r : active) {
-        if (r->state == RQ_PRE) {
-            const cudaError_t e = cudaEventQuery(r->ev);
-            if (e == cudaSuccess) ready.push_back(r);
-            else if (e != cudaErrorNotReady) { fatal(std::string("serving: ") + cudaGetErrorString(e)); return true; }
-        } else if (r->state == RQ_PUBLISHED) {
-            published.push_back(r);
+    std::vector<ServerReq*> pre, ready, published, lfail;
+    {
+        std::lock_guard<std::mutex> lk(mu);  // the launcher thread moves requests out of RQ_LAUNCH
+        for (ServerReq* r : active) {
+            if (r->state == RQ_PRE) pre.push_back(r);
+            else if (r->state == RQ_PUBLISHED) published.push_back(r);
+            else if (r->state == RQ_LFAIL) lfail.push_back(r);
         }
     }
-    if (ready.empty() && published.empty()) return false;
+    for (ServerReq* r : lfail) complete(r, r->launch_status, r->launch_msg);
+    for (ServerReq* r : pre) {
+        const cudaError_t e = cudaEventQuery(r->ev);
+        if (e == cudaSuccess) ready.push_back(r);
+        else if (e != cudaErrorNotReady) { fatal(std::string("serving: ") + cudaGetErrorString(e)); return true; }
+    }
+    if (ready.empty() && published.empty()) return !lfail.empty();
     // kernel state first, then the counters: after an exit the counters are final
     bool exited = false;
     if (res_launched) {
@@ -453,6 +541,10 @@ bool Server::step() {
             moved = true;
             continue;
         }
+        if (stopping) {  // the kernel may already have stopped claiming: wait for the next generation
+            deferred = true;
+            continue;
+        }
         bool fits = true;
         if (append(r, &fits)) {
             std::lock_guard<std::mutex> lk(mu);
@@ -467,15 +559,30 @@ bool Server::step() {
     }
     if (appended) publish();
     bool pending = false;
-    for (ServerReq* r : active) pending |= r->state == RQ_PUBLISHED;
-    if (pending) {
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        for (ServerReq* r : active) pending |= r->state == RQ_PUBLISHED;
+    }
+    if (stopping && !kernel_running()) {  // the old generation's kernel has exited
+        set_mapped(32, 0u);
+        stopping = false;
+        moved = true;
+    }
+    if (stopping) {
+        // its claimed tiles finish and report; requests keep starting meanwhile (no host wait:
+        // the kernel may still be queued behind long side-stream work)
+    } else if (pending) {
         if (!kernel_running()) {
             if (launch_resident() != SW_OK) { fatal("serving: resident kernel launch failed"); return true; }
             moved = true;
         }
     } else if (n_items > 0 && (deferred || !kernel_running())) {
-        stop_kernel();
-        reset_generation();
+        if (kernel_running()) {
+            set_mapped(32, 1u);  // exit once every published tile is claimed; reset when it has
+            stopping = true;
+        } else {
+            reset_generation();
+        }
         moved = true;
     }
     return moved;
@@ -537,6 +644,7 @@ sw_status sw_server_start(sw_handle h, const sw_server_cfg* cfg) {
         delete s;
         return server_fail(h, st, msg);
     }
+    s->launcher = std::thread(&Server::launch_loop, s);
     s->thr = std::thread(&Server::loop, s);
     h->server = s;
     return SW_OK;
@@ -623,6 +731,12 @@ sw_status sw_server_stop(sw_handle h) {
     }
     s->cv_work.notify_all();
     s->thr.join();  // drains: every submitted request completes first
+    {
+        std::lock_guard<std::mutex> lk(s->lmu);
+        s->lquit = true;
+    }
+    s->lcv.notify_all();
+    s->launcher.join();
     s->release_device();
     for (auto& kv : s->reqs) delete kv.second;
     s->reqs.clear();
