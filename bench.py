@@ -597,6 +597,23 @@ def main():
             tot, _, _, _ = timed(v, c, ks, W)
             depth_rows.append({"variant": lab, "ms": tot / ks, "eff_tflops": flop / (tot / ks / 1e3) / 1e12,
                                "err": row_err(v, c)})
+        # context: the vendor library's TF32 GEMM on the same operands (not part of the method)
+        tf32_prev = torch.backends.cuda.matmul.allow_tf32
+        torch.backends.cuda.matmul.allow_tf32 = True
+        with torch.cuda.stream(stream):
+            for _ in range(W):
+                torch.matmul(dA, dB, out=dC)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(ks):
+                torch.matmul(dA, dB, out=dC)
+            e1.record(stream)
+        stream.synchronize()
+        torch.backends.cuda.matmul.allow_tf32 = tf32_prev
+        ms_lib = e0.elapsed_time(e1) / ks
+        err_lib = float(np.max(np.abs(dC[idx].double().cpu().numpy() - R)) / (n * amax * bmax))
+        depth_rows.append({"variant": "cublas tf32 (torch, context)", "ms": ms_lib,
+                           "eff_tflops": flop / (ms_lib / 1e3) / 1e12, "err": err_lib})
         # the same sweep at n = 4096 (config 2's smaller size): its own seeded inputs and oracle rows
         n5 = n // 2
         A5, B5 = inputs.pair(n5, n5, n5, "uniform", seed=0, dtype=np.float32)

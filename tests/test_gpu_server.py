@@ -139,6 +139,31 @@ def test_server_mix_floats(srv, h):
             assert torch.equal(solo, dC), (m, n, k)
 
 
+def test_server_long_requests_beside_short_ones(srv):
+    """Requests estimated at 2 ms of work or more have their ops enqueued by the launcher thread
+    (deep FP64 plans hold thousands of kernels); two such FP64 products run beside short FP32 and
+    FP64 ones, every result bit-exact against the oracle on integer inputs."""
+    cases = [(1280, 1280, 1280, 8, 0, W | FUSED), (512, 512, 512, 4, 0, N), (300, 500, 200, 8, 64, W | FUSED),
+             (1536, 1152, 1280, 8, 0, W | FUSED), (1024, 768, 1024, 4, 256, W | FUSED), (640, 640, 640, 4, 0, W)]
+    for (m, n, k, eb, cutoff, var) in cases[:1] + cases[3:4]:
+        assert 2.0 * m * n * k / 1.5e9 >= 2.0  # long by the server's estimate (FP64 at 1.5 TFLOP/s)
+    probs = []
+    for i, (m, n, k, eb, cutoff, var) in enumerate(cases):
+        A, B, dA, dB, dC = device_problem(m, n, k, "int", seed=500 + 2 * i, eb=eb, lim=1)
+        probs.append((A, B, dA, dB, dC, req(dA, dB, dC, m, n, k, eb, cutoff, var)))
+    torch.cuda.synchronize()
+    tickets = []
+    for p in probs:
+        st, t = swmm.sw_server_submit(srv, p[5])
+        swmm.check(srv, st)
+        tickets.append(t)
+    for t in tickets:
+        swmm.check(srv, swmm.sw_server_wait(srv, t, -1))
+    for (m, n, k, eb, cutoff, var), (A, B, dA, dB, dC, _) in zip(cases, probs):
+        R = oracle.naive_mt(A.astype(np.float64), B.astype(np.float64))
+        assert np.array_equal(dC[:m, :n].cpu().numpy().astype(np.float64), R), (m, n, k, eb, hex(var))
+
+
 def test_server_budget_and_timeout(h):
     cfg = swmm.sw_server_cfg(0, 8, 64 << 20, 2000)
     swmm.check(h, swmm.sw_server_start(h, cfg))
