@@ -87,7 +87,7 @@ typedef enum {
     SW_EBUDGET = 3,       /* the request needs more workspace than the handle's budget */
     SW_ECUDA = 4,         /* a CUDA runtime / driver call failed */
     SW_ETIMEOUT = 5,      /* a bounded device-side wait expired (see sw_sync) */
-    SW_EUNSUPPORTED = 6   /* valid request this build does not implement (e.g. IN_PLACE, m != n) */
+    SW_EUNSUPPORTED = 6   /* valid request the library does not implement (e.g. IN_PLACE, m != n) */
 } sw_status;
 
 #define SW_ALGO_NAIVE 0x0u

@@ -26,8 +26,8 @@ not amplify (every leaf result carries the same mu), while the zero-mean part xi
 (E xi^2 <= 2 * 2^-20 / 3) is a random walk over the k terms that grows by sqrt(R) per level.
 With rho = sqrt(E a^2 E b^2) / (max|a| max|b|) and c_ij of RMS sqrt(k) E|ab|:
     tol = F z(N) 2^-10 rho sqrt(1 + (2/3) R^L) / sqrt(k) + 2^-20,
-F = 2.  The 2^-20 term allows for the FP32 accumulation of the tensor core.  Where SURVEY A10's
-fixed TF32 bound of 2e-4 applies (k >= 4096, L <= 2) the smaller of the two is used.
+F = 2.  The 2^-20 term allows for the FP32 accumulation of the tensor core.  Where the fixed TF32
+bound of 2e-4 set for these workloads applies (k >= 4096, L <= 2) the smaller of the two is used.
 
 Compensated leaves (split-BF16 and 3xTF32).  The operand split carries x to a relative error e
 (split-BF16: hi = bf16(x), lo = bf16(x - hi) and the dropped lo*lo term give a term error of
@@ -52,7 +52,7 @@ form a random walk over partial sums of RMS sqrt(j) RMS(st), so a leaf result er
 (u / sqrt(3)) k' RMS(s) RMS(t) / sqrt(2); over the leaves of the worst quadrant this grows by
 sqrt(R / 2) per level.  The operand sums add one rounding each (behaving like a term error).
     tol = F z(N) (u / sqrt(3)) rho (sqrt((R / 2)^L / 2) + sqrt(R^L / k)),  F = 4,
-and the benchmark spec bound 1e-13 is checked as well.
+and the fixed FP64 bound 1e-13 is checked as well.
 
 A result may be compared on sampled rows; N is then the number of compared elements.
 """
