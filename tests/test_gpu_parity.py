@@ -378,6 +378,43 @@ def test_full_size_sampled_rows(h, L):
     check_close(Cr, R, A, B, tol_tf32(Cr, A, B, L, v))
 
 
+@pytest.mark.parametrize("algo,L,leaf", [(S, 1, "tf32"), (S, 2, "tf32"), (K, 1, "tf32"), (K, 2, "tf32"),
+                                         (W, 1, "bf16x3")])
+def test_full_size_variants_sampled_rows(h, algo, L, leaf):
+    # the bench's other n = 8192 rows: Strassen and Knuth-form Winograd FUSED with TF32 leaves, and
+    # Winograd L1 with split-BF16 leaves, on the headline's operands
+    n = 8192
+    A, B = inputs.pair(n, n, n, "uniform", seed=0, dtype=np.float32)
+    v = algo | FUSED | (swmm.SW_LEAF_BF16X3 if leaf == "bf16x3" else 0)
+    cutoff = n >> L
+    assert depth(h, n, n, n, cutoff, v, 4) == L
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    C = swmm.mm(h, dA, dB, cutoff, v, sync=True)
+    rows = np.random.Generator(np.random.PCG64(97)).choice(n, 8, replace=False)
+    R = oracle.naive_mt(A[rows].astype(np.float64), B.astype(np.float64))
+    Cr = C[torch.from_numpy(rows).cuda()].cpu().numpy().astype(np.float64)
+    tol = tol_bf16x3(Cr, A, B, L, v) if leaf == "bf16x3" else tol_tf32(Cr, A, B, L, v)
+    check_close(Cr, R, A, B, tol)
+    del dA, dB, C
+
+
+@pytest.mark.parametrize("sched", [TWO, FUSED])
+def test_bf16x3_n16384_normal_depth1_sampled_rows(h, sched):
+    # config 3's other rows: split-BF16 leaves at n = 16384 on N(0, 1) operands, one level, with
+    # the Table 2 schedule and with the fused one; the FP32-accuracy bound 2e-6 holds
+    n, cutoff = 16384, 8192
+    v = W | sched | swmm.SW_LEAF_BF16X3
+    assert depth(h, n, n, n, cutoff, v, 4) == 1
+    A, B = inputs.pair(n, n, n, "normal", seed=0, dtype=np.float32)
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    C = swmm.mm(h, dA, dB, cutoff, v, sync=True)
+    rows = np.random.Generator(np.random.PCG64(96)).choice(n, 6, replace=False)
+    R = oracle.naive_mt(A[rows].astype(np.float64), B.astype(np.float64))
+    Cr = C[torch.from_numpy(rows).cuda()].cpu().numpy().astype(np.float64)
+    check_close(Cr, R, A, B, min(2e-6, tol_bf16x3(Cr, A, B, 1)))
+    del dA, dB, C
+
+
 # ------------------------------------------------------------------ split-BF16 leaves (hi*hi + hi*lo + lo*hi)
 # hi = bf16(x), lo = bf16(x - hi) carry x to a relative 2^-16, and the dropped lo*lo term is below
 # 2^-16 |a b|: each product term errs by < 3 * 2^-16 |a||b|, so the same Hoeffding argument as
