@@ -123,6 +123,11 @@ struct AddJob {
     const void* y;
     long long ldy;
     float sy;
+    // FP32 only, optional: z's bf16 halves hi = bf16(z), lo = bf16(z - hi) (leading dimension ldh),
+    // written in the same pass for split-BF16 leaves that read z next
+    void* zh = nullptr;
+    void* zl = nullptr;
+    long long ldh = 0;
 };
 cudaError_t launch_addsub2(int elem_bytes, const AddJob& a, const AddJob& b, cudaStream_t stream);
 

@@ -81,9 +81,17 @@ __device__ __forceinline__ void addsub_job(const AddJob& j, int block, int nbloc
     const T* x = static_cast<const T*>(j.x);
     const T* y = static_cast<const T*>(j.y);
     const T sy = (T)j.sy;
+    __nv_bfloat16* zh = static_cast<__nv_bfloat16*>(j.zh);
+    __nv_bfloat16* zl = static_cast<__nv_bfloat16*>(j.zl);
     for (long long e = block * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)nblocks * blockDim.x) {
         const int i = (int)(e / j.cols), c = (int)(e - (long long)i * j.cols);
-        z[i * j.ldz + c] = x[i * j.ldx + c] + sy * y[i * j.ldy + c];
+        const T v = x[i * j.ldx + c] + sy * y[i * j.ldy + c];
+        z[i * j.ldz + c] = v;
+        if (sizeof(T) == 4 && zh) {  // the split of split_bf16_kernel
+            const __nv_bfloat16 hv = __float2bfloat16_rn((float)v);
+            zh[i * j.ldh + c] = hv;
+            zl[i * j.ldh + c] = __float2bfloat16_rn((float)v - __bfloat162float(hv));
+        }
     }
 }
 
@@ -94,10 +102,27 @@ __device__ __forceinline__ void addsub4_job(const AddJob& j, int block, int nblo
     const float4* x = static_cast<const float4*>(j.x);
     const float4* y = static_cast<const float4*>(j.y);
     const long long ldz = j.ldz / 4, ldx = j.ldx / 4, ldy = j.ldy / 4;
+    uint2* zh = static_cast<uint2*>(j.zh);
+    uint2* zl = static_cast<uint2*>(j.zl);
+    const long long ldh = j.ldh / 4;
     for (long long e = block * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)nblocks * blockDim.x) {
         const int i = (int)(e / c4), c = (int)(e - (long long)i * c4);
         const float4 a = x[i * ldx + c], b = y[i * ldy + c];
-        z[i * ldz + c] = make_float4(a.x + j.sy * b.x, a.y + j.sy * b.y, a.z + j.sy * b.z, a.w + j.sy * b.w);
+        const float4 v = make_float4(a.x + j.sy * b.x, a.y + j.sy * b.y, a.z + j.sy * b.z, a.w + j.sy * b.w);
+        z[i * ldz + c] = v;
+        if (zh) {  // the split of split_bf16x4_kernel
+            const __nv_bfloat162 h01 = __floats2bfloat162_rn(v.x, v.y), h23 = __floats2bfloat162_rn(v.z, v.w);
+            const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
+            const __nv_bfloat162 l01 = __floats2bfloat162_rn(v.x - f01.x, v.y - f01.y);
+            const __nv_bfloat162 l23 = __floats2bfloat162_rn(v.z - f23.x, v.w - f23.y);
+            uint2 hh, ll;
+            hh.x = *reinterpret_cast<const unsigned*>(&h01);
+            hh.y = *reinterpret_cast<const unsigned*>(&h23);
+            ll.x = *reinterpret_cast<const unsigned*>(&l01);
+            ll.y = *reinterpret_cast<const unsigned*>(&l23);
+            zh[i * ldh + c] = hh;
+            zl[i * ldh + c] = ll;
+        }
     }
 }
 
@@ -113,24 +138,27 @@ __global__ void __launch_bounds__(256) addsub2_kernel(const AddJob a, const AddJ
 cudaError_t launch_addsub2(int elem_bytes, const AddJob& a, const AddJob& b, cudaStream_t stream) {
     const long long wa = (long long)std::max(a.rows, 0) * std::max(a.cols, 0);
     const long long wb = (long long)std::max(b.rows, 0) * std::max(b.cols, 0);
-    if (wa == 0 || wb == 0) {  // one job alone
+    const bool split = a.zh || b.zh;
+    if (split && elem_bytes != 4) return cudaErrorInvalidValue;
+    if ((wa == 0 || wb == 0) && !split) {  // one job alone
         const AddJob& j = wa ? a : b;
         return launch_addsub(elem_bytes, j.rows, j.cols, j.z, j.ldz, j.x, j.ldx, j.y, j.ldy, j.sy, stream);
     }
+    if (wa + wb == 0) return cudaSuccess;
     auto v4 = [](const AddJob& j) {
-        return ((j.cols | j.ldz | j.ldx | j.ldy) & 3) == 0 &&
-               ((reinterpret_cast<uintptr_t>(j.z) | reinterpret_cast<uintptr_t>(j.x) |
-                 reinterpret_cast<uintptr_t>(j.y)) & 15) == 0;
+        const long long w = (long long)std::max(j.rows, 0) * std::max(j.cols, 0);
+        return w == 0 ||
+               (((j.cols | j.ldz | j.ldx | j.ldy | (j.zh ? j.ldh : 0)) & 3) == 0 &&
+                ((reinterpret_cast<uintptr_t>(j.z) | reinterpret_cast<uintptr_t>(j.x) |
+                  reinterpret_cast<uintptr_t>(j.y)) & 15) == 0 &&
+                ((reinterpret_cast<uintptr_t>(j.zh) | reinterpret_cast<uintptr_t>(j.zl)) & 7) == 0);
     };
     const bool vec = elem_bytes == 4 && v4(a) && v4(b);
     const int per = vec ? 4 : 1;
-    const int g = grid_for((wa + wb) / per, 256);
-    const int ga = std::max(1, std::min(g - 1, (int)((g * wa + (wa + wb) / 2) / (wa + wb))));
-    if (g < 2) {
-        cudaError_t e = launch_addsub(elem_bytes, a.rows, a.cols, a.z, a.ldz, a.x, a.ldx, a.y, a.ldy, a.sy, stream);
-        return e != cudaSuccess ? e : launch_addsub(elem_bytes, b.rows, b.cols, b.z, b.ldz, b.x, b.ldx, b.y, b.ldy,
-                                                    b.sy, stream);
-    }
+    const int g = std::max(2, grid_for((wa + wb) / per, 256));
+    // blocks [0, ga) take job a; an empty job gets none
+    const int ga = wa == 0 ? 0 : wb == 0 ? g
+                 : std::max(1, std::min(g - 1, (int)((g * wa + (wa + wb) / 2) / (wa + wb))));
     if (elem_bytes == 8) addsub2_kernel<double, false><<<g, 256, 0, stream>>>(a, b, ga);
     else if (vec) addsub2_kernel<float, true><<<g, 256, 0, stream>>>(a, b, ga);
     else addsub2_kernel<float, false><<<g, 256, 0, stream>>>(a, b, ga);

@@ -92,9 +92,7 @@ bool Planner::gemm_split(View a, View b, View c, int mode) { return gemm_split_t
 bool Planner::simt(View a, View b, View c, int mode) { return simt_to(a, b, {Dest{c, 1.f, mode}}); }
 
 bool Planner::leaf_to(View a, View b, std::vector<Dest> d) {
-    // a block's first write stores, later ones add (the plan's launches run in order)
-    for (Dest& x : d)
-        if (x.mode < 0) x.mode = written.insert(std::make_tuple(x.c.p, x.c.rows, x.c.cols)).second ? TGT_STORE : TGT_ADD;
+    resolve_modes(d);
     if (eb == 8) return simt_to(a, b, d);
     if (bf || x3) return gemm_split_to(a, b, d);
     return gemm_to(a, b, d);
@@ -156,6 +154,14 @@ bool Planner::gemm_split_to(View a, View b, const std::vector<Dest>& d) {
     View ah, al, bh, bl;
     split(a, ah, al);
     split(b, bh, bl);
+    const bool ok = gemm_split_halves(a, ah, al, bh, bl, d);
+    ws_top = mark;
+    return ok;
+}
+
+bool Planner::gemm_split_halves(View a, View ah, View al, View bh, View bl, const std::vector<Dest>& d) {
+    const int rows = d[0].c.rows, cols = d[0].c.cols;
+    if (rows <= 0 || cols <= 0) return true;
     bool ok = true;
     if (!dry) {
         std::vector<Target> tv;
@@ -195,7 +201,6 @@ bool Planner::gemm_split_to(View a, View b, const std::vector<Dest>& d) {
         flush_tmaps(o);
         push(o);
     }
-    ws_top = mark;
     return ok;
 }
 
@@ -391,6 +396,45 @@ bool Planner::two_temp_folded(View a, View b, const std::vector<Dest>& d, int L)
     View X = talloc(m2, k2);
     View Y = tallocB(k2, n2);
     bool ok = true;
+    if (L == 1 && bf && !x3 && eb == 4 && k2 > 0) {
+        // split-BF16 leaves: every sum a leaf reads gets its bf16 halves from the sum launch itself
+        // (no split pass over X or Y); the halves live only while their leaf needs them, so the
+        // workspace peak stays at X, Y and one leaf's four halves
+        auto leaf = [&](View av, const View* ah, const View* al, View bv, const View* bh, const View* bl,
+                        std::vector<Dest> ds) {
+            resolve_modes(ds);
+            if (ds[0].c.rows <= 0 || ds[0].c.cols <= 0) return true;
+            const size_t mk = ws_top;
+            View a_h, a_l, b_h, b_l;
+            if (ah) { a_h = *ah; a_l = *al; } else split(av, a_h, a_l);
+            if (bh) { b_h = *bh; b_l = *bl; } else split(bv, b_h, b_l);
+            const bool r = gemm_split_halves(av, a_h, a_l, b_h, b_l, ds);
+            ws_top = mk;
+            return r;
+        };
+        const size_t mh = ws_top;
+        const View Xh = talloc_half(X.rows, X.cols), Xl = talloc_half(X.rows, X.cols);
+        const size_t mx = ws_top;
+        const View Yh = talloc_half(Y.rows, Y.cols), Yl = talloc_half(Y.rows, Y.cols);
+        add2(X, A11, A21, -1, Y, B22, B12, -1, &Xh, &Xl, &Yh, &Yl);        //  1,  2  S3, T3
+        ok &= leaf(X, &Xh, &Xl, Y, &Yh, &Yl, dest(6));                      //  3      P7
+        add2(X, A21, A22, +1, Y, B12, B11, -1, &Xh, &Xl, &Yh, &Yl);        //  4,  5  S1, T1
+        ok &= leaf(X, &Xh, &Xl, Y, &Yh, &Yl, dest(4));                      //  6      P5
+        add2(X, X, A11, -1, Y, B22, Y, -1, &Xh, &Xl, &Yh, &Yl);            //  7,  8  S2, T2
+        ok &= leaf(X, &Xh, &Xl, Y, &Yh, &Yl, dest(5));                      //  9      P6
+        ws_top = mx;                                                        // (T2's halves done)
+        add_split(X, A12, X, -1, Xh, Xl);                                   // 10      S4
+        ok &= leaf(X, &Xh, &Xl, B22, nullptr, nullptr, dest(2));            // 11      P3
+        ws_top = mh;
+        ok &= leaf(A11, nullptr, nullptr, B11, nullptr, nullptr, dest(0));  // 12      P1
+        const View Yh4 = talloc_half(Y.rows, Y.cols), Yl4 = talloc_half(Y.rows, Y.cols);
+        add_split(Y, Y, B21, -1, Yh4, Yl4);                                 // 18      T4
+        ok &= leaf(A22, nullptr, nullptr, Y, &Yh4, &Yl4, dest(3));          // 19      P4
+        ws_top = mh;
+        ok &= leaf(A12, nullptr, nullptr, B21, nullptr, nullptr, dest(1));  // 21      P2
+        ws_top = mark;
+        return ok;
+    }
     add2(X, A11, A21, -1, Y, B22, B12, -1);         //  1,  2  S3 -> X, T3 -> Y
     ok &= two_temp_folded(X, Y, dest(6), L - 1);    //  3      P7 = S3 T3
     add2(X, A21, A22, +1, Y, B12, B11, -1);         //  4,  5  S1 -> X, T1 -> Y

@@ -192,13 +192,30 @@ struct Planner {
         push(o);
     }
 
-    // two independent block additions (z1 = x1 + s1 y1, z2 = x2 + s2 y2) in one launch
-    void add2(View z1, View x1, View y1, float s1, View z2, View x2, View y2, float s2) {
+    // two independent block additions (z1 = x1 + s1 y1, z2 = x2 + s2 y2) in one launch; with
+    // halves (FP32, split-BF16 leaves next) each z's bf16 hi / lo halves are written as well
+    void add2(View z1, View x1, View y1, float s1, View z2, View x2, View y2, float s2,
+              const View* h1 = nullptr, const View* l1 = nullptr, const View* h2 = nullptr,
+              const View* l2 = nullptr) {
         Op o;
         o.kind = OP_ADDSUB2;
         o.eb = eb;
         o.job_a = {z1.rows, z1.cols, z1.p, z1.ld, x1.p, x1.ld, y1.p, y1.ld, s1};
         o.job_b = {z2.rows, z2.cols, z2.p, z2.ld, x2.p, x2.ld, y2.p, y2.ld, s2};
+        if (h1) { o.job_a.zh = h1->p; o.job_a.zl = l1->p; o.job_a.ldh = h1->ld; }
+        if (h2) { o.job_b.zh = h2->p; o.job_b.zl = l2->p; o.job_b.ldh = h2->ld; }
+        push(o);
+    }
+    // z = x + s y and z's bf16 halves in one pass (one job of the two-job launch)
+    void add_split(View z, View x, View y, float s, const View& hi, const View& lo) {
+        Op o;
+        o.kind = OP_ADDSUB2;
+        o.eb = eb;
+        o.job_a = {z.rows, z.cols, z.p, z.ld, x.p, x.ld, y.p, y.ld, s};
+        o.job_a.zh = hi.p;
+        o.job_a.zl = lo.p;
+        o.job_a.ldh = hi.ld;
+        o.job_b = {0, 0, nullptr, 0, nullptr, 0, nullptr, 0, 0.f};
         push(o);
     }
 
@@ -356,6 +373,14 @@ struct Planner {
     bool leaf_to(View a, View b, std::vector<Dest> d);
     bool gemm_to(View a, View b, const std::vector<Dest>& d);
     bool gemm_split_to(View a, View b, const std::vector<Dest>& d);
+    // the split leaf on halves made already (a, b: the FP32 operands' extents)
+    bool gemm_split_halves(View a, View ah, View al, View bh, View bl, const std::vector<Dest>& d);
+    // a block's first write stores, later ones add (the plan's launches run in order)
+    void resolve_modes(std::vector<Dest>& d) {
+        for (Dest& x : d)
+            if (x.mode < 0)
+                x.mode = written.insert(std::make_tuple(x.c.p, x.c.rows, x.c.cols)).second ? TGT_STORE : TGT_ADD;
+    }
     bool simt_to(View a, View b, const std::vector<Dest>& d);
     // Table 2 with its post-additions (steps 13-17, 20, 22) folded into the epilogues of the
     // products: each product adds +-P into the C blocks it feeds (used for the level just above
