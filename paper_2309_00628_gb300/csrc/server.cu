@@ -82,7 +82,7 @@ struct Server {
     bool lquit = false;
     int lbusy = 0;
     void launch_loop();
-    void launcher_drop_and_wait(std::vector<ServerReq*>* dropped);
+    void launcher_drop_and_wait();
     sw_server_cfg cfg{};
     int device = 0, sms = 0;
     std::thread thr;
@@ -278,8 +278,7 @@ void Server::complete(ServerReq* r, sw_status st, const std::string& msg) {
 
 // Fail every admitted request once no work of theirs can still be in flight.
 void Server::fail_all(sw_status st, const std::string& msg) {
-    std::vector<ServerReq*> dropped;  // never launched: completed below with the rest
-    launcher_drop_and_wait(&dropped);
+    launcher_drop_and_wait();  // requests it had not launched are completed below with the rest
     if (res_launched) {
         set_mapped(32, 1u);
         cudaEventSynchronize(res_ev);
@@ -415,10 +414,10 @@ void Server::launch_loop() {
     }
 }
 
-// Take back the requests still waiting for the launcher and wait until it is idle.
-void Server::launcher_drop_and_wait(std::vector<ServerReq*>* dropped) {
+// Drop the requests still waiting for the launcher (they stay in `active`, never launched) and
+// wait until the launcher is idle.
+void Server::launcher_drop_and_wait() {
     std::unique_lock<std::mutex> lk(lmu);
-    for (ServerReq* r : lq) dropped->push_back(r);
     lq.clear();
     lcv_idle.wait(lk, [&] { return lbusy == 0; });
 }
