@@ -64,3 +64,29 @@ def test_serving_latency_summaries():
     s = bench.latency_summary([0.004, 0.001, 0.002, 0.003])
     assert s["requests"] == 4 and s["p50_ms"] == 2.5 and s["p99_ms"] == 4.0
     assert bench.latency_summary([])["p50_ms"] is None
+
+
+def test_reference_arm_line_and_other_ranks():
+    # the reference arm times the FP64 oracle on the host's cores and prints the contract's line
+    # (a small n keeps it quick); under torchrun, ranks other than 0 exit 0 without a line
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    cmd = [sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--n", "512", "--steps", "1",
+           "--warmup", "3", "--cpu-seconds", "0.1"]
+    r = subprocess.run(cmd, capture_output=True, text=True, timeout=300, cwd=root)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [x for x in r.stdout.splitlines() if x.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["impl"] == "reference" and d["value"] > 0 and d["steps"] == 1 and d["warmup"] == 3
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["cpu_baseline"]["cores"] >= 1 and d["cpu_baseline"]["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    r1 = subprocess.run(cmd, capture_output=True, text=True, timeout=300, cwd=root, env=dict(os.environ, RANK="1"))
+    assert r1.returncode == 0 and not [x for x in r1.stdout.splitlines() if x.startswith("{")]
